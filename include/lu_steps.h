@@ -1,0 +1,69 @@
+/*
+ * lu_steps.h -- step-level entry points of libgb300lu.so, one per step of the
+ * blocked LU iteration, so that each step can be checked on its own.
+ *
+ * The steps are those of the paper's blocked right-looking LU (arxiv
+ * 2202.13995, section "Base Implementation", figure "lu_iteration"): factor
+ * the block column ("LU" and "left" blocks, here one panel with partial
+ * pivoting), update the "top" blocks with L (a triangular solve), and update
+ * the "inner" blocks by a matrix multiplication.
+ *
+ * Conventions: as lu.h, except that every matrix here is ROW-major (element
+ * (i, j) at p[i*ld + j]), which is the library's internal working layout.
+ * Each call enqueues its work on the context's stream and returns; status bits
+ * raised on the device (timeout, range) are reported by lu_ctx_status.
+ */
+#ifndef GB300_LU_STEPS_H
+#define GB300_LU_STEPS_H
+
+#include "lu.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Panel factorization with partial pivoting of the m x w row-major panel dP
+ * (FP64 when prec is LU_F64, FP32 otherwise), m >= w, w <= 512, in place:
+ * L below the diagonal (unit diagonal implied), U on and above it.
+ * dIpiv (device, w ints) receives the 1-based pivot rows (relative to the
+ * panel), dInfo (device, 1 int) the first zero pivot (1-based) or 0. */
+int lu_step_panel(lu_ctx ctx, lu_prec prec, int m, int w, void *dP, int ld, int *dIpiv, int *dInfo);
+
+/* Top-block update U12 = L11^-1 A12: dL (w x w row-major, only the strict
+ * lower triangle is read; unit diagonal), dX (w x N row-major) overwritten. */
+int lu_step_trsm(lu_ctx ctx, lu_prec prec, int w, int N, const void *dL, int ldl, void *dX, int ldx);
+
+/* Inner-block update C -= A B with C m x n, A m x k, B k x n, row-major.
+ * LU_F64: FP64 A, B, C on the CUDA cores.  LU_F32: FP32 on the CUDA cores.
+ * LU_BF16 / LU_FP16: FP32 A, B, C; A and B are rounded to BF16 / FP16
+ * (round-to-nearest-even) and multiplied on the tensor cores (tcgen05) with
+ * FP32 accumulation, then subtracted from C in FP32. */
+int lu_step_gemm(lu_ctx ctx, lu_prec prec, int m, int n, int k, void *dC, int ldc, const void *dA, int lda,
+                 const void *dB, int ldb);
+
+/* Read and clear the context's device status bits (synchronizes): returns
+ * LU_OK, LU_ETIMEOUT or LU_ERANGE. */
+int lu_ctx_status(lu_ctx ctx);
+
+/* Phase profiling.  When enabled, the library records a CUDA event pair on
+ * the context's stream around every kernel launch of the factorization and
+ * solve, per phase.  lu_profile_read synchronizes and returns, per phase, the
+ * summed device milliseconds and the number of launches since the last read
+ * (phases: 0 panel, 1 laswp, 2 trsm, 3 cast, 4 gemm, 5 solve, 6 residual,
+ * 7 other; arrays of LU_NPHASE entries), then clears the record. */
+#define LU_NPHASE 8
+int lu_profile_enable(lu_ctx ctx, int enable);
+int lu_profile_read(lu_ctx ctx, double *ms, long long *launches);
+
+/* Kernels this context has launched so far (all phases, profiling or not). */
+long long lu_launch_count(lu_ctx ctx);
+
+/* Number of SMs of the context's device and the library's build tag (static
+ * string naming the target architecture). */
+int lu_device_sm_count(lu_ctx ctx);
+const char *lu_build_tag(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_LU_STEPS_H */

@@ -107,18 +107,24 @@ def getf2(A):
     return LU, ipiv[:min(m, n)], int(info)
 
 
-def getrf(A, nb: int | None = None, ksteps: int = -1):
+def getrf(A, nb: int | None = None, ksteps: int = -1, timed: bool = False):
     """GEPP of a square matrix: unblocked (nb None) or the blocked right-looking
-    iteration with block width nb (optionally only its first `ksteps` steps)."""
+    iteration with block width nb (optionally only its first `ksteps` steps).
+    With timed=True a fourth value is the wall time of the C call alone."""
+    import time
     LU = _f64(A)
     n = LU.shape[0]
     assert LU.shape == (n, n)
     ipiv = np.zeros(max(1, n), dtype=np.int32)
     lib = _load()
+    t0 = time.perf_counter()
     if nb is None:
         info = lib.orc_getrf(n, _ptr(LU), max(1, n), _ptr(ipiv))
     else:
         info = lib.orc_getrf_blocked_steps(n, int(nb), _ptr(LU), max(1, n), _ptr(ipiv), int(ksteps))
+    dt = time.perf_counter() - t0
+    if timed:
+        return LU, ipiv[:n], int(info), dt
     return LU, ipiv[:n], int(info)
 
 

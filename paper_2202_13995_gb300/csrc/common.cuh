@@ -1,0 +1,129 @@
+// Device helpers shared by the kernels of the LU library: status bits, bounded
+// waits on %globaltimer, and a grid barrier for cooperative launches.
+//
+// Every spin in this library is bounded: a wait that runs past its limit sets
+// ST_TIMEOUT in the caller's device status word and returns false, and the
+// kernel then leaves without touching the data any further.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gb {
+
+// device status bits (OR-ed into a status word that the host reads)
+enum StatusBits : int {
+  ST_TIMEOUT = 1,   // a bounded device wait hit its limit
+  ST_RANGE = 2,     // a cast to a 16-bit format overflowed, or a NaN was met
+  ST_BADARG = 4,    // a kernel was given a size it cannot handle
+};
+
+// limit of every device spin (nanoseconds of %globaltimer)
+#ifndef GB_SPIN_LIMIT_NS
+#define GB_SPIN_LIMIT_NS 2000000000ull
+#endif
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_acquire_s32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_s32(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait until *flag == want (acquire).  Called by one thread.  Returns false
+// (and sets ST_TIMEOUT) if the limit runs out first.
+__device__ __forceinline__ bool wait_flag_eq(const int* flag, int want, int* status) {
+  if (ld_acquire_s32(flag) == want) return true;
+  const uint64_t t0 = gtimer();
+  while (true) {
+    for (int i = 0; i < 64; ++i) {
+      if (ld_acquire_s32(flag) == want) return true;
+    }
+    if (gtimer() - t0 > GB_SPIN_LIMIT_NS) {
+      atomicOr(status, ST_TIMEOUT);
+      return false;
+    }
+    __nanosleep(32);
+  }
+}
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).
+// bar[0] = arrival count, bar[1] = generation.  The host zeroes both before
+// the launch.  Returns false in every thread of the CTA if the wait timed out.
+struct GridBarrier {
+  unsigned* bar;
+  unsigned nblocks;
+};
+
+__device__ __forceinline__ bool grid_sync(const GridBarrier& gbar, int* status, int* smem_flag) {
+  __syncthreads();
+  if (gbar.nblocks > 1) {
+    if (threadIdx.x == 0) {
+      int ok = 1;
+      unsigned gen = ld_acquire_u32(gbar.bar + 1);
+      __threadfence();
+      unsigned arrived = atomicAdd(gbar.bar, 1u);
+      if (arrived == gbar.nblocks - 1) {
+        atomicExch(gbar.bar, 0u);
+        __threadfence();
+        st_release_u32(gbar.bar + 1, gen + 1);
+      } else {
+        const uint64_t t0 = gtimer();
+        while (ld_acquire_u32(gbar.bar + 1) == gen) {
+          if (gtimer() - t0 > GB_SPIN_LIMIT_NS) {
+            atomicOr(status, ST_TIMEOUT);
+            ok = 0;
+            break;
+          }
+        }
+      }
+      __threadfence();
+      *smem_flag = ok;
+    }
+    __syncthreads();
+    return *smem_flag != 0;
+  }
+  return true;
+}
+
+// (|v|, index) pair reduction used by the pivot search: larger |v| wins, and on
+// equal |v| the smaller row index wins (the first row of largest magnitude).
+template <typename T>
+__device__ __forceinline__ void argmax_merge(T& v, int& i, T v2, int i2) {
+  if (v2 > v || (v2 == v && i2 < i)) {
+    v = v2;
+    i = i2;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void warp_argmax(T& v, int& i) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    T v2 = __shfl_xor_sync(0xffffffffu, v, off);
+    int i2 = __shfl_xor_sync(0xffffffffu, i, off);
+    argmax_merge(v, i, v2, i2);
+  }
+}
+
+__host__ __device__ __forceinline__ int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace gb

@@ -1,0 +1,484 @@
+// Tensor-core trailing update for the mixed-precision factorization:
+//   C (FP32, row-major) -= Aop * Bop^T,  Aop = L21 and Bop = U12^T in BF16 or
+//   FP16 (K-major), products accumulated in FP32.
+//
+// This is the paper's "inner" block update by matrix multiplication (arxiv
+// 2202.13995, section "Base Implementation"; the paper's own design unrolls a
+// register-blocked GEMM in FPGA DSPs), here on the 5th-generation tensor cores:
+//   - warp 0 (one thread) streams K-chunks of 64 elements of both operands
+//     into a 4-stage shared-memory ring with TMA (128-byte swizzle);
+//   - warp 1 (one thread) issues tcgen05.mma (M=128, N=256, K=16) into one of
+//     two TMEM accumulators (2 x 256 columns), committing each stage back to
+//     the producer and each finished tile to the epilogue;
+//   - warps 2..9 drain a finished accumulator with tcgen05.ld while the next
+//     tile accumulates in the other one, and subtract it from C in place.
+// Persistent CTAs (one per SM) walk the output tiles.  Every mbarrier wait is
+// bounded; on timeout the kernel raises ST_TIMEOUT, lets its TMA loads and
+// MMAs land, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace gb {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BN = 256;
+constexpr int TC_BK = 64;  // one 128-byte swizzle row of 16-bit elements
+constexpr int TC_STAGES = 4;
+constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;  // 16 KB
+constexpr int TC_B_BYTES = TC_BN * TC_BK * 2;  // 32 KB
+constexpr int TC_EPI_WARPS = 8;
+constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
+constexpr int TC_TMEM_COLS = 512;
+constexpr size_t TC_SMEM = 1024 + (size_t)TC_STAGES * (TC_A_BYTES + TC_B_BYTES) + 256;
+
+// ------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the completion of the phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* status, volatile int* abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (true) {
+    for (int i = 0; i < 32; ++i)
+      if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (gtimer() - t0 > GB_SPIN_LIMIT_NS) {
+      atomicOr(status, ST_TIMEOUT);
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile stored with the
+// 128-byte swizzle (rows of 128 bytes, 8-row atoms 1024 bytes apart).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused with this swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;                    // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: kind::f16, D = F32, A = B = BF16 (fmt 1) or F16
+// (fmt 0), both K-major, M = 128, N = 256.
+__host__ __device__ constexpr uint32_t tc_idesc(uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_BN >> 3) << 17) | ((uint32_t)(TC_BM >> 4) << 24);
+}
+
+#define TMEM_LD_X32(taddr, v)                                                                                     \
+  asm volatile(                                                                                                   \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18," \
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                                             \
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),           \
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),     \
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),   \
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])    \
+      : "r"(taddr))
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// ------------------------------------------------------------ kernel
+struct TcParams {
+  float* C;
+  int64_t ldc;
+  int m, n, kchunks;
+  int tiles_m, tiles_n;
+  int vec_ok;  // C rows 16-byte aligned
+  uint32_t idesc;
+  int* status;
+};
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams P) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = smem_raw + (base - raw);
+  const uint32_t sA = base;
+  const uint32_t sB = base + TC_STAGES * TC_A_BYTES;
+  unsigned char* ctl = gbase + TC_STAGES * (TC_A_BYTES + TC_B_BYTES);
+  const uint32_t bar_full = smem_u32(ctl);
+  const uint32_t bar_empty = bar_full + 8 * TC_STAGES;
+  const uint32_t bar_tfull = bar_empty + 8 * TC_STAGES;
+  const uint32_t bar_tempty = bar_tfull + 16;
+  const uint32_t bar_drain = bar_tempty + 16;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ctl + 8 * (2 * TC_STAGES + 5));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(ctl + 8 * (2 * TC_STAGES + 5) + 8);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntiles = P.tiles_m * P.tiles_n;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(bar_full + 8 * s, 1);
+      mbar_init(bar_empty + 8 * s, 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(bar_tfull + 8 * a, 1);
+      mbar_init(bar_tempty + 8 * a, TC_EPI_WARPS);
+    }
+    mbar_init(bar_drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      int last_par[TC_STAGES];
+#pragma unroll
+      for (int s = 0; s < TC_STAGES; ++s) last_par[s] = -1;
+      int s = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int tm = t % P.tiles_m, tn = t / P.tiles_m;
+        for (int kc = 0; kc < P.kchunks; ++kc) {
+          if (!mbar_wait(bar_empty + 8 * s, ph ^ 1u, P.status, abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(bar_full + 8 * s, TC_A_BYTES + TC_B_BYTES);
+          tma_load_2d(sA + s * TC_A_BYTES, &tmA, kc * TC_BK, tm * TC_BM, bar_full + 8 * s);
+          tma_load_2d(sB + s * TC_B_BYTES, &tmB, kc * TC_BK, tn * TC_BN, bar_full + 8 * s);
+          last_par[s] = (int)ph;
+          if (++s == TC_STAGES) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+      if (!ok) {
+        // let every issued copy land before the CTA can exit
+        for (int q = 0; q < TC_STAGES; ++q) {
+          if (last_par[q] < 0) continue;
+          const uint64_t t0 = gtimer();
+          while (!mbar_try(bar_full + 8 * q, (uint32_t)last_par[q]) && gtimer() - t0 < GB_SPIN_LIMIT_NS) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      int acc = 0;
+      uint32_t aph = 0;
+      bool ok = true;
+      bool issued = false;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        if (!mbar_wait(bar_tempty + 8 * acc, aph ^ 1u, P.status, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dtm = tmem_base + (uint32_t)(acc * TC_BN);
+        for (int kc = 0; kc < P.kchunks; ++kc) {
+          if (!mbar_wait(bar_full + 8 * s, ph, P.status, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = sA + s * TC_A_BYTES, b0 = sB + s * TC_B_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < TC_BK / 16; ++kk) {
+            tc_mma(dtm, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), P.idesc, (kc | kk) ? 1u : 0u);
+          }
+          issued = true;
+          tc_commit(bar_empty + 8 * s);
+          if (++s == TC_STAGES) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (!ok) break;
+        tc_commit(bar_tfull + 8 * acc);
+        if (++acc == 2) {
+          acc = 0;
+          aph ^= 1u;
+        }
+      }
+      if (!ok && issued) {
+        // let the MMAs already issued finish before TMEM is freed
+        tc_commit(bar_drain);
+        const uint64_t t0 = gtimer();
+        while (!mbar_try(bar_drain, 0) && gtimer() - t0 < GB_SPIN_LIMIT_NS) {
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue: C -= accumulator
+    const int q = warp & 3;              // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;    // which 128 columns of the tile
+    int acc = 0;
+    uint32_t aph = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const int tm = t % P.tiles_m, tn = t / P.tiles_m;
+      int okw = 1;
+      if (lane == 0) okw = mbar_wait(bar_tfull + 8 * acc, aph, P.status, abort_flag) ? 1 : 0;
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      if (!okw) break;
+      tc_fence_after();
+      const int row = tm * TC_BM + q * 32 + lane;
+      float* crow = P.C + (int64_t)row * P.ldc;
+      const bool rok = row < P.m;
+#pragma unroll 1
+      for (int cc = 0; cc < 128; cc += 32) {
+        const int col0 = half * 128 + cc;
+        uint32_t v[32];
+        const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * TC_BN + col0);
+        TMEM_LD_X32(taddr, v);
+        tmem_wait_ld();
+        const int gc0 = tn * TC_BN + col0;
+        if (rok) {
+          if (P.vec_ok && gc0 + 32 <= P.n) {
+            float4* cp = reinterpret_cast<float4*>(crow + gc0);
+            float4 cv[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) cv[j] = cp[j];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              cv[j].x -= __uint_as_float(v[4 * j + 0]);
+              cv[j].y -= __uint_as_float(v[4 * j + 1]);
+              cv[j].z -= __uint_as_float(v[4 * j + 2]);
+              cv[j].w -= __uint_as_float(v[4 * j + 3]);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) cp[j] = cv[j];
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (gc0 + j < P.n) crow[gc0 + j] -= __uint_as_float(v[j]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_tempty + 8 * acc);
+      if (++acc == 2) {
+        acc = 0;
+        aph ^= 1u;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TC_TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------ operand casts
+// Aop[i*kpad + t] = L21(i, t), Bop[j*kpad + t] = U12(t, j), zero for t >= k.
+template <typename H>
+__device__ __forceinline__ H to16(float v);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+template <>
+__device__ __forceinline__ __half to16<__half>(float v) {
+  return __float2half_rn(v);
+}
+template <typename H>
+__device__ __forceinline__ bool bad16(H h);
+template <>
+__device__ __forceinline__ bool bad16<__nv_bfloat16>(__nv_bfloat16 h) {
+  return (__bfloat16_as_ushort(h) & 0x7f80u) == 0x7f80u;
+}
+template <>
+__device__ __forceinline__ bool bad16<__half>(__half h) {
+  return (__half_as_ushort(h) & 0x7c00u) == 0x7c00u;
+}
+
+template <typename H>
+__global__ void cast_a_kernel(const float* __restrict__ L21, int64_t ld, int m, int k, H* __restrict__ Aop, int kpad,
+                              int* status) {
+  const int i = blockIdx.y;
+  bool bad = false;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < kpad; t += gridDim.x * blockDim.x) {
+    H h = to16<H>(t < k ? L21[(int64_t)i * ld + t] : 0.0f);
+    bad |= bad16<H>(h);
+    Aop[(int64_t)i * kpad + t] = h;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_RANGE);
+}
+
+template <typename H>
+__global__ void cast_b_kernel(const float* __restrict__ U12, int64_t ld, int n, int k, H* __restrict__ Bop, int kpad,
+                              int* status) {
+  __shared__ float tile[32][33];
+  const int j0 = blockIdx.x * 32, t0 = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int r = ty; r < 32; r += 8) {
+    const int t = t0 + r, j = j0 + tx;
+    tile[r][tx] = (t < k && j < n) ? U12[(int64_t)t * ld + j] : 0.0f;
+  }
+  __syncthreads();
+  bool bad = false;
+  for (int r = ty; r < 32; r += 8) {
+    const int j = j0 + r, t = t0 + tx;
+    if (j < n && t < kpad) {
+      H h = to16<H>(tile[tx][r]);
+      bad |= bad16<H>(h);
+      Bop[(int64_t)j * kpad + t] = h;
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && tx == 0) atomicOr(status, ST_RANGE);
+}
+
+cudaError_t launch_cast_operands(int kind, const float* L21, const float* U12, int64_t ldw, int m, int n, int k,
+                                 void* Aop, void* Bop, int kpad, int* status, cudaStream_t st) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  if (m > 65535 * 64 || (kpad % 64) != 0 || k > kpad) return cudaErrorInvalidValue;
+  dim3 ga((unsigned)cdiv(kpad, 256), (unsigned)m);
+  dim3 gb_((unsigned)cdiv(n, 32), (unsigned)cdiv(kpad, 32));
+  if (kind == 1) {
+    cast_a_kernel<__nv_bfloat16><<<ga, 256, 0, st>>>(L21, ldw, m, k, (__nv_bfloat16*)Aop, kpad, status);
+    cast_b_kernel<__nv_bfloat16><<<gb_, dim3(32, 8), 0, st>>>(U12, ldw, n, k, (__nv_bfloat16*)Bop, kpad, status);
+  } else {
+    cast_a_kernel<__half><<<ga, 256, 0, st>>>(L21, ldw, m, k, (__half*)Aop, kpad, status);
+    cast_b_kernel<__half><<<gb_, dim3(32, 8), 0, st>>>(U12, ldw, n, k, (__half*)Bop, kpad, status);
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ host side
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static PFN_encodeTiled get_encode() {
+  static PFN_encodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_encodeTiled)p;
+  });
+  return fn;
+}
+
+static bool make_map(CUtensorMap* map, int kind, const void* ptr, int rows, int kpad, int box_rows) {
+  PFN_encodeTiled enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                   const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+cudaError_t tc_gemm_run(int kind, float* C, int64_t ldc, const void* Aop, const void* Bop, int m, int n, int kpad,
+                        int* status, const DevInfo& dev, cudaStream_t st) {
+  if (m <= 0 || n <= 0) return cudaSuccess;
+  if (kind != 1 && kind != 2) return cudaErrorInvalidValue;
+  if (kpad <= 0 || (kpad % TC_BK) != 0) return cudaErrorInvalidValue;
+  if (((uintptr_t)Aop & 15u) || ((uintptr_t)Bop & 15u)) return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, kind, Aop, m, kpad, TC_BM) || !make_map(&mb, kind, Bop, n, kpad, TC_BN))
+    return cudaErrorInvalidValue;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  TcParams P;
+  P.C = C;
+  P.ldc = ldc;
+  P.m = m;
+  P.n = n;
+  P.kchunks = kpad / TC_BK;
+  P.tiles_m = (int)cdiv(m, TC_BM);
+  P.tiles_n = (int)cdiv(n, TC_BN);
+  P.vec_ok = (((uintptr_t)C & 15u) == 0 && (ldc % 4) == 0) ? 1 : 0;
+  P.idesc = tc_idesc(kind == 1 ? 1u : 0u);
+  P.status = status;
+  const int ntiles = P.tiles_m * P.tiles_n;
+  const int grid = ntiles < dev.sm_count ? ntiles : dev.sm_count;
+  tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(ma, mb, P);
+  return cudaGetLastError();
+}
+
+size_t tc_gemm_plan_bytes() { return 0; }
+
+}  // namespace gb

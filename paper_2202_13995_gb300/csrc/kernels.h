@@ -1,0 +1,108 @@
+// Internal launchers of the LU library (not part of the C ABI).
+//
+// Layout of the working matrix W: ROW-major, W[i*ldw + j] = A(i, j), in the
+// factor's working type T (double for LU_F64, float otherwise).  Row
+// interchanges are then contiguous copies, and the trailing update's A operand
+// (L21) is K-major as stored.  The caller's A stays column-major FP64.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gb {
+
+struct DevInfo {
+  int sm_count;
+  int max_smem_optin;
+};
+
+// ---------------------------------------------------------------- panel.cu
+// Scratch of the cooperative panel kernel (global memory, owned by the caller).
+struct PanelScratch {
+  unsigned* bar;   // 2 words: grid barrier (zeroed by the launcher)
+  void* xval;      // [2][Gmax] T
+  int* xidx;       // [2][Gmax]
+  void* xrow;      // [2][Gmax][ib] T
+  void* xrowj;     // [2][ib] T
+  int* perm;       // 1 + 4*wmax ints: count, dst positions, src positions
+  int gmax;        // capacity in CTAs
+  int ibmax;
+  int wmax;
+};
+size_t panel_scratch_bytes(int gmax, int ibmax, int wmax, int tsize);
+void panel_scratch_carve(PanelScratch* s, void* base, int gmax, int ibmax, int wmax, int tsize);
+
+// Factor the m x w panel whose (0,0) element is W(k,k) (row stride ldw) with
+// partial pivoting.  Writes ipiv[k..k+w) (1-based, absolute), lowers *info to
+// the first zero pivot (absolute, 1-based; the caller initialises it to
+// INT_MAX), and the panel's net row permutation into scratch.perm.
+template <typename T>
+cudaError_t launch_panel(T* Wkk, int64_t ldw, int m, int w, int kabs, int* ipiv, int* info, int* status,
+                         const PanelScratch& s, const DevInfo& dev, cudaStream_t st);
+
+// Apply the panel permutation in scratch.perm (positions relative to row k) to
+// columns [0, k) and [k + w, n) of W, and to the row-index vector rowid.
+template <typename T>
+cudaError_t launch_laswp(T* W, int64_t ldw, int n, int k, int w, const int* perm, int* rowid, cudaStream_t st);
+
+// U12 <- L11^-1 A12: L11 = unit-lower w x w at W(k,k), A12 = w x N at W(k,k+w).
+template <typename T>
+cudaError_t launch_trsm_lower(const T* L11, T* A12, int64_t ldw, int w, int N, cudaStream_t st);
+
+// W (row-major T) <- A (column-major FP64), n x n.
+template <typename T>
+cudaError_t launch_to_working(const double* A, int64_t lda, T* W, int64_t ldw, int n, cudaStream_t st);
+// LU (column-major FP64) <- W (row-major T), n x n.
+template <typename T>
+cudaError_t launch_from_working(const T* W, int64_t ldw, double* LU, int64_t ldlu, int n, cudaStream_t st);
+
+cudaError_t launch_iota(int* v, int n, cudaStream_t st);
+
+// ---------------------------------------------------------------- gemm_simt.cu
+// C (m x n) -= A (m x k) * B (k x n), all row-major in T, CUDA-core FMA.
+template <typename T>
+cudaError_t launch_gemm_simt(T* C, int64_t ldc, const T* A, int64_t lda, const T* B, int64_t ldb, int m, int n,
+                             int k, cudaStream_t st);
+
+// ---------------------------------------------------------------- gemm_tc.cu
+// Operand casts for the tensor-core update (kind 1 = BF16, 2 = FP16):
+//   Aop[i*kpad + t] = L21(i, t)     (K-major, m x k)
+//   Bop[j*kpad + t] = U12(t, j)     (K-major, n x k)
+// kpad >= k is a multiple of 64 with zero fill.  Overflow or NaN sets ST_RANGE.
+cudaError_t launch_cast_operands(int kind, const float* L21, const float* U12, int64_t ldw, int m, int n, int k,
+                                 void* Aop, void* Bop, int kpad, int* status, cudaStream_t st);
+// C (row-major FP32, m x n) -= Aop * Bop^T on tcgen05 (FP32 accumulate in TMEM).
+struct TcGemmPlan;
+size_t tc_gemm_plan_bytes();
+cudaError_t tc_gemm_run(int kind, float* C, int64_t ldc, const void* Aop, const void* Bop, int m, int n, int kpad,
+                        int* status, const DevInfo& dev, cudaStream_t st);
+
+// ---------------------------------------------------------------- solve.cu
+struct SolveScratch {
+  int* sync;       // flags [nblk] + ticket (zeroed per launch by the launcher)
+  void* y;         // n x NR (T) workspace
+  void* z;         // n x NR (T) workspace
+  int nblk_max;
+};
+size_t solve_scratch_bytes(int n, int tsize);
+void solve_scratch_carve(SolveScratch* s, void* base, int n, int tsize);
+
+// X = U^-1 L^-1 P B for one chunk of <= 32 right-hand sides.  B, X: FP64
+// column-major (may alias).  Computed in T.
+template <typename T>
+cudaError_t launch_lu_solve(const T* W, int64_t ldw, const int* rowid, int n, int nrhs, const double* B,
+                            int64_t ldb, double* X, int64_t ldx, const SolveScratch& s, int* status, cudaStream_t st);
+
+// R = B - A X (FP64), with per-column max |r|, max |x|, max |b| into norms
+// (3*nrhs doubles, zeroed by the launcher).  partial: workspace of
+// residual_partial_bytes(n, nrhs).
+size_t residual_partial_bytes(int n, int nrhs);
+cudaError_t launch_residual(const double* A, int64_t lda, const double* X, int64_t ldx, const double* B,
+                            int64_t ldb, double* R, int64_t ldr, int n, int nrhs, double* partial, double* norms,
+                            cudaStream_t st);
+// anorm[0] = ||A||_inf (max row sum of |A|).
+cudaError_t launch_norm_inf(const double* A, int64_t lda, int n, double* partial, double* anorm, cudaStream_t st);
+// X[:, q] += D[:, q] for columns q with active[q] != 0.
+cudaError_t launch_add_update(double* X, int64_t ldx, const double* D, int64_t ldd, int n, int nrhs,
+                              const int* active, cudaStream_t st);
+
+}  // namespace gb

@@ -1,0 +1,659 @@
+// C ABI of the LU library: contexts, the blocked factorization driver, the
+// solve and the mixed-precision refinement loop (see include/lu.h).
+//
+// The driver follows the paper's blocked right-looking iteration (arxiv
+// 2202.13995, section "Base Implementation", figure "lu_iteration"): per block
+// column k of width nb,
+//   1. panel   -- factor the m x nb block column with partial pivoting
+//                 (the paper's "LU" + "left" blocks),
+//   2. laswp   -- apply its row interchanges to the other columns,
+//   3. trsm    -- U12 <- L11^-1 A12 (the "top" blocks),
+//   4. update  -- A22 <- A22 - L21 U12 (the "inner" blocks, a GEMM).
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lu.h"
+#include "../../include/lu_steps.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace gb;
+
+struct lu_ctx_s {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  DevInfo dev{};
+  int* d_status = nullptr;   // device status bits
+  double* d_small = nullptr; // 4 + 3*32 doubles: anorm, norms
+  int* d_active = nullptr;   // 32 ints: refinement column mask
+  int* h_pinned = nullptr;   // pinned: 64 ints
+  double* h_norms = nullptr; // pinned: 4 + 3*32 doubles
+  // step-level scratch (lazily sized)
+  void* step_ws = nullptr;
+  size_t step_ws_bytes = 0;
+  // launch accounting and optional per-phase event timing
+  long long launches = 0;
+  bool prof = false;
+  struct Rec {
+    int phase;
+    int nk;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+};
+
+enum { PH_PANEL = 0, PH_LASWP, PH_TRSM, PH_CAST, PH_GEMM, PH_SOLVE, PH_RESID, PH_OTHER, PH_N };
+
+static cudaEvent_t ev_get(lu_ctx c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch wrapper: counts the kernels a launcher starts and, when profiling,
+// brackets them with an event pair on the context's stream.
+template <typename F>
+static cudaError_t run_phase(lu_ctx c, int phase, int nk, F&& launch) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (c->prof) {
+    a = ev_get(c);
+    b = ev_get(c);
+    cudaEventRecord(a, c->stream);
+  }
+  cudaError_t e = launch();
+  if (c->prof) {
+    cudaEventRecord(b, c->stream);
+    c->recs.push_back({phase, nk, a, b});
+  }
+  if (e == cudaSuccess) c->launches += nk;
+  return e;
+}
+#define PHASE(c, ph, nk, expr) run_phase((c), (ph), (nk), [&]() { return (expr); })
+
+struct lu_fact_s {
+  lu_ctx ctx = nullptr;
+  int n = 0;
+  lu_prec prec = LU_F64;
+  int nb = 0;
+  int64_t ldw = 0;
+  int tsize = 8;
+  void* W = nullptr;  // working matrix, row-major T
+  int* ipiv = nullptr;
+  int* rowid = nullptr;
+  int* info_d = nullptr;
+  void* panel_mem = nullptr;
+  PanelScratch ps{};
+  void* aop = nullptr;  // tensor-core operands (K-major, 16-bit)
+  void* bop = nullptr;
+  int kpad = 0;
+  void* solve_mem = nullptr;
+  SolveScratch ss{};
+  double* vec_ws = nullptr;  // refinement: R, D, partial sums
+  size_t vec_ws_bytes = 0;
+  int info = -1;             // cached host info (-1 = unknown)
+};
+
+static const char* k_err[] = {"ok",
+                              "singular factor (exact zero pivot)",
+                              "device allocation failed",
+                              "refinement did not converge within max_iter",
+                              "16-bit cast overflow or NaN",
+                              "a bounded device wait timed out",
+                              "not finished",
+                              "CUDA runtime error",
+                              "internal error"};
+
+extern "C" const char* lu_strerror(int code) {
+  if (code < 0) return "invalid argument";
+  if (code <= LU_EINTERNAL) return k_err[code];
+  return "unknown status";
+}
+
+extern "C" const char* lu_build_tag(void) { return "gb300lu sm_103a"; }
+
+#define CU_TRY(expr)                                                                          \
+  do {                                                                                        \
+    cudaError_t e_ = (expr);                                                                  \
+    if (e_ != cudaSuccess) {                                                                  \
+      if (getenv("GB300LU_DEBUG")) fprintf(stderr, "gb300lu: %s -> %s\n", #expr, cudaGetErrorString(e_)); \
+      return (e_ == cudaErrorMemoryAllocation) ? LU_ENOMEM : LU_ECUDA;                        \
+    }                                                                                         \
+  } while (0)
+
+static int dalloc(lu_ctx c, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return LU_OK;
+  cudaError_t e = cudaMallocAsync(p, bytes, c->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return LU_ENOMEM;
+  }
+  return LU_OK;
+}
+
+static void dfree(lu_ctx c, void* p) {
+  if (p) cudaFreeAsync(p, c->stream);
+}
+
+extern "C" int lu_create(lu_ctx* out, void* cuda_stream) {
+  if (!out) return -1;
+  *out = nullptr;
+  lu_ctx c = new (std::nothrow) lu_ctx_s();
+  if (!c) return LU_ENOMEM;
+  c->stream = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return LU_ECUDA;
+  }
+  cudaDeviceGetAttribute(&c->dev.sm_count, cudaDevAttrMultiProcessorCount, c->device);
+  cudaDeviceGetAttribute(&c->dev.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
+  if (cudaMalloc(&c->d_status, 64 * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&c->d_small, 128 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&c->d_active, 64 * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&c->h_pinned, 64 * sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&c->h_norms, 128 * sizeof(double)) != cudaSuccess) {
+    lu_destroy(c);
+    return LU_ENOMEM;
+  }
+  cudaMemset(c->d_status, 0, 64 * sizeof(int));
+  cudaMemset(c->d_small, 0, 128 * sizeof(double));
+  *out = c;
+  return LU_OK;
+}
+
+extern "C" void lu_destroy(lu_ctx c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& r : c->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->pool) cudaEventDestroy(e);
+  if (c->step_ws) cudaFree(c->step_ws);
+  if (c->d_status) cudaFree(c->d_status);
+  if (c->d_small) cudaFree(c->d_small);
+  if (c->d_active) cudaFree(c->d_active);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  if (c->h_norms) cudaFreeHost(c->h_norms);
+  delete c;
+}
+
+extern "C" int lu_device_sm_count(lu_ctx c) { return c ? c->dev.sm_count : 0; }
+
+extern "C" long long lu_launch_count(lu_ctx c) { return c ? c->launches : 0; }
+
+extern "C" int lu_profile_enable(lu_ctx c, int enable) {
+  if (!c) return -1;
+  c->prof = enable != 0;
+  return LU_OK;
+}
+
+extern "C" int lu_profile_read(lu_ctx c, double* ms, long long* launches) {
+  if (!c) return -1;
+  if (!ms) return -2;
+  if (!launches) return -3;
+  for (int p = 0; p < PH_N; ++p) {
+    ms[p] = 0.0;
+    launches[p] = 0;
+  }
+  CU_TRY(cudaStreamSynchronize(c->stream));
+  for (auto& r : c->recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) ms[r.phase] += t;
+    launches[r.phase] += r.nk;
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->recs.clear();
+  return LU_OK;
+}
+
+static int read_status(lu_ctx c) {
+  CU_TRY(cudaMemcpyAsync(c->h_pinned, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU_TRY(cudaStreamSynchronize(c->stream));
+  const int s = c->h_pinned[0];
+  if (s) {
+    CU_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+  }
+  if (s & ST_TIMEOUT) return LU_ETIMEOUT;
+  if (s & ST_RANGE) return LU_ERANGE;
+  if (s & ST_BADARG) return LU_EINTERNAL;
+  return LU_OK;
+}
+
+extern "C" int lu_ctx_status(lu_ctx c) {
+  if (!c) return -1;
+  return read_status(c);
+}
+
+static int default_nb(int n, lu_prec prec) {
+  if (prec == LU_F64 || prec == LU_F32) return n >= 4096 ? 256 : 64;
+  return n >= 2048 ? 256 : 64;
+}
+
+static int round_up(int v, int a) { return (v + a - 1) / a * a; }
+
+// ------------------------------------------------------------------ factor
+template <typename T>
+static int factor_loop(lu_fact f) {
+  lu_ctx c = f->ctx;
+  cudaStream_t st = c->stream;
+  T* W = (T*)f->W;
+  const int n = f->n, nb = f->nb;
+  const int64_t ld = f->ldw;
+  for (int k = 0; k < n; k += nb) {
+    const int w = (n - k) < nb ? (n - k) : nb;
+    T* Wkk = W + (int64_t)k * ld + k;
+    CU_TRY(PHASE(c, PH_PANEL, 1, launch_panel<T>(Wkk, ld, n - k, w, k, f->ipiv, f->info_d, c->d_status, f->ps, c->dev, st)));
+    CU_TRY(PHASE(c, PH_LASWP, 1, launch_laswp<T>(W, ld, n, k, w, f->ps.perm, f->rowid, st)));
+    const int rest = n - k - w;
+    if (rest > 0) {
+      T* U12 = Wkk + w;
+      T* L21 = Wkk + (int64_t)w * ld;
+      T* A22 = L21 + w;
+      CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12, ld, w, rest, st)));
+      if (f->prec == LU_BF16 || f->prec == LU_FP16) {
+        const int kind = f->prec == LU_BF16 ? 1 : 2;
+        CU_TRY(PHASE(c, PH_CAST, 2, launch_cast_operands(kind, (const float*)L21, (const float*)U12, ld, rest, rest,
+                                                          w, f->aop, f->bop, f->kpad, c->d_status, st)));
+        CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)A22, ld, f->aop, f->bop, rest, rest, f->kpad,
+                                                 c->d_status, c->dev, st)));
+      } else {
+        CU_TRY(PHASE(c, PH_GEMM, 1, launch_gemm_simt<T>(A22, ld, L21, ld, U12, ld, rest, rest, w, st)));
+      }
+    }
+  }
+  return LU_OK;
+}
+
+extern "C" void lu_fact_free(lu_fact f) {
+  if (!f) return;
+  lu_ctx c = f->ctx;
+  dfree(c, f->W);
+  dfree(c, f->ipiv);
+  dfree(c, f->panel_mem);
+  dfree(c, f->aop);
+  dfree(c, f->solve_mem);
+  dfree(c, f->vec_ws);
+  delete f;
+}
+
+extern "C" int lu_factor(lu_ctx c, int n, const double* dA, int lda, lu_prec prec, int nb, lu_fact* out,
+                         int* info) {
+  if (!c) return -1;
+  if (n < 0) return -2;
+  if (!dA && n > 0) return -3;
+  if (lda < (n > 1 ? n : 1)) return -4;
+  if (prec < LU_F64 || prec > LU_F32) return -5;
+  if (nb < 0 || nb > 512) return -6;
+  if (!out) return -7;
+  *out = nullptr;
+  if (nb == 0) nb = default_nb(n, prec);
+  lu_fact f = new (std::nothrow) lu_fact_s();
+  if (!f) return LU_ENOMEM;
+  f->ctx = c;
+  f->n = n;
+  f->prec = prec;
+  f->nb = nb < n ? nb : (n > 0 ? n : 1);
+  f->tsize = prec == LU_F64 ? 8 : 4;
+  f->ldw = round_up(n > 0 ? n : 1, 64);
+  const int nn = n > 0 ? n : 1;
+  int rc = LU_OK;
+  const int gmax = c->dev.sm_count;
+  size_t pbytes = panel_scratch_bytes(gmax, 32, f->nb, f->tsize);
+  if ((rc = dalloc(c, &f->W, (size_t)f->ldw * nn * f->tsize)) ||
+      (rc = dalloc(c, (void**)&f->ipiv, (size_t)(2 * nn + 64) * sizeof(int))) ||
+      (rc = dalloc(c, &f->panel_mem, pbytes)) ||
+      (rc = dalloc(c, &f->solve_mem, solve_scratch_bytes(nn, f->tsize)))) {
+    lu_fact_free(f);
+    return rc;
+  }
+  f->rowid = f->ipiv + nn;
+  f->info_d = f->rowid + nn;
+  panel_scratch_carve(&f->ps, f->panel_mem, gmax, 32, f->nb, f->tsize);
+  solve_scratch_carve(&f->ss, f->solve_mem, nn, f->tsize);
+  if (prec == LU_BF16 || prec == LU_FP16) {
+    f->kpad = round_up(f->nb, 64);
+    if ((rc = dalloc(c, &f->aop, (size_t)2 * nn * f->kpad * 2 + 1024))) {
+      lu_fact_free(f);
+      return rc;
+    }
+    f->bop = (char*)f->aop + ((size_t)nn * f->kpad * 2 + 1023) / 1024 * 1024;
+  }
+  cudaStream_t st = c->stream;
+  auto fail = [&](int r) {
+    lu_fact_free(f);
+    return r;
+  };
+  if (cudaMemsetAsync(f->info_d, 0x7f, sizeof(int), st) != cudaSuccess) return fail(LU_ECUDA);
+  if (n > 0) {
+    if (PHASE(c, PH_OTHER, 1, launch_iota(f->rowid, n, st)) != cudaSuccess) return fail(LU_ECUDA);
+    if (prec == LU_F64) {
+      if (PHASE(c, PH_OTHER, 1, launch_to_working<double>(dA, lda, (double*)f->W, f->ldw, n, st)) != cudaSuccess)
+        return fail(LU_ECUDA);
+      rc = factor_loop<double>(f);
+    } else {
+      if (PHASE(c, PH_OTHER, 1, launch_to_working<float>(dA, lda, (float*)f->W, f->ldw, n, st)) != cudaSuccess)
+        return fail(LU_ECUDA);
+      rc = factor_loop<float>(f);
+    }
+    if (rc) return fail(rc);
+  }
+  *out = f;
+  if (info) {
+    rc = lu_fact_info(f, info);
+    if (rc) return rc;
+  }
+  return LU_OK;
+}
+
+extern "C" int lu_fact_info(lu_fact f, int* info) {
+  if (!f) return -1;
+  lu_ctx c = f->ctx;
+  CU_TRY(cudaMemcpyAsync(c->h_pinned + 8, f->info_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  const int rs = read_status(c);  // synchronizes
+  const int v = c->h_pinned[8];
+  f->info = (v == 0x7f7f7f7f) ? 0 : v;
+  if (info) *info = f->info;
+  return rs;
+}
+
+extern "C" int lu_fact_ipiv(lu_fact f, int* dIpiv) {
+  if (!f) return -1;
+  if (!dIpiv) return -2;
+  if (f->n == 0) return LU_OK;
+  CU_TRY(cudaMemcpyAsync(dIpiv, f->ipiv, (size_t)f->n * sizeof(int), cudaMemcpyDeviceToDevice, f->ctx->stream));
+  return LU_OK;
+}
+
+extern "C" int lu_fact_lu(lu_fact f, double* dLU, int ldlu) {
+  if (!f) return -1;
+  if (!dLU && f->n > 0) return -2;
+  if (ldlu < f->n) return -3;
+  if (f->n == 0) return LU_OK;
+  if (f->prec == LU_F64)
+    CU_TRY(launch_from_working<double>((const double*)f->W, f->ldw, dLU, ldlu, f->n, f->ctx->stream));
+  else
+    CU_TRY(launch_from_working<float>((const float*)f->W, f->ldw, dLU, ldlu, f->n, f->ctx->stream));
+  return LU_OK;
+}
+
+// ------------------------------------------------------------------ solve
+static int ensure_info(lu_fact f) {
+  if (f->info < 0) {
+    int info = 0;
+    int rc = lu_fact_info(f, &info);
+    if (rc) return rc;
+  }
+  return f->info > 0 ? LU_ESINGULAR : LU_OK;
+}
+
+static int solve_chunks(lu_fact f, int nrhs, const double* dB, int64_t ldb, double* dX, int64_t ldx) {
+  lu_ctx c = f->ctx;
+  for (int q0 = 0; q0 < nrhs; q0 += 32) {
+    const int nr = (nrhs - q0) < 32 ? (nrhs - q0) : 32;
+    if (f->prec == LU_F64) {
+      CU_TRY(PHASE(c, PH_SOLVE, 2, launch_lu_solve<double>((const double*)f->W, f->ldw, f->rowid, f->n, nr,
+                                                            dB + q0 * ldb, ldb, dX + q0 * ldx, ldx, f->ss,
+                                                            c->d_status, c->stream)));
+    } else {
+      CU_TRY(PHASE(c, PH_SOLVE, 2, launch_lu_solve<float>((const float*)f->W, f->ldw, f->rowid, f->n, nr,
+                                                           dB + q0 * ldb, ldb, dX + q0 * ldx, ldx, f->ss,
+                                                           c->d_status, c->stream)));
+    }
+  }
+  return LU_OK;
+}
+
+extern "C" int lu_solve(lu_fact f, int nrhs, double* dB, int ldb) {
+  if (!f) return -1;
+  if (nrhs < 0) return -2;
+  if (!dB && nrhs > 0 && f->n > 0) return -3;
+  if (ldb < (f->n > 1 ? f->n : 1)) return -4;
+  if (f->n == 0 || nrhs == 0) return LU_OK;
+  int rc = ensure_info(f);
+  if (rc) return rc;
+  return solve_chunks(f, nrhs, dB, ldb, dB, ldb);
+}
+
+// ------------------------------------------------------------------ residual / refinement
+static double hpl_scaled(int n, double rn, double an, double xn, double bn) {
+  const double eps = std::ldexp(1.0, -53);
+  const double den = eps * (an * xn + bn) * (double)n;
+  return den > 0 ? rn / den : (rn > 0 ? INFINITY : 0.0);
+}
+
+static int ensure_vec_ws(lu_fact f, int nrhs) {
+  const size_t n = (size_t)f->n;
+  const size_t need = 2 * n * nrhs * 8 + residual_partial_bytes(f->n, nrhs > 32 ? 32 : nrhs) + 4096;
+  if (f->vec_ws_bytes >= need) return LU_OK;
+  dfree(f->ctx, f->vec_ws);
+  f->vec_ws = nullptr;
+  f->vec_ws_bytes = 0;
+  int rc = dalloc(f->ctx, (void**)&f->vec_ws, need);
+  if (rc) return rc;
+  f->vec_ws_bytes = need;
+  return LU_OK;
+}
+
+// norms of one chunk of <= 32 columns into c->h_norms (anorm computed by caller)
+static int residual_chunk(lu_ctx c, int n, int nr, const double* dA, int64_t lda, const double* dX, int64_t ldx,
+                          const double* dB, int64_t ldb, double* dR, int64_t ldr, double* partial) {
+  double* norms = c->d_small + 4;
+  CU_TRY(PHASE(c, PH_RESID, 2, launch_residual(dA, lda, dX, ldx, dB, ldb, dR, ldr, n, nr, partial, norms, c->stream)));
+  CU_TRY(cudaMemcpyAsync(c->h_norms + 4, norms, (size_t)3 * nr * sizeof(double), cudaMemcpyDeviceToHost,
+                         c->stream));
+  return LU_OK;
+}
+
+extern "C" int lu_refine(lu_fact f, const double* dA, int lda, const double* dB, int ldb, double* dX, int ldx,
+                         int nrhs, double tol, int max_iter, int* iters, double* scaled_resid) {
+  if (!f) return -1;
+  const int n = f->n;
+  if (!dA && n > 0) return -2;
+  if (lda < (n > 1 ? n : 1)) return -3;
+  if (!dB && n > 0 && nrhs > 0) return -4;
+  if (ldb < (n > 1 ? n : 1)) return -5;
+  if (!dX && n > 0 && nrhs > 0) return -6;
+  if (ldx < (n > 1 ? n : 1)) return -7;
+  if (nrhs < 0) return -8;
+  if (!(tol > 0)) return -9;
+  if (max_iter < 0) return -10;
+  if (iters) *iters = 0;
+  if (scaled_resid) *scaled_resid = 0.0;
+  if (n == 0 || nrhs == 0) return LU_OK;
+  int rc = ensure_info(f);
+  if (rc) return rc;
+  rc = ensure_vec_ws(f, nrhs);
+  if (rc) return rc;
+  lu_ctx c = f->ctx;
+  cudaStream_t st = c->stream;
+  double* R = f->vec_ws;
+  double* D = R + (size_t)n * nrhs;
+  double* partial = D + (size_t)n * nrhs;
+  // ||A||_inf once
+  CU_TRY(PHASE(c, PH_RESID, 2, launch_norm_inf(dA, lda, n, partial, c->d_small, st)));
+  CU_TRY(cudaMemcpyAsync(c->h_norms, c->d_small, sizeof(double), cudaMemcpyDeviceToHost, st));
+  // x0 = solve(b)
+  rc = solve_chunks(f, nrhs, dB, ldb, dX, ldx);
+  if (rc) return rc;
+  int it = 0;
+  double worst = 0.0;
+  int result = LU_OK;
+  while (true) {
+    // r = b - A x per chunk, norms -> host
+    worst = 0.0;
+    int nactive = 0;
+    for (int q0 = 0; q0 < nrhs; q0 += 32) {
+      const int nr = (nrhs - q0) < 32 ? (nrhs - q0) : 32;
+      rc = residual_chunk(c, n, nr, dA, lda, dX + (int64_t)q0 * ldx, ldx, dB + (int64_t)q0 * ldb, ldb,
+                          R + (size_t)q0 * n, n, partial);
+      if (rc) return rc;
+      rc = read_status(c);  // synchronizes
+      if (rc) return rc;
+      const double an = c->h_norms[0];
+      for (int q = 0; q < nr; ++q) {
+        const double s = hpl_scaled(n, c->h_norms[4 + q], an, c->h_norms[4 + nr + q], c->h_norms[4 + 2 * nr + q]);
+        if (!(s < tol)) ++nactive;
+        c->h_pinned[16 + (q0 + q) % 32] = !(s < tol);
+        if (!(s <= worst)) worst = s;
+      }
+      if (it < max_iter) {
+        CU_TRY(cudaMemcpyAsync(c->d_active + 0, c->h_pinned + 16, (size_t)nr * sizeof(int), cudaMemcpyHostToDevice,
+                               st));
+        // d = solve(r) and x += d for the active columns of this chunk
+        bool any = false;
+        for (int q = 0; q < nr; ++q) any = any || c->h_pinned[16 + q];
+        if (any) {
+          rc = solve_chunks(f, nr, R + (size_t)q0 * n, n, D, n);
+          if (rc) return rc;
+          CU_TRY(PHASE(c, PH_OTHER, 1, launch_add_update(dX + (int64_t)q0 * ldx, ldx, D, n, n, nr, c->d_active, st)));
+          CU_TRY(cudaStreamSynchronize(st));  // h_pinned is reused by the next chunk
+        }
+      }
+    }
+    if (nactive == 0) break;
+    if (it >= max_iter) {
+      result = LU_ENOTCONV;
+      break;
+    }
+    ++it;
+  }
+  if (iters) *iters = it;
+  if (scaled_resid) *scaled_resid = worst;
+  return result;
+}
+
+extern "C" int lu_scaled_residual(lu_ctx c, int n, int nrhs, const double* dA, int lda, const double* dX, int ldx,
+                                  const double* dB, int ldb, double* out) {
+  if (!c) return -1;
+  if (n < 0) return -2;
+  if (nrhs < 0) return -3;
+  if (!out) return -10;
+  if (n == 0 || nrhs == 0) return LU_OK;
+  const size_t need = residual_partial_bytes(n, nrhs > 32 ? 32 : nrhs) + 256;
+  void* ws = nullptr;
+  int rc = dalloc(c, &ws, need);
+  if (rc) return rc;
+  double* partial = (double*)ws;
+  rc = LU_OK;
+  if (launch_norm_inf(dA, lda, n, partial, c->d_small, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->h_norms, c->d_small, sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+    rc = LU_ECUDA;
+  for (int q0 = 0; q0 < nrhs && rc == LU_OK; q0 += 32) {
+    const int nr = (nrhs - q0) < 32 ? (nrhs - q0) : 32;
+    rc = residual_chunk(c, n, nr, dA, lda, dX + (int64_t)q0 * ldx, ldx, dB + (int64_t)q0 * ldb, ldb, nullptr, 0,
+                        partial);
+    if (rc) break;
+    rc = read_status(c);
+    if (rc) break;
+    for (int q = 0; q < nr; ++q)
+      out[q0 + q] = hpl_scaled(n, c->h_norms[4 + q], c->h_norms[0], c->h_norms[4 + nr + q], c->h_norms[4 + 2 * nr + q]);
+  }
+  dfree(c, ws);
+  return rc;
+}
+
+// ------------------------------------------------------------------ step-level entry points
+static int ensure_step_ws(lu_ctx c, size_t bytes) {
+  if (c->step_ws_bytes >= bytes) return LU_OK;
+  cudaStreamSynchronize(c->stream);
+  if (c->step_ws) cudaFree(c->step_ws);
+  c->step_ws = nullptr;
+  c->step_ws_bytes = 0;
+  if (cudaMalloc(&c->step_ws, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return LU_ENOMEM;
+  }
+  c->step_ws_bytes = bytes;
+  return LU_OK;
+}
+
+extern "C" int lu_step_panel(lu_ctx c, lu_prec prec, int m, int w, void* dP, int ld, int* dIpiv, int* dInfo) {
+  if (!c) return -1;
+  if (prec < LU_F64 || prec > LU_F32) return -2;
+  if (m < 1) return -3;
+  if (w < 1 || w > m || w > 512) return -4;
+  if (!dP) return -5;
+  if (ld < w) return -6;
+  if (!dIpiv) return -7;
+  if (!dInfo) return -8;
+  const int tsize = prec == LU_F64 ? 8 : 4;
+  const int gmax = c->dev.sm_count;
+  const size_t pbytes = panel_scratch_bytes(gmax, 32, w, tsize);
+  int rc = ensure_step_ws(c, pbytes);
+  if (rc) return rc;
+  PanelScratch ps;
+  panel_scratch_carve(&ps, c->step_ws, gmax, 32, w, tsize);
+  CU_TRY(cudaMemsetAsync(dInfo, 0x7f, sizeof(int), c->stream));
+  if (prec == LU_F64)
+    CU_TRY(launch_panel<double>((double*)dP, ld, m, w, 0, dIpiv, dInfo, c->d_status, ps, c->dev, c->stream));
+  else
+    CU_TRY(launch_panel<float>((float*)dP, ld, m, w, 0, dIpiv, dInfo, c->d_status, ps, c->dev, c->stream));
+  // info: sentinel -> 0
+  CU_TRY(cudaMemcpyAsync(c->h_pinned + 9, dInfo, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CU_TRY(cudaStreamSynchronize(c->stream));
+  if (c->h_pinned[9] == 0x7f7f7f7f) CU_TRY(cudaMemsetAsync(dInfo, 0, sizeof(int), c->stream));
+  return LU_OK;
+}
+
+extern "C" int lu_step_trsm(lu_ctx c, lu_prec prec, int w, int N, const void* dL, int ldl, void* dX, int ldx) {
+  if (!c) return -1;
+  if (prec < LU_F64 || prec > LU_F32) return -2;
+  if (w < 1 || w > 512) return -3;
+  if (N < 0) return -4;
+  if (!dL) return -5;
+  if (!dX && N > 0) return -7;
+  if (ldl != ldx) return -6;  // the kernel shares one row stride
+  if (prec == LU_F64)
+    CU_TRY(launch_trsm_lower<double>((const double*)dL, (double*)dX, ldx, w, N, c->stream));
+  else
+    CU_TRY(launch_trsm_lower<float>((const float*)dL, (float*)dX, ldx, w, N, c->stream));
+  return LU_OK;
+}
+
+extern "C" int lu_step_gemm(lu_ctx c, lu_prec prec, int m, int n, int k, void* dC, int ldc, const void* dA, int lda,
+                            const void* dB, int ldb) {
+  if (!c) return -1;
+  if (prec < LU_F64 || prec > LU_F32) return -2;
+  if (m < 0) return -3;
+  if (n < 0) return -4;
+  if (k < 0) return -5;
+  if (m == 0 || n == 0 || k == 0) return LU_OK;
+  if (prec == LU_F64) {
+    CU_TRY(launch_gemm_simt<double>((double*)dC, ldc, (const double*)dA, lda, (const double*)dB, ldb, m, n, k,
+                                    c->stream));
+    return LU_OK;
+  }
+  if (prec == LU_F32) {
+    CU_TRY(launch_gemm_simt<float>((float*)dC, ldc, (const float*)dA, lda, (const float*)dB, ldb, m, n, k, c->stream));
+    return LU_OK;
+  }
+  // tensor-core path: the cast kernel reads A (m x k) and B (k x n) with one
+  // row stride, so the operands are first packed into one strided buffer
+  if (lda != ldb) return -9;
+  const int kpad = round_up(k, 64);
+  const size_t abytes = ((size_t)m * kpad * 2 + 1023) / 1024 * 1024;
+  const size_t bbytes = ((size_t)n * kpad * 2 + 1023) / 1024 * 1024;
+  int rc = ensure_step_ws(c, abytes + bbytes);
+  if (rc) return rc;
+  void* aop = c->step_ws;
+  void* bop = (char*)c->step_ws + abytes;
+  const int kind = prec == LU_BF16 ? 1 : 2;
+  CU_TRY(launch_cast_operands(kind, (const float*)dA, (const float*)dB, lda, m, n, k, aop, bop, kpad, c->d_status,
+                              c->stream));
+  CU_TRY(tc_gemm_run(kind, (float*)dC, ldc, aop, bop, m, n, kpad, c->d_status, c->dev, c->stream));
+  return LU_OK;
+}

@@ -1,0 +1,572 @@
+// Panel factorization with partial pivoting, row interchanges (laswp), the
+// top-block triangular solve (trsm) and the layout conversions.
+//
+// Method: the paper's blocked right-looking LU (arxiv 2202.13995, section
+// "Base Implementation", figure "lu_iteration") factors the diagonal block,
+// then updates the "top" blocks with L and the "left" blocks with U.  With
+// partial pivoting the pivot of a column is searched over every row below the
+// diagonal, so the diagonal block and the left blocks are factored together
+// as one m x w panel here (LAPACK's dgetrf structure).
+//
+// The working matrix W is row-major (see kernels.h).
+#include <climits>
+#include <cstdio>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace gb {
+
+template <typename T>
+__device__ __forceinline__ T tabs(T v) {
+  return v < T(0) ? -v : v;
+}
+
+// ============================================================ panel getrf
+//
+// One cooperative launch factors the whole panel.  CTA c owns the contiguous
+// rows [c*R, c*R + R) of the panel.  The panel is processed in sub-panels of
+// ib (<= 32) columns; a sub-panel's rows are held in shared memory, so each
+// column step costs one grid barrier:
+//   1. every CTA finds the first row of largest |a| among its rows >= j and
+//      publishes (|a|, row) and that row's sub-panel values;
+//   2. grid barrier;
+//   3. every CTA reduces the G candidates (largest |a|, then lowest row) to
+//      the pivot p, swaps rows j and p inside its tile where it owns them,
+//      scales its column entries below j by 1/pivot (a division, as in the
+//      definition) and applies the rank-1 update to the sub-panel columns.
+// After a sub-panel, its interchanges are applied to the other panel columns,
+// the sub-panel's L block solves the top rows of the panel columns to its
+// right, and every CTA updates its own rows of those columns (a rank-ib GEMM).
+
+constexpr int PNL_THREADS = 256;
+constexpr int PNL_WARPS = PNL_THREADS / 32;
+constexpr int PNL_IB = 32;
+
+template <typename T>
+struct PanelParams {
+  T* A;  // W(k, k)
+  int64_t ld;
+  int m, w, ib, R, G;
+  int kabs;
+  int* ipiv;  // absolute ipiv array (entries kabs .. kabs + w written)
+  int* info;
+  int* status;
+  unsigned* bar;
+  T* xval;
+  int* xidx;
+  T* xrow;
+  T* xrowj;
+  int* perm;
+};
+
+__host__ __device__ inline size_t panel_smem_bytes(int R, int ib, int w, int tsize) {
+  const int Rs = R | 1;
+  size_t tcount = (size_t)ib * Rs + 2 * ib + (size_t)ib * ib + (size_t)ib * 32 + 2 * (size_t)ib * 32 + PNL_WARPS;
+  size_t icount = PNL_WARPS + ib + 4 * (size_t)w + 4 * (size_t)ib + 8;
+  return tcount * tsize + icount * sizeof(int) + 16;
+}
+
+// Swap, in a row-permutation record, the contents of slot sa with the slot of
+// position p (appending p as a new slot when it is not yet recorded).
+// pos[s]: a row position; cur[s]: the original position whose row now sits at
+// pos[s].  Positions [base, lim) map to slots [0, lim - base) directly.
+// Executed by one full warp.
+__device__ __forceinline__ void perm_swap(int* pos, int* cur, int* cnt, int sa, int p, int base, int lim,
+                                          int lane) {
+  int sb;
+  if (p < lim) {
+    sb = p - base;
+  } else {
+    const int ndirect = lim - base;
+    const int n = *cnt;
+    sb = -1;
+    for (int s0 = ndirect; s0 < n; s0 += 32) {
+      const int s = s0 + lane;
+      const unsigned hit = __ballot_sync(0xffffffffu, s < n && pos[s] == p);
+      if (hit) {
+        sb = s0 + __ffs(hit) - 1;
+        break;
+      }
+    }
+    if (sb < 0) {
+      sb = n;
+      if (lane == 0) {
+        pos[n] = p;
+        cur[n] = p;
+        *cnt = n + 1;
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    const int t = cur[sa];
+    cur[sa] = cur[sb];
+    cur[sb] = t;
+  }
+  __syncwarp();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int cta = blockIdx.x;
+  const int G = P.G, R = P.R, Rs = R | 1, ib = P.ib, w = P.w;
+  const int64_t ld = P.ld;
+  const int row0 = cta * R;
+  const int rloc = max(0, min(P.m, row0 + R) - row0);
+
+  T* S = reinterpret_cast<T*>(smem_raw);  // [ib][Rs]: column t of the tile, row r
+  T* prow = S + (size_t)ib * Rs;          // pivot row (sub-panel columns)
+  T* rjv = prow + ib;                     // row j before the swap
+  T* Lsub = rjv + ib;                     // [ib][ib] unit-lower block of the sub-panel
+  T* Ust = Lsub + ib * ib;                // [ib][32] U rows for the in-panel update
+  T* stage = Ust + ib * 32;               // [2*ib][32] interchange staging
+  T* redv = stage + 2 * ib * 32;          // [PNL_WARPS]
+  int* redi = reinterpret_cast<int*>(redv + PNL_WARPS);
+  int* spiv = redi + PNL_WARPS;  // [ib]
+  int* fpos = spiv + ib;         // [2w] whole-panel permutation record
+  int* fcur = fpos + 2 * w;
+  int* spos = fcur + 2 * w;      // [2ib] sub-panel permutation record
+  int* scur = spos + 2 * ib;
+  int* misc = scur + 2 * ib;     // 0: fcnt 1: scnt 2: barrier flag 3: local best row 4: pivot row
+  const GridBarrier gbar{P.bar, (unsigned)G};
+
+  for (int s = tid; s < w; s += PNL_THREADS) {
+    fpos[s] = s;
+    fcur[s] = s;
+  }
+  if (tid == 0) misc[0] = w;
+  __syncthreads();
+
+  for (int j0 = 0; j0 < w; j0 += ib) {
+    const int ibs = min(ib, w - j0);
+    for (int r = warp; r < rloc; r += PNL_WARPS)
+      if (lane < ibs) S[lane * Rs + r] = __ldcg(P.A + (int64_t)(row0 + r) * ld + j0 + lane);
+    for (int s = tid; s < ibs; s += PNL_THREADS) {
+      spos[s] = j0 + s;
+      scur[s] = j0 + s;
+    }
+    if (tid == 0) misc[1] = ibs;
+    __syncthreads();
+
+    for (int j = 0; j < ibs; ++j) {
+      const int jg = j0 + j;
+      const int par = jg & 1;
+      // ---- 1. local pivot candidate
+      T bv = T(-1);
+      int bi = INT_MAX;
+      for (int r = tid; r < rloc; r += PNL_THREADS) {
+        const int gi = row0 + r;
+        if (gi >= jg) {
+          const T v = tabs(S[j * Rs + r]);
+          if (v != v) atomicOr(P.status, ST_RANGE);
+          argmax_merge(bv, bi, v, gi);
+        }
+      }
+      warp_argmax(bv, bi);
+      if (lane == 0) {
+        redv[warp] = bv;
+        redi[warp] = bi;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        bv = lane < PNL_WARPS ? redv[lane] : T(-1);
+        bi = lane < PNL_WARPS ? redi[lane] : INT_MAX;
+        warp_argmax(bv, bi);
+        if (lane == 0) {
+          misc[3] = bi;
+          P.xval[par * G + cta] = bv;
+          P.xidx[par * G + cta] = bi;
+        }
+      }
+      __syncthreads();
+      bi = misc[3];
+      if (bi != INT_MAX && tid < ibs) P.xrow[((int64_t)par * G + cta) * ib + tid] = S[tid * Rs + (bi - row0)];
+      if (jg >= row0 && jg < row0 + rloc && tid < ibs) P.xrowj[par * ib + tid] = S[tid * Rs + (jg - row0)];
+      // ---- 2. exchange
+      if (!grid_sync(gbar, P.status, &misc[2])) return;
+      // ---- 3. pivot = best candidate over all CTAs
+      bv = T(-1);
+      bi = INT_MAX;
+      for (int c = tid; c < G; c += PNL_THREADS) argmax_merge(bv, bi, __ldcg(P.xval + par * G + c), __ldcg(P.xidx + par * G + c));
+      warp_argmax(bv, bi);
+      if (lane == 0) {
+        redv[warp] = bv;
+        redi[warp] = bi;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        bv = lane < PNL_WARPS ? redv[lane] : T(-1);
+        bi = lane < PNL_WARPS ? redi[lane] : INT_MAX;
+        warp_argmax(bv, bi);
+        if (lane == 0) misc[4] = bi;
+      }
+      __syncthreads();
+      const int p = misc[4];
+      const int owner_p = p / R;
+      if (tid < ibs) {
+        prow[tid] = __ldcg(P.xrow + ((int64_t)par * G + owner_p) * ib + tid);
+        rjv[tid] = __ldcg(P.xrowj + par * ib + tid);
+      }
+      __syncthreads();
+      if (tid < ibs) {
+        if (p != jg && p >= row0 && p < row0 + rloc) S[tid * Rs + (p - row0)] = rjv[tid];
+        if (jg >= row0 && jg < row0 + rloc) S[tid * Rs + (jg - row0)] = prow[tid];
+      }
+      if (warp == 0) {
+        if (lane == 0) {
+          spiv[j] = p;
+          if (cta == 0) {
+            P.ipiv[P.kabs + jg] = P.kabs + p + 1;
+            if (prow[j] == T(0)) atomicMin(P.info, P.kabs + jg + 1);
+          }
+        }
+        if (p != jg) {
+          perm_swap(fpos, fcur, &misc[0], jg, p, 0, w, lane);
+          perm_swap(spos, scur, &misc[1], jg - j0, p, j0, j0 + ibs, lane);
+        }
+      }
+      __syncthreads();
+      // ---- 4. scale the column below the pivot, rank-1 update of the sub-panel
+      const T piv = prow[j];
+      for (int r = tid; r < rloc; r += PNL_THREADS) {
+        const int gi = row0 + r;
+        if (gi > jg) {
+          T l = S[j * Rs + r];
+          if (piv != T(0)) l = l / piv;
+          S[j * Rs + r] = l;
+          for (int c = j + 1; c < ibs; ++c) S[c * Rs + r] -= l * prow[c];
+        }
+      }
+      __syncthreads();
+    }
+
+    // ---- sub-panel done: write the tile back
+    for (int r = warp; r < rloc; r += PNL_WARPS)
+      if (lane < ibs) P.A[(int64_t)(row0 + r) * ld + j0 + lane] = S[lane * Rs + r];
+    if (!grid_sync(gbar, P.status, &misc[2])) return;
+
+    // ---- interchanges of this sub-panel on the other panel columns, and the
+    //      top-row triangular solve of the columns to its right
+    const int nout = w - ibs;
+    const int scnt = misc[1];
+    const int nchunk = (nout + 31) / 32;
+    if (nchunk > 0 && cta < nchunk) {
+      for (int e = tid; e < ibs * ibs; e += PNL_THREADS) {
+        const int t = e / ibs, s = e % ibs;
+        Lsub[t * ib + s] = __ldcg(P.A + (int64_t)(j0 + t) * ld + j0 + s);
+      }
+      __syncthreads();
+    }
+    for (int q = cta; q < nchunk; q += G) {
+      const int o = q * 32 + lane;
+      const int c = o < j0 ? o : o + ibs;
+      for (int s = warp; s < scnt; s += PNL_WARPS)
+        if (o < nout) stage[s * 32 + lane] = __ldcg(P.A + (int64_t)scur[s] * ld + c);
+      __syncthreads();
+      for (int s = warp; s < scnt; s += PNL_WARPS)
+        if (o < nout) P.A[(int64_t)spos[s] * ld + c] = stage[s * 32 + lane];
+      __syncthreads();
+      if (warp == 0 && o < nout && o >= j0) {
+        // forward substitution with the unit-lower sub-panel block; the
+        // column lives in the (now free) staging area, lane = column
+        T* xs = stage;
+        for (int t = 0; t < ibs; ++t) xs[t * 32 + lane] = __ldcg(P.A + (int64_t)(j0 + t) * ld + c);
+        for (int t = 1; t < ibs; ++t) {
+          T v = xs[t * 32 + lane];
+          for (int s = 0; s < t; ++s) v -= Lsub[t * ib + s] * xs[s * 32 + lane];
+          xs[t * 32 + lane] = v;
+        }
+        for (int t = 0; t < ibs; ++t) P.A[(int64_t)(j0 + t) * ld + c] = xs[t * 32 + lane];
+      }
+      __syncthreads();
+    }
+    if (j0 + ibs < w) {
+      if (!grid_sync(gbar, P.status, &misc[2])) return;
+      // ---- rank-ibs update of own rows below the sub-panel, columns to its right
+      const int c0 = j0 + ibs;
+      for (int cc = c0; cc < w; cc += 32) {
+        const int cw = min(32, w - cc);
+        for (int t = warp; t < ibs; t += PNL_WARPS)
+          if (lane < cw) Ust[t * 32 + lane] = __ldcg(P.A + (int64_t)(j0 + t) * ld + cc + lane);
+        __syncthreads();
+        for (int r = warp; r < rloc; r += PNL_WARPS) {
+          const int gi = row0 + r;
+          if (gi >= c0 && lane < cw) {
+            T a = __ldcg(P.A + (int64_t)gi * ld + cc + lane);
+            for (int t = 0; t < ibs; ++t) a -= S[t * Rs + r] * Ust[t * 32 + lane];
+            P.A[(int64_t)gi * ld + cc + lane] = a;
+          }
+        }
+        __syncthreads();
+      }
+    }
+  }
+  // ---- whole-panel permutation for the row interchanges outside the panel
+  if (cta == 0) {
+    const int fcnt = misc[0];
+    if (tid == 0) P.perm[0] = fcnt;
+    for (int s = tid; s < fcnt; s += PNL_THREADS) {
+      P.perm[1 + s] = fpos[s];
+      P.perm[1 + 2 * w + s] = fcur[s];
+    }
+  }
+}
+
+size_t panel_scratch_bytes(int gmax, int ibmax, int wmax, int tsize) {
+  size_t b = 64;                                   // barrier
+  b += 2 * (size_t)gmax * tsize + 256;             // xval
+  b += 2 * (size_t)gmax * sizeof(int) + 256;       // xidx
+  b += 2 * (size_t)gmax * ibmax * tsize + 256;     // xrow
+  b += 2 * (size_t)ibmax * tsize + 256;            // xrowj
+  b += (1 + 4 * (size_t)wmax) * sizeof(int) + 256; // perm
+  return b;
+}
+
+static inline char* align_up(char* p, size_t a) { return (char*)(((uintptr_t)p + a - 1) / a * a); }
+
+void panel_scratch_carve(PanelScratch* s, void* base, int gmax, int ibmax, int wmax, int tsize) {
+  char* p = (char*)base;
+  s->bar = (unsigned*)p;
+  p += 64;
+  s->xval = p;
+  p = align_up(p + 2 * (size_t)gmax * tsize, 256);
+  s->xidx = (int*)p;
+  p = align_up(p + 2 * (size_t)gmax * sizeof(int), 256);
+  s->xrow = p;
+  p = align_up(p + 2 * (size_t)gmax * ibmax * tsize, 256);
+  s->xrowj = p;
+  p = align_up(p + 2 * (size_t)ibmax * tsize, 256);
+  s->perm = (int*)p;
+  s->gmax = gmax;
+  s->ibmax = ibmax;
+  s->wmax = wmax;
+}
+
+template <typename T>
+cudaError_t launch_panel(T* Wkk, int64_t ldw, int m, int w, int kabs, int* ipiv, int* info, int* status,
+                         const PanelScratch& s, const DevInfo& dev, cudaStream_t st) {
+  if (w <= 0 || m < w || w > s.wmax) return cudaErrorInvalidValue;
+  const int ib = PNL_IB < s.ibmax ? PNL_IB : s.ibmax;
+  // rows per CTA: at least 64 (fewer CTAs on short panels), at most what the
+  // co-resident grid needs
+  static int occ_cache[2][64] = {};
+  int R = 64;
+  int gcap = dev.sm_count < s.gmax ? dev.sm_count : s.gmax;
+  if ((int64_t)R * gcap < m) R = (int)cdiv(m, gcap);
+  size_t smem = panel_smem_bytes(R, ib, w, sizeof(T));
+  if (smem > (size_t)dev.max_smem_optin) return cudaErrorInvalidConfiguration;
+  auto kern = panel_getrf_kernel<T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PNL_THREADS, smem);
+  if (e != cudaSuccess) return e;
+  (void)occ_cache;
+  const int G = (int)cdiv(m, R);
+  if (per_sm < 1 || G > per_sm * dev.sm_count || G > s.gmax) return cudaErrorCooperativeLaunchTooLarge;
+  e = cudaMemsetAsync(s.bar, 0, 2 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  PanelParams<T> P;
+  P.A = Wkk;
+  P.ld = ldw;
+  P.m = m;
+  P.w = w;
+  P.ib = ib;
+  P.R = R;
+  P.G = G;
+  P.kabs = kabs;
+  P.ipiv = ipiv;
+  P.info = info;
+  P.status = status;
+  P.bar = s.bar;
+  P.xval = (T*)s.xval;
+  P.xidx = s.xidx;
+  P.xrow = (T*)s.xrow;
+  P.xrowj = (T*)s.xrowj;
+  P.perm = s.perm;
+  void* args[] = {&P};
+  return cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(PNL_THREADS), args, smem, st);
+}
+
+// ============================================================ laswp
+// Apply a panel's net row permutation (count c, dst positions, src positions;
+// relative to row k) to columns [0, k) and [k + w, n) of W.  CTA q handles a
+// chunk of CW consecutive columns: it stages every source row segment in
+// shared memory, then writes them to their destinations (so that sources are
+// read before any destination is overwritten).  Block 0 also permutes rowid.
+
+template <typename T>
+__global__ void __launch_bounds__(256) laswp_kernel(T* W, int64_t ldw, int n, int k, int w, const int* perm,
+                                                     int* rowid) {
+  constexpr int CW = 128 / sizeof(T);  // columns per chunk: one 128-byte row segment
+  constexpr int RPP = 256 / CW;        // row segments per pass
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* stage = reinterpret_cast<T*>(smem_raw);
+  const int cnt = perm[0];
+  const int* dst = perm + 1;
+  const int* src = perm + 1 + 2 * w;
+  const int nout = n - w;
+  const int o = blockIdx.x * CW + (threadIdx.x % CW);
+  const int rsub = threadIdx.x / CW;
+  const int c = o < k ? o : o + w;
+  for (int s = rsub; s < cnt; s += RPP)
+    if (o < nout) stage[s * CW + (threadIdx.x % CW)] = W[(int64_t)(k + src[s]) * ldw + c];
+  if (blockIdx.x == 0 && rowid != nullptr) {
+    int* istage = reinterpret_cast<int*>(stage + (size_t)2 * w * CW);
+    for (int s = threadIdx.x; s < cnt; s += 256) istage[s] = rowid[k + src[s]];
+    __syncthreads();
+    for (int s = threadIdx.x; s < cnt; s += 256) rowid[k + dst[s]] = istage[s];
+  }
+  __syncthreads();
+  for (int s = rsub; s < cnt; s += RPP)
+    if (o < nout) W[(int64_t)(k + dst[s]) * ldw + c] = stage[s * CW + (threadIdx.x % CW)];
+}
+
+template <typename T>
+cudaError_t launch_laswp(T* W, int64_t ldw, int n, int k, int w, const int* perm, int* rowid, cudaStream_t st) {
+  constexpr int CW = 128 / sizeof(T);
+  const int nout = n - w;
+  const int blocks = nout > 0 ? (int)cdiv(nout, CW) : 1;
+  const size_t smem = (size_t)2 * w * CW * sizeof(T) + 2 * (size_t)w * sizeof(int) + 16;
+  auto kern = laswp_kernel<T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  laswp_kernel<T><<<blocks, 256, smem, st>>>(W, ldw, n, k, w, perm, rowid);
+  return cudaGetLastError();
+}
+
+// ============================================================ trsm (top blocks)
+// U12 <- L11^-1 A12 for the unit-lower w x w block L11 (the paper's "top"
+// block update).  CTA = a strip of 32 columns of A12 held in shared memory
+// (lane = column).  Blocked by 32 rows: warp 0 solves a 32 x 32 diagonal
+// block by substitution, then all warps apply it to the rows below.
+
+template <typename T>
+__global__ void __launch_bounds__(256) trsm_lower_kernel(const T* L, T* X, int64_t ldw, int w, int N) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Xs = reinterpret_cast<T*>(smem_raw);  // [w][32]
+  T* Ld = Xs + (size_t)w * 32;             // [32][33]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
+  const bool cok = c < N;
+  for (int r = warp; r < w; r += 8) Xs[r * 32 + lane] = cok ? X[(int64_t)r * ldw + c] : T(0);
+  for (int b0 = 0; b0 < w; b0 += 32) {
+    const int bw = min(32, w - b0);
+    for (int e = threadIdx.x; e < bw * 32; e += 256) {
+      const int t = e >> 5, s = e & 31;
+      Ld[t * 33 + s] = (s < bw) ? L[(int64_t)(b0 + t) * ldw + b0 + s] : T(0);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      T x[32];
+#pragma unroll
+      for (int t = 0; t < 32; ++t) x[t] = (t < bw) ? Xs[(b0 + t) * 32 + lane] : T(0);
+#pragma unroll
+      for (int t = 1; t < 32; ++t) {
+        T v = x[t];
+#pragma unroll
+        for (int s = 0; s < 32; ++s)
+          if (s < t) v -= Ld[t * 33 + s] * x[s];
+        x[t] = v;
+      }
+#pragma unroll
+      for (int t = 0; t < 32; ++t)
+        if (t < bw) Xs[(b0 + t) * 32 + lane] = x[t];
+    }
+    __syncthreads();
+    for (int r = b0 + bw + warp; r < w; r += 8) {
+      const T lv = lane < bw ? L[(int64_t)r * ldw + b0 + lane] : T(0);
+      T acc = Xs[r * 32 + lane];
+      for (int t = 0; t < bw; ++t) acc -= __shfl_sync(0xffffffffu, lv, t) * Xs[(b0 + t) * 32 + lane];
+      Xs[r * 32 + lane] = acc;
+    }
+    __syncthreads();
+  }
+  if (cok)
+    for (int r = warp; r < w; r += 8) X[(int64_t)r * ldw + c] = Xs[r * 32 + lane];
+}
+
+template <typename T>
+cudaError_t launch_trsm_lower(const T* L11, T* A12, int64_t ldw, int w, int N, cudaStream_t st) {
+  if (N <= 0) return cudaSuccess;
+  const size_t smem = ((size_t)w * 32 + 32 * 33) * sizeof(T);
+  auto kern = trsm_lower_kernel<T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  trsm_lower_kernel<T><<<(int)cdiv(N, 32), 256, smem, st>>>(L11, A12, ldw, w, N);
+  return cudaGetLastError();
+}
+
+// ============================================================ layout conversions
+template <typename T>
+__global__ void to_working_kernel(const double* __restrict__ A, int64_t lda, T* __restrict__ W, int64_t ldw, int n) {
+  __shared__ double tile[32][33];
+  const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  for (int jj = ty; jj < 32; jj += 8) {
+    const int i = bi + tx, j = bj + jj;
+    tile[jj][tx] = (i < n && j < n) ? A[(int64_t)j * lda + i] : 0.0;
+  }
+  __syncthreads();
+  for (int ii = ty; ii < 32; ii += 8) {
+    const int i = bi + ii, j = bj + tx;
+    if (i < n && j < n) W[(int64_t)i * ldw + j] = (T)tile[tx][ii];
+  }
+}
+
+template <typename T>
+__global__ void from_working_kernel(const T* __restrict__ W, int64_t ldw, double* __restrict__ LU, int64_t ldlu,
+                                    int n) {
+  __shared__ double tile[32][33];
+  const int bi = blockIdx.y * 32, bj = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int ii = ty; ii < 32; ii += 8) {
+    const int i = bi + ii, j = bj + tx;
+    tile[ii][tx] = (i < n && j < n) ? (double)W[(int64_t)i * ldw + j] : 0.0;
+  }
+  __syncthreads();
+  for (int jj = ty; jj < 32; jj += 8) {
+    const int i = bi + tx, j = bj + jj;
+    if (i < n && j < n) LU[(int64_t)j * ldlu + i] = tile[tx][jj];
+  }
+}
+
+template <typename T>
+cudaError_t launch_to_working(const double* A, int64_t lda, T* W, int64_t ldw, int n, cudaStream_t st) {
+  dim3 grid((unsigned)cdiv(n, 32), (unsigned)cdiv(n, 32));
+  to_working_kernel<T><<<grid, dim3(32, 8), 0, st>>>(A, lda, W, ldw, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_from_working(const T* W, int64_t ldw, double* LU, int64_t ldlu, int n, cudaStream_t st) {
+  dim3 grid((unsigned)cdiv(n, 32), (unsigned)cdiv(n, 32));
+  from_working_kernel<T><<<grid, dim3(32, 8), 0, st>>>(W, ldw, LU, ldlu, n);
+  return cudaGetLastError();
+}
+
+__global__ void iota_kernel(int* v, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = i;
+}
+
+cudaError_t launch_iota(int* v, int n, cudaStream_t st) {
+  iota_kernel<<<(int)cdiv(n, 256), 256, 0, st>>>(v, n);
+  return cudaGetLastError();
+}
+
+#define GB_INST(T)                                                                                              \
+  template cudaError_t launch_panel<T>(T*, int64_t, int, int, int, int*, int*, int*, const PanelScratch&,      \
+                                       const DevInfo&, cudaStream_t);                                           \
+  template cudaError_t launch_laswp<T>(T*, int64_t, int, int, int, const int*, int*, cudaStream_t);            \
+  template cudaError_t launch_trsm_lower<T>(const T*, T*, int64_t, int, int, cudaStream_t);                    \
+  template cudaError_t launch_to_working<T>(const double*, int64_t, T*, int64_t, int, cudaStream_t);           \
+  template cudaError_t launch_from_working<T>(const T*, int64_t, double*, int64_t, int, cudaStream_t);
+GB_INST(double)
+GB_INST(float)
+#undef GB_INST
+
+}  // namespace gb

@@ -1,0 +1,298 @@
+"""Thin ctypes binding of libgb300lu.so (the C ABI in include/lu.h and lu_steps.h).
+
+Only argument marshalling happens here: every step of the solve runs in the
+library's CUDA kernels.  PyTorch supplies device memory and the stream.  The
+binding refuses to work without the compiled library (there is no fallback).
+
+Matrices are torch CUDA tensors.  The C ABI is column-major: an (n, n) FP64
+tensor with strides (1, lda) is passed as is; the step-level entry points take
+row-major tensors (strides (ld, 1)).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+import weakref
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgb300lu.so")
+
+LU_F64, LU_BF16, LU_FP16, LU_F32 = 0, 1, 2, 3
+PRECS = {"f64": LU_F64, "bf16": LU_BF16, "fp16": LU_FP16, "f32": LU_F32}
+LU_OK, LU_ESINGULAR, LU_ENOMEM, LU_ENOTCONV, LU_ERANGE, LU_ETIMEOUT, LU_EAGAIN, LU_ECUDA, LU_EINTERNAL = range(9)
+
+EXPORTED = [
+    "lu_create", "lu_destroy", "lu_strerror", "lu_factor", "lu_fact_info", "lu_fact_ipiv", "lu_fact_lu",
+    "lu_solve", "lu_refine", "lu_scaled_residual", "lu_fact_free",
+    "lu_step_panel", "lu_step_trsm", "lu_step_gemm", "lu_ctx_status", "lu_device_sm_count", "lu_build_tag",
+    "lu_profile_enable", "lu_profile_read", "lu_launch_count",
+]
+PHASES = ["panel", "laswp", "trsm", "cast", "gemm", "solve", "residual", "other"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class LuError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = _lib.lu_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} (code {code})" if what else f"{msg} (code {code})")
+
+
+def load():
+    """Load the library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(the solver has no CPU fallback)")
+        lib = C.CDLL(LIB_PATH)
+        P, I, D = C.c_void_p, C.c_int, C.c_double
+        PP = C.POINTER(C.c_void_p)
+        IP = C.POINTER(C.c_int)
+        DP = C.POINTER(C.c_double)
+        sig = {
+            "lu_create": (I, [PP, P]),
+            "lu_destroy": (None, [P]),
+            "lu_strerror": (C.c_char_p, [I]),
+            "lu_factor": (I, [P, I, P, I, I, I, PP, IP]),
+            "lu_fact_info": (I, [P, IP]),
+            "lu_fact_ipiv": (I, [P, P]),
+            "lu_fact_lu": (I, [P, P, I]),
+            "lu_solve": (I, [P, I, P, I]),
+            "lu_refine": (I, [P, P, I, P, I, P, I, I, D, I, IP, DP]),
+            "lu_scaled_residual": (I, [P, I, I, P, I, P, I, P, I, DP]),
+            "lu_fact_free": (None, [P]),
+            "lu_step_panel": (I, [P, I, I, I, P, I, P, P]),
+            "lu_step_trsm": (I, [P, I, I, I, P, I, P, I]),
+            "lu_step_gemm": (I, [P, I, I, I, I, P, I, P, I, P, I]),
+            "lu_ctx_status": (I, [P]),
+            "lu_device_sm_count": (I, [P]),
+            "lu_build_tag": (C.c_char_p, []),
+            "lu_profile_enable": (I, [P, I]),
+            "lu_profile_read": (I, [P, DP, C.POINTER(C.c_longlong)]),
+            "lu_launch_count": (C.c_longlong, [P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, what: str):
+    if rc != LU_OK:
+        raise LuError(rc, what)
+
+
+def _prec(p) -> int:
+    return PRECS[p] if isinstance(p, str) else int(p)
+
+
+def _colmajor(t, name: str, rows: int | None = None):
+    """(ptr, ld, ncols) of a column-major CUDA FP64 tensor (1-D = one column)."""
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64):
+        raise TypeError(f"{name}: expected a CUDA float64 tensor")
+    if t.dim() == 1:
+        if t.stride(0) != 1:
+            raise ValueError(f"{name}: 1-D tensor must be contiguous")
+        return t.data_ptr(), max(1, t.shape[0]), 1
+    if t.dim() != 2 or (t.stride(0) != 1 and t.shape[0] > 1):
+        raise ValueError(f"{name}: expected a column-major (n, k) tensor with strides (1, ld)")
+    ld = t.stride(1) if t.shape[1] > 1 else max(1, t.shape[0])
+    return t.data_ptr(), max(1, ld), t.shape[1]
+
+
+def _rowmajor(t, name: str):
+    if not t.is_cuda:
+        raise TypeError(f"{name}: expected a CUDA tensor")
+    if t.dim() != 2 or (t.stride(1) != 1 and t.shape[1] > 1):
+        raise ValueError(f"{name}: expected a row-major (m, n) tensor with strides (ld, 1)")
+    ld = t.stride(0) if t.shape[0] > 1 else max(1, t.shape[1])
+    return t.data_ptr(), max(1, ld)
+
+
+def colmajor_empty(n: int, k: int, device="cuda", dtype=None):
+    """An uninitialised (n, k) column-major tensor (strides (1, n))."""
+    import torch
+    return torch.empty((k, n), dtype=dtype or torch.float64, device=device).t()
+
+
+class Context:
+    """A library context bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, stream=None):
+        import torch
+        lib = load()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        self._h = None
+        self._factors = weakref.WeakSet()
+        _check(lib.lu_create(C.byref(h), C.c_void_p(stream.cuda_stream)), "lu_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        """Free every factorization still alive, then the context."""
+        if getattr(self, "_h", None):
+            for f in list(self._factors):
+                f.free()
+            load().lu_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def sm_count(self) -> int:
+        return load().lu_device_sm_count(self._h)
+
+    def status(self) -> int:
+        return load().lu_ctx_status(self._h)
+
+    def launch_count(self) -> int:
+        return int(load().lu_launch_count(self._h))
+
+    def profile(self, enable: bool = True):
+        _check(load().lu_profile_enable(self._h, 1 if enable else 0), "lu_profile_enable")
+
+    def profile_read(self) -> dict:
+        """{phase: (milliseconds, launches)} since the last read (synchronizes)."""
+        ms = (C.c_double * len(PHASES))()
+        nl = (C.c_longlong * len(PHASES))()
+        _check(load().lu_profile_read(self._h, ms, nl), "lu_profile_read")
+        return {p: (ms[i], int(nl[i])) for i, p in enumerate(PHASES)}
+
+    def factor(self, A, prec="f64", nb: int = 0, sync: bool = True) -> "Factor":
+        """Factor P A = L U of the column-major FP64 (n, n) tensor A."""
+        ptr, lda, ncol = _colmajor(A, "A")
+        n = A.shape[0]
+        if ncol != n:
+            raise ValueError("A must be square")
+        f = C.c_void_p()
+        info = C.c_int(-1)
+        rc = load().lu_factor(self._h, n, C.c_void_p(ptr), lda, _prec(prec), int(nb), C.byref(f),
+                              C.byref(info) if sync else None)
+        if f.value:
+            fac = Factor(self, f, n, _prec(prec))
+            self._factors.add(fac)
+        else:
+            fac = None
+        _check(rc, "lu_factor")
+        if sync:
+            fac._info = info.value
+        return fac
+
+    def scaled_residual(self, A, X, B) -> np.ndarray:
+        pa, lda, _ = _colmajor(A, "A")
+        px, ldx, nrhs = _colmajor(X, "X")
+        pb, ldb, _ = _colmajor(B, "B")
+        out = (C.c_double * max(1, nrhs))()
+        _check(load().lu_scaled_residual(self._h, A.shape[0], nrhs, C.c_void_p(pa), lda, C.c_void_p(px), ldx,
+                                         C.c_void_p(pb), ldb, out), "lu_scaled_residual")
+        return np.array(out[:nrhs])
+
+    # ---- step-level entry points (row-major operands)
+    def step_panel(self, P, ipiv, info, prec="f64"):
+        pp, ld = _rowmajor(P, "P")
+        m, w = P.shape
+        _check(load().lu_step_panel(self._h, _prec(prec), m, w, C.c_void_p(pp), ld, C.c_void_p(ipiv.data_ptr()),
+                                    C.c_void_p(info.data_ptr())), "lu_step_panel")
+
+    def step_trsm(self, L, X, prec="f64"):
+        pl, ldl = _rowmajor(L, "L")
+        px, ldx = _rowmajor(X, "X")
+        w, N = X.shape
+        _check(load().lu_step_trsm(self._h, _prec(prec), w, N, C.c_void_p(pl), ldl, C.c_void_p(px), ldx),
+               "lu_step_trsm")
+
+    def step_gemm(self, Cm, A, B, prec="f64"):
+        pc, ldc = _rowmajor(Cm, "C")
+        pa, lda = _rowmajor(A, "A")
+        pb, ldb = _rowmajor(B, "B")
+        m, k = A.shape
+        n = B.shape[1]
+        _check(load().lu_step_gemm(self._h, _prec(prec), m, n, k, C.c_void_p(pc), ldc, C.c_void_p(pa), lda,
+                                   C.c_void_p(pb), ldb), "lu_step_gemm")
+
+
+class Factor:
+    """A factorization owned by the library (freed by free() or garbage collection)."""
+
+    def __init__(self, ctx: Context, handle, n: int, prec: int):
+        self.ctx = ctx
+        self._h = handle
+        self.n = n
+        self.prec = prec
+        self._info = None
+
+    def free(self):
+        if getattr(self, "_h", None):
+            load().lu_fact_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    @property
+    def info(self) -> int:
+        if self._info is None:
+            v = C.c_int(0)
+            _check(load().lu_fact_info(self._h, C.byref(v)), "lu_fact_info")
+            self._info = v.value
+        return self._info
+
+    def ipiv(self):
+        import torch
+        out = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        _check(load().lu_fact_ipiv(self._h, C.c_void_p(out.data_ptr())), "lu_fact_ipiv")
+        return out
+
+    def lu(self):
+        out = colmajor_empty(self.n, self.n)
+        _check(load().lu_fact_lu(self._h, C.c_void_p(out.data_ptr()), max(1, self.n)), "lu_fact_lu")
+        return out
+
+    def solve_(self, B):
+        """Overwrite B (column-major FP64, (n,) or (n, nrhs)) with the solution."""
+        pb, ldb, nrhs = _colmajor(B, "B")
+        _check(load().lu_solve(self._h, nrhs, C.c_void_p(pb), ldb), "lu_solve")
+        return B
+
+    def refine(self, A, B, X, tol: float = 16.0, max_iter: int = 50, raise_on_notconv: bool = True):
+        """Iterative refinement to HPL scaled residual < tol; returns (iters, scaled residual)."""
+        pa, lda, _ = _colmajor(A, "A")
+        pb, ldb, nrhs = _colmajor(B, "B")
+        px, ldx, _ = _colmajor(X, "X")
+        it = C.c_int(0)
+        sr = C.c_double(0.0)
+        rc = load().lu_refine(self._h, C.c_void_p(pa), lda, C.c_void_p(pb), ldb, C.c_void_p(px), ldx, nrhs,
+                              float(tol), int(max_iter), C.byref(it), C.byref(sr))
+        if rc == LU_ENOTCONV and not raise_on_notconv:
+            return it.value, sr.value
+        _check(rc, "lu_refine")
+        return it.value, sr.value

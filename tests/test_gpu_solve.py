@@ -1,0 +1,216 @@
+"""End-to-end parity of the GPU solve (lu_factor / lu_solve / lu_refine through
+the C ABI) against the CPU oracle, on the seeded HPL-shaped workloads.
+
+Bars (the FP64 oracle decides):
+  - FP64 path: pivots identical to the oracle's; factors and x within a few
+    units of roundoff times the size; HPL scaled residual < 16;
+  - mixed path (BF16/FP16/FP32 factor + FP64 refinement): scaled residual < 16
+    and ||x - x_oracle||_inf / ||x_oracle||_inf <= 1e-10 (well-conditioned A);
+  - full-size cases: properties that hold at any size (scaled residual, the
+    b = A*ones closed form) and the first block step compared with the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2202_13995_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+EPS = 2.0 ** -53
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    from paper_2202_13995_gb300 import lu
+    c = lu.Context()
+    yield c
+    torch.cuda.synchronize()
+    c.close()
+
+
+def _dev(a):
+    import torch
+    from paper_2202_13995_gb300 import lu
+    a = np.asarray(a, dtype=np.float64)
+    if a.ndim == 1:
+        return torch.from_numpy(a.copy()).cuda()
+    t = lu.colmajor_empty(a.shape[0], a.shape[1])
+    t.copy_(torch.from_numpy(np.asfortranarray(a)))
+    return t
+
+
+def _fwd_tol(LU, ipiv, A):
+    kappa = O.cond1_est(LU, ipiv, O.norm_one(A))
+    return max(1e-10, 10 * kappa * EPS), kappa
+
+
+@pytest.mark.parametrize("n,nb", [(1, 64), (2, 64), (3, 1), (63, 64), (64, 64), (65, 64), (129, 32), (500, 64),
+                                  (1500, 256), (2048, 128), (777, 100)])
+def test_factor_solve_f64(ctx, n, nb):
+    A = I.hpl_matrix(n, 40 + n)
+    B = I.hpl_rhs(n, 1, 40 + n)
+    f = ctx.factor(_dev(A), "f64", nb)
+    assert f.info == 0
+    LUo, ipo, info = O.getrf(A, nb)
+    assert info == 0
+    assert np.array_equal(f.ipiv().cpu().numpy(), ipo)
+    LUg = f.lu().cpu().numpy()
+    assert np.abs(LUg - LUo).max() <= 256 * n * EPS * max(1.0, np.abs(LUo).max())
+    x = _dev(B)
+    f.solve_(x)
+    xo = O.getrs(LUo, ipo, B)
+    tol, kappa = _fwd_tol(LUo, ipo, A)
+    xg = x.cpu().numpy()
+    assert np.abs(xg - xo).max() / np.abs(xo).max() <= tol, kappa
+    assert O.scaled_residual(A, xg, B)[0] < 16.0
+    assert ctx.scaled_residual(_dev(A), x, _dev(B))[0] < 16.0
+    assert ctx.status() == 0
+
+
+def test_config0_n1024_nb64(ctx):
+    """The small configuration: n = 1024, nb = 64, A and b uniform[-0.5, 0.5]."""
+    n = 1024
+    A = I.hpl_matrix(n, 1)
+    B = I.hpl_rhs(n, 1, 1)
+    f = ctx.factor(_dev(A), "f64", 64)
+    xo, LUo, ipo, _ = O.solve(A, B, nb=64)
+    assert np.array_equal(f.ipiv().cpu().numpy(), ipo)
+    x = _dev(B)
+    f.solve_(x)
+    tol, _ = _fwd_tol(LUo, ipo, A)
+    assert np.abs(x.cpu().numpy() - xo).max() / np.abs(xo).max() <= tol
+    assert O.scaled_residual(A, x.cpu().numpy(), B)[0] < 16.0
+
+
+@pytest.mark.parametrize("nrhs", [3, 32, 40])
+def test_multi_rhs_f64(ctx, nrhs):
+    n = 700
+    A = I.hpl_matrix(n, 77)
+    B = I.hpl_rhs(n, nrhs, 78)
+    f = ctx.factor(_dev(A), "f64", 64)
+    X = _dev(B)
+    f.solve_(X)
+    Xo, LUo, ipo, _ = O.solve(A, B)
+    tol, _ = _fwd_tol(LUo, ipo, A)
+    Xg = X.cpu().numpy()
+    assert np.abs(Xg - Xo).max() / np.abs(Xo).max() <= tol
+    assert np.all(O.scaled_residual(A, Xg, B) < 16.0)
+
+
+def test_all_ones_closed_form(ctx):
+    """The paper's validation idea: b = A * ones gives x = ones."""
+    n = 1200
+    A = I.hpl_matrix(n, 5)
+    b = O.residual(A, np.ones(n), np.zeros(n)) * -1.0  # b = A * ones, summed by the oracle
+    f = ctx.factor(_dev(A), "f64", 128)
+    x = _dev(b)
+    f.solve_(x)
+    LUo, ipo, _ = O.getrf(A, 128)
+    tol, _ = _fwd_tol(LUo, ipo, A)
+    assert np.abs(x.cpu().numpy() - 1.0).max() <= 10 * tol * n
+
+
+def test_singular(ctx):
+    from paper_2202_13995_gb300 import lu
+    n = 300
+    A = I.hpl_matrix(n, 9)
+    A[:, 150] = 0.0
+    f = ctx.factor(_dev(A), "f64", 64)
+    _, _, info = O.getrf(A, 64)
+    assert f.info == info == 151
+    with pytest.raises(lu.LuError) as e:
+        f.solve_(_dev(np.ones(n)))
+    assert e.value.code == lu.LU_ESINGULAR
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "f32"])
+@pytest.mark.parametrize("n,nrhs", [(256, 1), (1000, 1), (2048, 32), (3000, 5)])
+def test_mixed_refine(ctx, prec, n, nrhs):
+    """Low-precision factor + FP64 refinement reaches the FP64 oracle's x."""
+    A = I.hpl_matrix(n, 60 + n, diag_shift=n / 4)
+    B = I.hpl_rhs(n, nrhs, 61 + n)
+    Ad, Bd = _dev(A), _dev(B)
+    f = ctx.factor(Ad, prec, 0)
+    assert f.info == 0
+    assert np.array_equal(f.ipiv().cpu().numpy(), np.arange(1, n + 1))  # diagonal shift: no interchanges
+    X = _dev(np.zeros((n, nrhs)))
+    iters, res = f.refine(Ad, Bd, X, 16.0, 50)
+    assert res < 16.0 and iters <= 10
+    Xo, _, _, _ = O.solve(A, B)
+    Xg = X.cpu().numpy()
+    assert np.abs(Xg - Xo).max() / np.abs(Xo).max() <= 1e-10
+    assert np.all(O.scaled_residual(A, Xg, B) < 16.0)
+    assert ctx.status() == 0
+
+
+def test_mixed_refine_with_pivoting(ctx):
+    """No diagonal shift: interchanges happen, and refinement still converges."""
+    n = 1024
+    A = I.hpl_matrix(n, 3)
+    B = I.hpl_rhs(n, 2, 4)
+    Ad, Bd = _dev(A), _dev(B)
+    f = ctx.factor(Ad, "fp16", 128)
+    X = _dev(np.zeros((n, 2)))
+    iters, res = f.refine(Ad, Bd, X, 16.0, 50)
+    assert res < 16.0
+    Xo, LUo, ipo, _ = O.solve(A, B)
+    # refinement stops once the scaled residual is below 16, i.e. at a backward
+    # error of up to 16 n u: the forward distance to the oracle's x is then
+    # bounded by about kappa * (16 + 16) * n * u, not by 1e-10 (kappa ~ 1e4 here)
+    kappa = O.cond1_est(LUo, ipo, O.norm_one(A))
+    tol = max(1e-10, kappa * 32 * n * EPS)
+    assert np.abs(X.cpu().numpy() - Xo).max() / np.abs(Xo).max() <= tol
+
+
+@pytest.mark.slow
+def test_full_size_f64_n16384(ctx):
+    """The FP64 configuration at full size (n = 16384, nb = 256): the first
+    block step against the oracle, then backward stability of the solve."""
+    import torch
+    n, nb = 16384, 256
+    Ad = I.hpl_matrix_torch(n, 2, device="cuda")
+    bd = I.hpl_rhs_torch(n, 1, 2, device="cuda")
+    f = ctx.factor(Ad, "f64", nb)
+    assert f.info == 0
+    ip = f.ipiv().cpu().numpy()
+    LUg = f.lu()
+    x = bd.clone()
+    f.solve_(x)
+    torch.cuda.synchronize()
+    A = Ad.cpu().numpy()
+    # first block step by the oracle: pivots 0..nb and rows 0..nb of U are final
+    O.set_threads(0)
+    LU1, ip1, _ = O.getrf(A, nb, ksteps=1)
+    assert np.array_equal(ip[:nb], ip1[:nb])
+    U_rows = LUg[:nb, :].cpu().numpy()
+    assert np.abs(U_rows - LU1[:nb, :]).max() <= 1e-12 * max(1.0, np.abs(LU1[:nb, :]).max())
+    xg = x.cpu().numpy()
+    b = bd.cpu().numpy()
+    assert O.scaled_residual(A, xg, b)[0] < 16.0
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_full_size_mixed_n32768(ctx, prec):
+    """The mixed configuration at full size (n = 32768, A + (n/4) I): b = A*ones
+    has the closed-form solution ones (kappa ~ 1), and the refined x reaches it."""
+    import torch
+    n = 32768
+    Ad = I.hpl_matrix_torch(n, 3, diag_shift=n / 4, device="cuda")
+    f = ctx.factor(Ad, prec, 0)
+    assert f.info == 0
+    ip = f.ipiv().cpu().numpy()
+    assert np.array_equal(ip, np.arange(1, n + 1))
+    ones = torch.ones((n, 1), dtype=torch.float64, device="cuda")
+    from paper_2202_13995_gb300 import lu
+    A = Ad.cpu().numpy()
+    b = -O.residual(A, np.ones(n), np.zeros(n))  # oracle: b = A * ones
+    bd = _dev(b.reshape(n, 1))
+    X = lu.colmajor_empty(n, 1)
+    iters, res = f.refine(Ad, bd, X, 16.0, 50)
+    assert res < 16.0
+    xg = X.cpu().numpy()[:, 0]
+    assert np.abs(xg - 1.0).max() <= 1e-10
+    assert O.scaled_residual(A, xg, b) < 16.0
+    del ones
