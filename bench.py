@@ -40,6 +40,9 @@ WORKLOADS = {
     "hpl_mixed_bf16_n32768": dict(n=32768, nb=0, prec="bf16", nrhs=1, seed=3, shift=0.25),
     "hpl_mixed_fp16_n32768": dict(n=32768, nb=0, prec="fp16", nrhs=1, seed=3, shift=0.25),
     "hpl_mixed_bf16_n32768_rhs32": dict(n=32768, nb=0, prec="bf16", nrhs=32, seed=3, shift=0.25),
+    # smaller cases of the same shapes (profiling captures)
+    "hpl_f64_n4096_nb256": dict(n=4096, nb=256, prec="f64", nrhs=1, seed=2, shift=0.0),
+    "hpl_mixed_bf16_n8192": dict(n=8192, nb=0, prec="bf16", nrhs=1, seed=3, shift=0.25),
 }
 DEFAULT = "hpl_f64_n16384_nb256"
 METRIC = "LU solve TFLOP/s (HPL count 2/3 n^3 + 2 n^2 nrhs) at scaled residual < 16"
