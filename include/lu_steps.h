@@ -29,6 +29,33 @@ extern "C" {
  * panel), dInfo (device, 1 int) the first zero pivot (1-based) or 0. */
 int lu_step_panel(lu_ctx ctx, lu_prec prec, int m, int w, void *dP, int ld, int *dIpiv, int *dInfo);
 
+/* The same panel factorization for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this entry point exists for callers
+ * that must not call cudaMalloc when they factor a panel -- for instance code
+ * that runs while another thread captures a CUDA graph in global capture
+ * mode, or a service that reserves all of its device memory at start-up and
+ * allows no allocation afterwards.  lu_step_panel allocates its scratch on
+ * first use; this variant allocates nothing and creates no context object.
+ *
+ * Its scratch is one fixed 1 MiB array in device memory, held on every GPU
+ * that loads the library until the process exits.  Limits: w <= 512, and
+ * the device has at most 1024 SMs; larger requests return -4 (argument 4,
+ * w, invalid) without running anything.  The first call on each device (with
+ * that device current) looks up the array's device address and the SM count;
+ * make that first call before any stream capture begins.
+ *
+ * Every call uses the same array and leaves its last contents there: calls
+ * whose work overlaps on the GPU (on different streams, or from different
+ * threads without ordering) race on it and give wrong results.
+ *
+ * Arguments as lu_step_panel, with the stream passed directly (a
+ * cudaStream_t, NULL = legacy default stream) and dStatus (device, 1 int),
+ * which the call zeroes and the kernel then ORs device status bits into
+ * (1 = a bounded device wait timed out, 2 = a NaN was met).  dInfo receives
+ * 0 or the first zero pivot (1-based).  Asynchronous: returns once enqueued. */
+int lu_step_panel_static(void *cuda_stream, lu_prec prec, int m, int w, void *dP, int ld, int *dIpiv, int *dInfo,
+                         int *dStatus);
+
 /* Top-block update U12 = L11^-1 A12: dL (w x w row-major, only the strict
  * lower triangle is read; unit diagonal), dX (w x N row-major) overwritten. */
 int lu_step_trsm(lu_ctx ctx, lu_prec prec, int w, int N, const void *dL, int ldl, void *dX, int ldx);

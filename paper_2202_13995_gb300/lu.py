@@ -28,7 +28,7 @@ EXPORTED = [
     "lu_create", "lu_destroy", "lu_strerror", "lu_factor", "lu_fact_info", "lu_fact_ipiv", "lu_fact_lu",
     "lu_solve", "lu_refine", "lu_scaled_residual", "lu_fact_free",
     "lu_step_panel", "lu_step_trsm", "lu_step_gemm", "lu_ctx_status", "lu_device_sm_count", "lu_build_tag",
-    "lu_profile_enable", "lu_profile_read", "lu_launch_count",
+    "lu_profile_enable", "lu_profile_read", "lu_launch_count", "lu_step_panel_static",
 ]
 PHASES = ["panel", "laswp", "trsm", "cast", "gemm", "solve", "residual", "other"]
 
@@ -78,6 +78,7 @@ def load():
             "lu_profile_enable": (I, [P, I]),
             "lu_profile_read": (I, [P, DP, C.POINTER(C.c_longlong)]),
             "lu_launch_count": (C.c_longlong, [P]),
+            "lu_step_panel_static": (I, [P, I, I, I, P, I, P, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -219,6 +220,14 @@ class Context:
         m, w = P.shape
         _check(load().lu_step_panel(self._h, _prec(prec), m, w, C.c_void_p(pp), ld, C.c_void_p(ipiv.data_ptr()),
                                     C.c_void_p(info.data_ptr())), "lu_step_panel")
+
+    def step_panel_static(self, P, ipiv, info, status, prec="f64"):
+        """lu_step_panel_static on this context's stream (allocates nothing)."""
+        pp, ld = _rowmajor(P, "P")
+        m, w = P.shape
+        _check(load().lu_step_panel_static(C.c_void_p(self.stream.cuda_stream), _prec(prec), m, w, C.c_void_p(pp),
+                                           ld, C.c_void_p(ipiv.data_ptr()), C.c_void_p(info.data_ptr()),
+                                           C.c_void_p(status.data_ptr())), "lu_step_panel_static")
 
     def step_trsm(self, L, X, prec="f64"):
         pl, ldl = _rowmajor(L, "L")
