@@ -448,7 +448,7 @@ static bool make_map(CUtensorMap* map, int kind, const void* ptr, int rows, int 
 }
 
 cudaError_t tc_gemm_run(int kind, float* C, int64_t ldc, const void* Aop, const void* Bop, int m, int n, int kpad,
-                        int* status, const DevInfo& dev, cudaStream_t st) {
+                        int* status, const DevInfo& dev, cudaStream_t st, int max_ctas) {
   if (m <= 0 || n <= 0) return cudaSuccess;
   if (kind != 1 && kind != 2) return cudaErrorInvalidValue;
   if (kpad <= 0 || (kpad % TC_BK) != 0) return cudaErrorInvalidValue;
@@ -474,7 +474,8 @@ cudaError_t tc_gemm_run(int kind, float* C, int64_t ldc, const void* Aop, const 
   P.idesc = tc_idesc(kind == 1 ? 1u : 0u);
   P.status = status;
   const int ntiles = P.tiles_m * P.tiles_n;
-  const int grid = ntiles < dev.sm_count ? ntiles : dev.sm_count;
+  int grid = ntiles < dev.sm_count ? ntiles : dev.sm_count;
+  if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
   tc_gemm_kernel<<<grid, TC_THREADS, TC_SMEM, st>>>(ma, mb, P);
   return cudaGetLastError();
 }

@@ -31,6 +31,9 @@ struct PanelScratch {
 size_t panel_scratch_bytes(int gmax, int ibmax, int wmax, int tsize);
 void panel_scratch_carve(PanelScratch* s, void* base, int gmax, int ibmax, int wmax, int tsize);
 
+// CTAs that launch_panel uses for an m x w panel of element size tsize.
+int panel_grid_size(int m, int w, int tsize, const DevInfo& dev, int gmax);
+
 // Factor the m x w panel whose (0,0) element is W(k,k) (row stride ldw) with
 // partial pivoting.  Writes ipiv[k..k+w) (1-based, absolute), lowers *info to
 // the first zero pivot (absolute, 1-based; the caller initialises it to
@@ -73,8 +76,9 @@ cudaError_t launch_cast_operands(int kind, const float* L21, const float* U12, i
 // C (row-major FP32, m x n) -= Aop * Bop^T on tcgen05 (FP32 accumulate in TMEM).
 struct TcGemmPlan;
 size_t tc_gemm_plan_bytes();
+// max_ctas > 0 caps the persistent grid (to leave SMs to a concurrent kernel).
 cudaError_t tc_gemm_run(int kind, float* C, int64_t ldc, const void* Aop, const void* Bop, int m, int n, int kpad,
-                        int* status, const DevInfo& dev, cudaStream_t st);
+                        int* status, const DevInfo& dev, cudaStream_t st, int max_ctas = 0);
 
 // ---------------------------------------------------------------- solve.cu
 struct SolveScratch {
@@ -82,7 +86,12 @@ struct SolveScratch {
   void* y;         // n x NR (T) workspace
   void* z;         // n x NR (T) workspace
   int nblk_max;
+  void* dinv = nullptr;     // optional inverses of the 64 x 64 diagonal blocks
+  bool dinv_ready = false;
 };
+size_t solve_dinv_bytes(int n, int tsize);
+template <typename T>
+cudaError_t launch_trinv(const T* W, int64_t ldw, int n, T* Dinv, cudaStream_t st);
 size_t solve_scratch_bytes(int n, int tsize);
 void solve_scratch_carve(SolveScratch* s, void* base, int n, int tsize);
 

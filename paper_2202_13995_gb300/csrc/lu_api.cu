@@ -17,8 +17,8 @@
 #include <new>
 #include <vector>
 
-#include "../../include/lu.h"
-#include "../../include/lu_steps.h"
+#include "lu.h"
+#include "lu_steps.h"
 #include "common.cuh"
 #include "kernels.h"
 
@@ -46,6 +46,10 @@ struct lu_ctx_s {
   };
   std::vector<Rec> recs;
   std::vector<cudaEvent_t> pool;
+  // lookahead: a side stream for the next panel, joined back by events
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_next = nullptr, ev_panel = nullptr;
+  bool lookahead = true;
 };
 
 enum { PH_PANEL = 0, PH_LASWP, PH_TRSM, PH_CAST, PH_GEMM, PH_SOLVE, PH_RESID, PH_OTHER, PH_N };
@@ -64,22 +68,23 @@ static cudaEvent_t ev_get(lu_ctx c) {
 // Launch wrapper: counts the kernels a launcher starts and, when profiling,
 // brackets them with an event pair on the context's stream.
 template <typename F>
-static cudaError_t run_phase(lu_ctx c, int phase, int nk, F&& launch) {
+static cudaError_t run_phase(lu_ctx c, int phase, int nk, cudaStream_t st, F&& launch) {
   cudaEvent_t a = nullptr, b = nullptr;
   if (c->prof) {
     a = ev_get(c);
     b = ev_get(c);
-    cudaEventRecord(a, c->stream);
+    cudaEventRecord(a, st);
   }
   cudaError_t e = launch();
   if (c->prof) {
-    cudaEventRecord(b, c->stream);
+    cudaEventRecord(b, st);
     c->recs.push_back({phase, nk, a, b});
   }
   if (e == cudaSuccess) c->launches += nk;
   return e;
 }
-#define PHASE(c, ph, nk, expr) run_phase((c), (ph), (nk), [&]() { return (expr); })
+#define PHASE(c, ph, nk, expr) run_phase((c), (ph), (nk), (c)->stream, [&]() { return (expr); })
+#define PHASE_ON(c, st, ph, nk, expr) run_phase((c), (ph), (nk), (st), [&]() { return (expr); })
 
 struct lu_fact_s {
   lu_ctx ctx = nullptr;
@@ -169,6 +174,13 @@ extern "C" int lu_create(lu_ctx* out, void* cuda_stream) {
   }
   cudaMemset(c->d_status, 0, 64 * sizeof(int));
   cudaMemset(c->d_small, 0, 128 * sizeof(double));
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_next, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_panel, cudaEventDisableTiming) != cudaSuccess) {
+    lu_destroy(c);
+    return LU_ECUDA;
+  }
+  if (getenv("GB300LU_NO_LOOKAHEAD")) c->lookahead = false;
   *out = c;
   return LU_OK;
 }
@@ -181,6 +193,12 @@ extern "C" void lu_destroy(lu_ctx c) {
     cudaEventDestroy(r.b);
   }
   for (auto e : c->pool) cudaEventDestroy(e);
+  if (c->side) {
+    cudaStreamSynchronize(c->side);
+    cudaStreamDestroy(c->side);
+  }
+  if (c->ev_next) cudaEventDestroy(c->ev_next);
+  if (c->ev_panel) cudaEventDestroy(c->ev_panel);
   if (c->step_ws) cudaFree(c->step_ws);
   if (c->d_status) cudaFree(c->d_status);
   if (c->d_small) cudaFree(c->d_small);
@@ -253,28 +271,61 @@ static int factor_loop(lu_fact f) {
   T* W = (T*)f->W;
   const int n = f->n, nb = f->nb;
   const int64_t ld = f->ldw;
+  const bool tc = f->prec == LU_BF16 || f->prec == LU_FP16;
+  const int kind = f->prec == LU_BF16 ? 1 : 2;
+  // Depth-1 lookahead (the paper's overlap of the next communication phase
+  // with the update phase): the next panel's columns are updated first, then
+  // that panel is factored on the side stream while the rest of the trailing
+  // matrix is updated on the remaining SMs.
+  const bool lookahead = tc && c->lookahead && c->side != nullptr;
+  bool panel_ready = false;
   for (int k = 0; k < n; k += nb) {
     const int w = (n - k) < nb ? (n - k) : nb;
     T* Wkk = W + (int64_t)k * ld + k;
-    CU_TRY(PHASE(c, PH_PANEL, 1, launch_panel<T>(Wkk, ld, n - k, w, k, f->ipiv, f->info_d, c->d_status, f->ps, c->dev, st)));
+    if (panel_ready) {
+      CU_TRY(cudaStreamWaitEvent(st, c->ev_panel, 0));
+      panel_ready = false;
+    } else {
+      CU_TRY(PHASE(c, PH_PANEL, 1, launch_panel<T>(Wkk, ld, n - k, w, k, f->ipiv, f->info_d, c->d_status, f->ps,
+                                                   c->dev, st)));
+    }
     CU_TRY(PHASE(c, PH_LASWP, 1, launch_laswp<T>(W, ld, n, k, w, f->ps.perm, f->rowid, st)));
     const int rest = n - k - w;
-    if (rest > 0) {
-      T* U12 = Wkk + w;
-      T* L21 = Wkk + (int64_t)w * ld;
-      T* A22 = L21 + w;
-      CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12, ld, w, rest, st)));
-      if (f->prec == LU_BF16 || f->prec == LU_FP16) {
-        const int kind = f->prec == LU_BF16 ? 1 : 2;
-        CU_TRY(PHASE(c, PH_CAST, 2, launch_cast_operands(kind, (const float*)L21, (const float*)U12, ld, rest, rest,
-                                                          w, f->aop, f->bop, f->kpad, c->d_status, st)));
-        CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)A22, ld, f->aop, f->bop, rest, rest, f->kpad,
-                                                 c->d_status, c->dev, st)));
-      } else {
-        CU_TRY(PHASE(c, PH_GEMM, 1, launch_gemm_simt<T>(A22, ld, L21, ld, U12, ld, rest, rest, w, st)));
-      }
+    if (rest <= 0) continue;
+    T* U12 = Wkk + w;
+    T* L21 = Wkk + (int64_t)w * ld;
+    T* A22 = L21 + w;
+    CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12, ld, w, rest, st)));
+    if (!tc) {
+      CU_TRY(PHASE(c, PH_GEMM, 1, launch_gemm_simt<T>(A22, ld, L21, ld, U12, ld, rest, rest, w, st)));
+      continue;
     }
+    CU_TRY(PHASE(c, PH_CAST, 2, launch_cast_operands(kind, (const float*)L21, (const float*)U12, ld, rest, rest, w,
+                                                      f->aop, f->bop, f->kpad, c->d_status, st)));
+    const int w2 = rest < nb ? rest : nb;
+    if (!lookahead || rest <= w2) {
+      CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)A22, ld, f->aop, f->bop, rest, rest, f->kpad,
+                                               c->d_status, c->dev, st)));
+      continue;
+    }
+    // columns of the next panel first
+    CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)A22, ld, f->aop, f->bop, rest, w2, f->kpad, c->d_status,
+                                             c->dev, st)));
+    CU_TRY(cudaEventRecord(c->ev_next, st));
+    CU_TRY(cudaStreamWaitEvent(c->side, c->ev_next, 0));
+    T* Wn = A22;  // W(k + w, k + w)
+    CU_TRY(PHASE_ON(c, c->side, PH_PANEL, 1, launch_panel<T>(Wn, ld, rest, w2, k + w, f->ipiv, f->info_d,
+                                                             c->d_status, f->ps, c->dev, c->side)));
+    CU_TRY(cudaEventRecord(c->ev_panel, c->side));
+    panel_ready = true;
+    // the rest of the trailing matrix on the SMs the panel leaves free
+    const int gp = panel_grid_size(rest, w2, sizeof(T), c->dev, f->ps.gmax);
+    const int cap = c->dev.sm_count - (gp > 0 ? gp : 0);
+    const void* bop2 = (const char*)f->bop + (size_t)w2 * f->kpad * 2;
+    CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)(A22 + w2), ld, f->aop, bop2, rest, rest - w2, f->kpad,
+                                             c->d_status, c->dev, st, cap > 8 ? cap : 8)));
   }
+  if (panel_ready) CU_TRY(cudaStreamWaitEvent(st, c->ev_panel, 0));
   return LU_OK;
 }
 
@@ -286,6 +337,7 @@ extern "C" void lu_fact_free(lu_fact f) {
   dfree(c, f->panel_mem);
   dfree(c, f->aop);
   dfree(c, f->solve_mem);
+  dfree(c, f->ss.dinv);
   dfree(c, f->vec_ws);
   delete f;
 }
@@ -324,6 +376,13 @@ extern "C" int lu_factor(lu_ctx c, int n, const double* dA, int lda, lu_prec pre
   f->info_d = f->rowid + nn;
   panel_scratch_carve(&f->ps, f->panel_mem, gmax, 32, f->nb, f->tsize);
   solve_scratch_carve(&f->ss, f->solve_mem, nn, f->tsize);
+  if (prec != LU_F64) {
+    // FP32 factors: inverted diagonal blocks for the correction solves
+    if ((rc = dalloc(c, &f->ss.dinv, solve_dinv_bytes(nn, f->tsize)))) {
+      lu_fact_free(f);
+      return rc;
+    }
+  }
   if (prec == LU_BF16 || prec == LU_FP16) {
     f->kpad = round_up(f->nb, 64);
     if ((rc = dalloc(c, &f->aop, (size_t)2 * nn * f->kpad * 2 + 1024))) {
@@ -348,6 +407,12 @@ extern "C" int lu_factor(lu_ctx c, int n, const double* dA, int lda, lu_prec pre
       if (PHASE(c, PH_OTHER, 1, launch_to_working<float>(dA, lda, (float*)f->W, f->ldw, n, st)) != cudaSuccess)
         return fail(LU_ECUDA);
       rc = factor_loop<float>(f);
+      if (!rc && f->ss.dinv) {
+        if (PHASE(c, PH_OTHER, 1, launch_trinv<float>((const float*)f->W, f->ldw, n, (float*)f->ss.dinv, st)) !=
+            cudaSuccess)
+          return fail(LU_ECUDA);
+        f->ss.dinv_ready = true;
+      }
     }
     if (rc) return fail(rc);
   }

@@ -11,6 +11,7 @@
 // The working matrix W is row-major (see kernels.h).
 #include <climits>
 #include <cstdio>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -42,6 +43,12 @@ __device__ __forceinline__ T tabs(T v) {
 constexpr int PNL_THREADS = 256;
 constexpr int PNL_WARPS = PNL_THREADS / 32;
 constexpr int PNL_IB = 32;
+// After each column's barrier every CTA reads all candidate rows at once
+// (one L2 round trip); up to PNL_XG CTAs.
+constexpr int PNL_XG = 160;
+constexpr int PNL_XQ = PNL_XG * PNL_IB / PNL_THREADS;  // candidate values per thread
+constexpr int PNL_HF = 2048;  // hash buckets: rows outside the panel's top w rows
+constexpr int PNL_HS = 128;   // hash buckets: rows outside a sub-panel's top rows
 
 template <typename T>
 struct PanelParams {
@@ -62,49 +69,71 @@ struct PanelParams {
 
 __host__ __device__ inline size_t panel_smem_bytes(int R, int ib, int w, int tsize) {
   const int Rs = R | 1;
-  size_t tcount = (size_t)ib * Rs + 2 * ib + (size_t)ib * ib + (size_t)ib * 32 + 2 * (size_t)ib * 32 + PNL_WARPS;
-  size_t icount = PNL_WARPS + ib + 4 * (size_t)w + 4 * (size_t)ib + 8;
+  size_t tcount = (size_t)ib * Rs + (size_t)ib * ib + (size_t)ib * 32 + 2 * (size_t)ib * 32 + PNL_WARPS +
+                  (size_t)PNL_XG * ib;
+  size_t icount = PNL_WARPS + 4 * (size_t)w + 4 * (size_t)ib + 2 * PNL_HF + 2 * PNL_HS + 8;
   return tcount * tsize + icount * sizeof(int) + 16;
 }
 
-// Swap, in a row-permutation record, the contents of slot sa with the slot of
-// position p (appending p as a new slot when it is not yet recorded).
-// pos[s]: a row position; cur[s]: the original position whose row now sits at
-// pos[s].  Positions [base, lim) map to slots [0, lim - base) directly.
-// Executed by one full warp.
-__device__ __forceinline__ void perm_swap(int* pos, int* cur, int* cnt, int sa, int p, int base, int lim,
-                                          int lane) {
-  int sb;
-  if (p < lim) {
-    sb = p - base;
-  } else {
-    const int ndirect = lim - base;
-    const int n = *cnt;
-    sb = -1;
-    for (int s0 = ndirect; s0 < n; s0 += 32) {
-      const int s = s0 + lane;
-      const unsigned hit = __ballot_sync(0xffffffffu, s < n && pos[s] == p);
-      if (hit) {
-        sb = s0 + __ffs(hit) - 1;
-        break;
+// Row-permutation record: slot s holds position pos[s] and the original
+// position cur[s] of the row that now sits there.  Positions [base, lim) use
+// slots [0, lim - base) directly; other positions are found through an
+// open-addressing hash (key = position, value = slot).  One thread only.
+struct PermRec {
+  int* pos;
+  int* cur;
+  int* hkey;
+  int* hval;
+  int mask;
+  int base, lim;
+  int* cnt;
+  __device__ __forceinline__ int slot(int p) const {
+    if (p < lim) return p - base;
+    unsigned b = ((unsigned)p * 2654435761u) & (unsigned)mask;
+    while (true) {
+      const int k = hkey[b];
+      if (k == p) return hval[b];
+      if (k < 0) {
+        const int s = (*cnt)++;
+        hkey[b] = p;
+        hval[b] = s;
+        pos[s] = p;
+        cur[s] = p;
+        return s;
       }
+      b = (b + 1) & (unsigned)mask;
     }
-    if (sb < 0) {
-      sb = n;
-      if (lane == 0) {
-        pos[n] = p;
-        cur[n] = p;
-        *cnt = n + 1;
-      }
-    }
-    __syncwarp();
   }
-  if (lane == 0) {
+  __device__ __forceinline__ void swap_rows(int a, int p) const {  // positions a (direct) and p
+    const int sa = slot(a), sb = slot(p);
     const int t = cur[sa];
     cur[sa] = cur[sb];
     cur[sb] = t;
   }
-  __syncwarp();
+};
+
+// Grid barrier on a monotonic arrival counter (zeroed by the launcher): the
+// k-th barrier waits until the counter reaches k * G.  Arrival is a release
+// reduction, so a CTA never waits on its own arrival round trip.
+__device__ __forceinline__ bool grid_sync_mono(unsigned* count, unsigned target, int* status, int* smem_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+    int ok = 1;
+    if (ld_acquire_u32(count) < target) {
+      const uint64_t t0 = gtimer();
+      while (ld_acquire_u32(count) < target) {
+        if (gtimer() - t0 > GB_SPIN_LIMIT_NS) {
+          atomicOr(status, ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    *smem_flag = ok;
+  }
+  __syncthreads();
+  return *smem_flag != 0;
 }
 
 template <typename T>
@@ -118,26 +147,30 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
   const int rloc = max(0, min(P.m, row0 + R) - row0);
 
   T* S = reinterpret_cast<T*>(smem_raw);  // [ib][Rs]: column t of the tile, row r
-  T* prow = S + (size_t)ib * Rs;          // pivot row (sub-panel columns)
-  T* rjv = prow + ib;                     // row j before the swap
-  T* Lsub = rjv + ib;                     // [ib][ib] unit-lower block of the sub-panel
+  T* Lsub = S + (size_t)ib * Rs;          // [ib][ib] unit-lower block of the sub-panel
   T* Ust = Lsub + ib * ib;                // [ib][32] U rows for the in-panel update
   T* stage = Ust + ib * 32;               // [2*ib][32] interchange staging
-  T* redv = stage + 2 * ib * 32;          // [PNL_WARPS]
+  T* xall = stage + 2 * ib * 32;          // [PNL_XG][ib] all candidate rows
+  T* redv = xall + PNL_XG * ib;           // [PNL_WARPS]
   int* redi = reinterpret_cast<int*>(redv + PNL_WARPS);
-  int* spiv = redi + PNL_WARPS;  // [ib]
-  int* fpos = spiv + ib;         // [2w] whole-panel permutation record
+  int* fpos = redi + PNL_WARPS;  // [2w] whole-panel permutation record
   int* fcur = fpos + 2 * w;
   int* spos = fcur + 2 * w;      // [2ib] sub-panel permutation record
   int* scur = spos + 2 * ib;
-  int* misc = scur + 2 * ib;     // 0: fcnt 1: scnt 2: barrier flag 3: local best row 4: pivot row
-  const GridBarrier gbar{P.bar, (unsigned)G};
+  int* hfk = scur + 2 * ib;      // [PNL_HF] keys / values
+  int* hfv = hfk + PNL_HF;
+  int* hsk = hfv + PNL_HF;       // [PNL_HS]
+  int* hsv = hsk + PNL_HS;
+  int* misc = hsv + PNL_HS;      // 0: fcnt 1: scnt 2: barrier flag
+  unsigned nbar = 0;
 
   for (int s = tid; s < w; s += PNL_THREADS) {
     fpos[s] = s;
     fcur[s] = s;
   }
+  for (int s = tid; s < PNL_HF; s += PNL_THREADS) hfk[s] = -1;
   if (tid == 0) misc[0] = w;
+  const PermRec fperm{fpos, fcur, hfk, hfv, PNL_HF - 1, 0, w, &misc[0]};
   __syncthreads();
 
   for (int j0 = 0; j0 < w; j0 += ib) {
@@ -148,23 +181,24 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
       spos[s] = j0 + s;
       scur[s] = j0 + s;
     }
+    for (int s = tid; s < PNL_HS; s += PNL_THREADS) hsk[s] = -1;
     if (tid == 0) misc[1] = ibs;
+    const PermRec sperm{spos, scur, hsk, hsv, PNL_HS - 1, j0, j0 + ibs, &misc[1]};
     __syncthreads();
+    // local candidate of the sub-panel's first column
+    T bv = T(-1);
+    int bi = INT_MAX;
+    for (int r = tid; r < rloc; r += PNL_THREADS) {
+      const int gi = row0 + r;
+      if (gi >= j0) argmax_merge(bv, bi, tabs(S[r]), gi);
+    }
 
     for (int j = 0; j < ibs; ++j) {
       const int jg = j0 + j;
       const int par = jg & 1;
-      // ---- 1. local pivot candidate
-      T bv = T(-1);
-      int bi = INT_MAX;
-      for (int r = tid; r < rloc; r += PNL_THREADS) {
-        const int gi = row0 + r;
-        if (gi >= jg) {
-          const T v = tabs(S[j * Rs + r]);
-          if (v != v) atomicOr(P.status, ST_RANGE);
-          argmax_merge(bv, bi, v, gi);
-        }
-      }
+      // ---- 1. this CTA's candidate: first row of largest |a| in column j
+      //      among its rows >= jg; publish it with its sub-panel values
+      if (bv != bv) atomicOr(P.status, ST_RANGE);
       warp_argmax(bv, bi);
       if (lane == 0) {
         redv[warp] = bv;
@@ -172,65 +206,73 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
       }
       __syncthreads();
       if (warp == 0) {
-        bv = lane < PNL_WARPS ? redv[lane] : T(-1);
-        bi = lane < PNL_WARPS ? redi[lane] : INT_MAX;
-        warp_argmax(bv, bi);
+        T v = lane < PNL_WARPS ? redv[lane] : T(-1);
+        int i = lane < PNL_WARPS ? redi[lane] : INT_MAX;
+        warp_argmax(v, i);
         if (lane == 0) {
-          misc[3] = bi;
-          P.xval[par * G + cta] = bv;
-          P.xidx[par * G + cta] = bi;
+          P.xval[par * G + cta] = v;
+          P.xidx[par * G + cta] = i;
         }
+        if (i != INT_MAX && lane < ibs) P.xrow[((int64_t)par * G + cta) * ib + lane] = S[lane * Rs + (i - row0)];
+      } else if (warp == 1) {
+        if (jg >= row0 && jg < row0 + rloc && lane < ibs) P.xrowj[par * ib + lane] = S[lane * Rs + (jg - row0)];
       }
-      __syncthreads();
-      bi = misc[3];
-      if (bi != INT_MAX && tid < ibs) P.xrow[((int64_t)par * G + cta) * ib + tid] = S[tid * Rs + (bi - row0)];
-      if (jg >= row0 && jg < row0 + rloc && tid < ibs) P.xrowj[par * ib + tid] = S[tid * Rs + (jg - row0)];
       // ---- 2. exchange
-      if (!grid_sync(gbar, P.status, &misc[2])) return;
-      // ---- 3. pivot = best candidate over all CTAs
+      if (!grid_sync_mono(P.bar, (++nbar) * (unsigned)G, P.status, &misc[2])) return;
+      // ---- 3. every candidate row, (|a|, row) pair and row jg in one round
+      T xq[PNL_XQ];
+#pragma unroll
+      for (int q = 0; q < PNL_XQ; ++q) {
+        const int e = tid + q * PNL_THREADS;
+        xq[q] = e < G * ib ? __ldcg(P.xrow + (int64_t)par * G * ib + e) : T(0);
+      }
+      const T rjq = tid < ibs ? __ldcg(P.xrowj + par * ib + tid) : T(0);
       bv = T(-1);
       bi = INT_MAX;
-      for (int c = tid; c < G; c += PNL_THREADS) argmax_merge(bv, bi, __ldcg(P.xval + par * G + c), __ldcg(P.xidx + par * G + c));
+      if (tid < G) {
+        bv = __ldcg(P.xval + par * G + tid);
+        bi = __ldcg(P.xidx + par * G + tid);
+      }
+#pragma unroll
+      for (int q = 0; q < PNL_XQ; ++q) {
+        const int e = tid + q * PNL_THREADS;
+        if (e < G * ib) xall[e] = xq[q];
+      }
       warp_argmax(bv, bi);
       if (lane == 0) {
         redv[warp] = bv;
         redi[warp] = bi;
       }
       __syncthreads();
-      if (warp == 0) {
-        bv = lane < PNL_WARPS ? redv[lane] : T(-1);
-        bi = lane < PNL_WARPS ? redi[lane] : INT_MAX;
-        warp_argmax(bv, bi);
-        if (lane == 0) misc[4] = bi;
+      {
+        T v = lane < PNL_WARPS ? redv[lane] : T(-1);
+        int i = lane < PNL_WARPS ? redi[lane] : INT_MAX;
+        warp_argmax(v, i);
+        bi = i;  // the pivot row, in every thread
       }
-      __syncthreads();
-      const int p = misc[4];
-      const int owner_p = p / R;
+      const int p = bi;
+      const T* prow = xall + (p / R) * ib;  // the pivot row's sub-panel values
       if (tid < ibs) {
-        prow[tid] = __ldcg(P.xrow + ((int64_t)par * G + owner_p) * ib + tid);
-        rjv[tid] = __ldcg(P.xrowj + par * ib + tid);
-      }
-      __syncthreads();
-      if (tid < ibs) {
-        if (p != jg && p >= row0 && p < row0 + rloc) S[tid * Rs + (p - row0)] = rjv[tid];
+        if (p != jg && p >= row0 && p < row0 + rloc) S[tid * Rs + (p - row0)] = rjq;
         if (jg >= row0 && jg < row0 + rloc) S[tid * Rs + (jg - row0)] = prow[tid];
       }
-      if (warp == 0) {
-        if (lane == 0) {
-          spiv[j] = p;
-          if (cta == 0) {
-            P.ipiv[P.kabs + jg] = P.kabs + p + 1;
-            if (prow[j] == T(0)) atomicMin(P.info, P.kabs + jg + 1);
-          }
+      if (tid == 0) {
+        if (cta == 0) {
+          P.ipiv[P.kabs + jg] = P.kabs + p + 1;
+          if (prow[j] == T(0)) atomicMin(P.info, P.kabs + jg + 1);
         }
         if (p != jg) {
-          perm_swap(fpos, fcur, &misc[0], jg, p, 0, w, lane);
-          perm_swap(spos, scur, &misc[1], jg - j0, p, j0, j0 + ibs, lane);
+          fperm.swap_rows(jg, p);
+          sperm.swap_rows(jg, p);
         }
       }
       __syncthreads();
-      // ---- 4. scale the column below the pivot, rank-1 update of the sub-panel
+      // ---- 4. scale the column below the pivot (a division, as in the
+      //      definition), rank-1 update of the sub-panel, and the local
+      //      candidate of the next column on the way
       const T piv = prow[j];
+      bv = T(-1);
+      bi = INT_MAX;
       for (int r = tid; r < rloc; r += PNL_THREADS) {
         const int gi = row0 + r;
         if (gi > jg) {
@@ -238,15 +280,16 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
           if (piv != T(0)) l = l / piv;
           S[j * Rs + r] = l;
           for (int c = j + 1; c < ibs; ++c) S[c * Rs + r] -= l * prow[c];
+          if (j + 1 < ibs) argmax_merge(bv, bi, tabs(S[(j + 1) * Rs + r]), gi);
         }
       }
-      __syncthreads();
     }
 
-    // ---- sub-panel done: write the tile back
+    // ---- sub-panel done: write the tile back (after every thread's last update)
+    __syncthreads();
     for (int r = warp; r < rloc; r += PNL_WARPS)
       if (lane < ibs) P.A[(int64_t)(row0 + r) * ld + j0 + lane] = S[lane * Rs + r];
-    if (!grid_sync(gbar, P.status, &misc[2])) return;
+    if (!grid_sync_mono(P.bar, (++nbar) * (unsigned)G, P.status, &misc[2])) return;
 
     // ---- interchanges of this sub-panel on the other panel columns, and the
     //      top-row triangular solve of the columns to its right
@@ -255,19 +298,19 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
     const int nchunk = (nout + 31) / 32;
     if (nchunk > 0 && cta < nchunk) {
       for (int e = tid; e < ibs * ibs; e += PNL_THREADS) {
-        const int t = e / ibs, s = e % ibs;
-        Lsub[t * ib + s] = __ldcg(P.A + (int64_t)(j0 + t) * ld + j0 + s);
+        const int t = e / ibs, s2 = e % ibs;
+        Lsub[t * ib + s2] = __ldcg(P.A + (int64_t)(j0 + t) * ld + j0 + s2);
       }
       __syncthreads();
     }
     for (int q = cta; q < nchunk; q += G) {
       const int o = q * 32 + lane;
       const int c = o < j0 ? o : o + ibs;
-      for (int s = warp; s < scnt; s += PNL_WARPS)
-        if (o < nout) stage[s * 32 + lane] = __ldcg(P.A + (int64_t)scur[s] * ld + c);
+      for (int s2 = warp; s2 < scnt; s2 += PNL_WARPS)
+        if (o < nout) stage[s2 * 32 + lane] = __ldcg(P.A + (int64_t)scur[s2] * ld + c);
       __syncthreads();
-      for (int s = warp; s < scnt; s += PNL_WARPS)
-        if (o < nout) P.A[(int64_t)spos[s] * ld + c] = stage[s * 32 + lane];
+      for (int s2 = warp; s2 < scnt; s2 += PNL_WARPS)
+        if (o < nout) P.A[(int64_t)spos[s2] * ld + c] = stage[s2 * 32 + lane];
       __syncthreads();
       if (warp == 0 && o < nout && o >= j0) {
         // forward substitution with the unit-lower sub-panel block; the
@@ -276,7 +319,7 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
         for (int t = 0; t < ibs; ++t) xs[t * 32 + lane] = __ldcg(P.A + (int64_t)(j0 + t) * ld + c);
         for (int t = 1; t < ibs; ++t) {
           T v = xs[t * 32 + lane];
-          for (int s = 0; s < t; ++s) v -= Lsub[t * ib + s] * xs[s * 32 + lane];
+          for (int s2 = 0; s2 < t; ++s2) v -= Lsub[t * ib + s2] * xs[s2 * 32 + lane];
           xs[t * 32 + lane] = v;
         }
         for (int t = 0; t < ibs; ++t) P.A[(int64_t)(j0 + t) * ld + c] = xs[t * 32 + lane];
@@ -284,7 +327,7 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
       __syncthreads();
     }
     if (j0 + ibs < w) {
-      if (!grid_sync(gbar, P.status, &misc[2])) return;
+      if (!grid_sync_mono(P.bar, (++nbar) * (unsigned)G, P.status, &misc[2])) return;
       // ---- rank-ibs update of own rows below the sub-panel, columns to its right
       const int c0 = j0 + ibs;
       for (int cc = c0; cc < w; cc += 32) {
@@ -306,11 +349,12 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
   }
   // ---- whole-panel permutation for the row interchanges outside the panel
   if (cta == 0) {
+    __syncthreads();
     const int fcnt = misc[0];
     if (tid == 0) P.perm[0] = fcnt;
-    for (int s = tid; s < fcnt; s += PNL_THREADS) {
-      P.perm[1 + s] = fpos[s];
-      P.perm[1 + 2 * w + s] = fcur[s];
+    for (int s2 = tid; s2 < fcnt; s2 += PNL_THREADS) {
+      P.perm[1 + s2] = fpos[s2];
+      P.perm[1 + 2 * w + s2] = fcur[s2];
     }
   }
 }
@@ -345,27 +389,45 @@ void panel_scratch_carve(PanelScratch* s, void* base, int gmax, int ibmax, int w
   s->wmax = wmax;
 }
 
+// CTAs of one panel launch.  FP64 panels are bound by the (slow) FP64 pipes,
+// so they spread over every SM; FP32 panels are bound by the per-column
+// exchange, which is cheaper with fewer CTAs (one L2 round trip per column),
+// and leave the other SMs to the concurrent trailing update.  Each CTA's
+// sub-panel tile must fit in shared memory.
+int panel_grid_size(int m, int w, int tsize, const DevInfo& dev, int gmax) {
+  const int cap = dev.sm_count < gmax ? dev.sm_count : gmax;
+  int target = tsize == 8 ? cap : (64 < cap ? 64 : cap);
+  static const int forced = getenv("GB300LU_PANEL_G") ? atoi(getenv("GB300LU_PANEL_G")) : 0;
+  if (forced > 0) target = forced < cap ? forced : cap;
+  const size_t budget = (size_t)dev.max_smem_optin - 48 * 1024;
+  int R = (int)cdiv(m, target);
+  if (R < 64) R = 64;
+  while ((size_t)PNL_IB * (R | 1) * tsize > budget && target < cap) {
+    ++target;
+    R = (int)cdiv(m, target);
+  }
+  if ((size_t)PNL_IB * (R | 1) * tsize > budget) return -1;
+  if (panel_smem_bytes(R, PNL_IB, w, tsize) > (size_t)dev.max_smem_optin) return -1;
+  return (int)cdiv(m, R);
+}
+
 template <typename T>
 cudaError_t launch_panel(T* Wkk, int64_t ldw, int m, int w, int kabs, int* ipiv, int* info, int* status,
                          const PanelScratch& s, const DevInfo& dev, cudaStream_t st) {
   if (w <= 0 || m < w || w > s.wmax) return cudaErrorInvalidValue;
+  if (s.gmax > PNL_XG) return cudaErrorInvalidValue;  // every candidate row fits the exchange buffer
   const int ib = PNL_IB < s.ibmax ? PNL_IB : s.ibmax;
-  // rows per CTA: at least 64 (fewer CTAs on short panels), at most what the
-  // co-resident grid needs
-  static int occ_cache[2][64] = {};
-  int R = 64;
-  int gcap = dev.sm_count < s.gmax ? dev.sm_count : s.gmax;
-  if ((int64_t)R * gcap < m) R = (int)cdiv(m, gcap);
-  size_t smem = panel_smem_bytes(R, ib, w, sizeof(T));
-  if (smem > (size_t)dev.max_smem_optin) return cudaErrorInvalidConfiguration;
+  const int G0 = panel_grid_size(m, w, sizeof(T), dev, s.gmax);
+  if (G0 <= 0) return cudaErrorInvalidConfiguration;
+  const int R = (int)cdiv(m, G0);
+  const int G = (int)cdiv(m, R);  // <= G0; every CTA owns at least one row
+  const size_t smem = panel_smem_bytes(R, ib, w, sizeof(T));
   auto kern = panel_getrf_kernel<T>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PNL_THREADS, smem);
   if (e != cudaSuccess) return e;
-  (void)occ_cache;
-  const int G = (int)cdiv(m, R);
   if (per_sm < 1 || G > per_sm * dev.sm_count || G > s.gmax) return cudaErrorCooperativeLaunchTooLarge;
   e = cudaMemsetAsync(s.bar, 0, 2 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;

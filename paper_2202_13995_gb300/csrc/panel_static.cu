@@ -12,7 +12,7 @@
 #include <climits>
 #include <mutex>
 
-#include "../../include/lu_steps.h"
+#include "lu_steps.h"
 #include "common.cuh"
 #include "kernels.h"
 

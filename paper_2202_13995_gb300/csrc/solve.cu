@@ -18,128 +18,269 @@
 namespace gb {
 
 constexpr int TS_BS = 64;
+constexpr int TS_NRMAX = 8;  // right-hand sides per launch
 
-template <typename T, int NR>
+// Leading dimension of the solution workspaces: a multiple of 16 elements, so
+// that every 16-byte chunk of a solution block starts 16-byte aligned.
+__host__ __device__ __forceinline__ int64_t trsv_ldy(int n) { return ((int64_t)n + 15) / 16 * 16; }
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Shared memory of one triangular-solve CTA: a ring of STAGES matrix blocks
+// (64 x 64, rows contiguous) with the matching solution blocks, plus the
+// padded diagonal block.
+template <typename T, int NR, int STAGES>
 struct TrsvSmem {
-  T Ls[TS_BS][TS_BS + 1];
-  T ys[TS_BS][NR];
-  T red[3][NR][TS_BS];
+  T Lb[STAGES][TS_BS][TS_BS];
+  T yb[STAGES][NR][TS_BS];
+  T Ld[TS_BS][TS_BS + 1];  // diagonal block (or its inverse), padded rows
+  T v[NR][TS_BS];
   int flag;
   int blk;
 };
 
+// With DINV, the diagonal block's inverse (precomputed by trinv_kernel) turns
+// the serial substitution into a parallel matrix-vector product; the FP32
+// correction solves of the refinement use it.  The FP64 solve substitutes
+// (with the division of the definition).
+
 // LOWER: Y = L^-1 (P B) with unit-lower L; the right-hand side is gathered
-//        from B through rowid (P b)[i] = b[rowid[i]].
+//        from B through rowid: (P b)[i] = b[rowid[i]].
 // UPPER: X = U^-1 Y with non-unit upper U; the result goes to Yout (T) for
 //        the later blocks and to X (FP64).
-template <typename T, int NR, bool LOWER>
+// Y layouts: Yin/Yout[q * ldy + i] (column q of the n x nr block), ldy = trsv_ldy(n).
+// Requires ldw % (16 / sizeof(T)) == 0 and a 16-byte aligned W (the working
+// matrix is allocated that way).
+template <typename T, int NR, int STAGES, bool LOWER, bool DINV>
 __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int64_t ldw, int n, int nrhs,
                                                    const double* __restrict__ B, int64_t ldb,
                                                    const int* __restrict__ rowid, const T* __restrict__ Yin,
                                                    T* Yout, double* X, int64_t ldx, int* flags, int* ticket,
-                                                   int* status) {
+                                                   int* status, const T* __restrict__ Dinv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TrsvSmem<T, NR>& sm = *reinterpret_cast<TrsvSmem<T, NR>*>(smem_raw);
+  TrsvSmem<T, NR, STAGES>& sm = *reinterpret_cast<TrsvSmem<T, NR, STAGES>*>(smem_raw);
+  constexpr int CH = 16 / sizeof(T);  // elements per 16-byte chunk
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int r = tid & 63, g = tid >> 6;
   const int nblk = (n + TS_BS - 1) / TS_BS;
-  if (tid == 0) sm.blk = atomicAdd(ticket, 1);
+  const int64_t ldy = trsv_ldy(n);
+  if (tid == 0) {
+    sm.blk = atomicAdd(ticket, 1);
+    sm.flag = 1;
+  }
   __syncthreads();
   const int t_ = sm.blk;
   const int ib = LOWER ? t_ : nblk - 1 - t_;
   const int i0 = ib * TS_BS;
   const int rows = min(TS_BS, n - i0);
-
-  T acc[NR];
-#pragma unroll
-  for (int q = 0; q < NR; ++q) acc[q] = T(0);
-
-  const int jfirst = LOWER ? 0 : nblk - 1;
-  const int jstep = LOWER ? 1 : -1;
   const int count = LOWER ? ib : nblk - 1 - ib;
-  for (int it = 0; it < count; ++it) {
-    const int jb = jfirst + it * jstep;
-    const int j0 = jb * TS_BS;
-    const int cols = min(TS_BS, n - j0);
-    // matrix block first: it does not depend on the flag
-    for (int e = tid; e < TS_BS * TS_BS; e += 256) {
+  auto jb_of = [&](int it) { return LOWER ? it : nblk - 1 - it; };
+
+  // Off the dependency chain: the diagonal block (or its inverse) and this
+  // block's right-hand side are loaded first; all loads issue before any use.
+  {
+    constexpr int PER = TS_BS * TS_BS / 256;
+    T dv[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + q * 256;
       const int rr = e >> 6, cc = e & 63;
-      sm.Ls[rr][cc] = (rr < rows && cc < cols) ? W[(int64_t)(i0 + rr) * ldw + j0 + cc] : T(0);
+      if (DINV)
+        dv[q] = Dinv[((int64_t)ib * 2 + (LOWER ? 0 : 1)) * TS_BS * TS_BS + e];
+      else
+        dv[q] = (rr < rows && cc < rows) ? W[(int64_t)(i0 + rr) * ldw + i0 + cc] : T(0);
     }
-    if (tid == 0) sm.flag = wait_flag_eq(flags + jb, 1, status) ? 1 : 0;
-    __syncthreads();
-    if (!sm.flag) return;
-    for (int e = tid; e < TS_BS * NR; e += 256) {
-      const int c = e & 63, q = e >> 6;
-      sm.ys[c][q] = (q < nrhs && c < cols) ? __ldcg(Yout + (int64_t)q * n + j0 + c) : T(0);
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int cc = 0; cc < 16; ++cc) {
-      const int c = g * 16 + cc;
-      const T l = sm.Ls[r][c];
 #pragma unroll
-      for (int q = 0; q < NR; ++q) acc[q] = fma(l, sm.ys[c][q], acc[q]);
+    for (int q = 0; q < PER; ++q) {
+      const int e = tid + q * 256;
+      sm.Ld[e >> 6][e & 63] = dv[q];
     }
-    __syncthreads();
   }
-  // reduce the four column groups in a fixed order
-  if (g > 0) {
+  // this block's right-hand side: thread (row tid & 63) holds columns
+  // q = (tid >> 6) + 4 u, u = 0, 1
+  T rhs[2] = {T(0), T(0)};
 #pragma unroll
-    for (int q = 0; q < NR; ++q) sm.red[g - 1][q][r] = acc[q];
+  for (int u = 0; u < 2; ++u) {
+    const int r = tid & 63, q = (tid >> 6) + 4 * u;
+    if (q < NR && r < rows && q < nrhs) {
+      if (LOWER)
+        rhs[u] = (T)B[(int64_t)q * ldb + rowid[i0 + r]];
+      else
+        rhs[u] = Yin[(int64_t)q * trsv_ldy(n) + i0 + r];
+    }
   }
-  // diagonal block
-  for (int e = tid; e < TS_BS * TS_BS; e += 256) {
-    const int rr = e >> 6, cc = e & 63;
-    sm.Ls[rr][cc] = (rr < rows && cc < rows) ? W[(int64_t)(i0 + rr) * ldw + i0 + cc] : T(0);
-  }
-  __syncthreads();
-  if (g == 0) {
+
+  // issue the loads of iteration `it` into its stage (all threads), after the
+  // solution block it needs has been published (warp 0 waits for the flag)
+  auto issue = [&](int it) {
+    if (it < count) {
+      const int jb = jb_of(it);
+      const int j0 = jb * TS_BS;
+      const int cols = min(TS_BS, n - j0);
+      const int st = it % STAGES;
+      for (int e = tid; e < TS_BS * TS_BS / CH; e += 256) {
+        const int rr = e / (TS_BS / CH), cc = (e % (TS_BS / CH)) * CH;
+        T* dst = &sm.Lb[st][rr][cc];
+        if (rr < rows && cc + CH <= cols) {
+          cp_async16(dst, W + (int64_t)(i0 + rr) * ldw + j0 + cc);
+        } else {
+#pragma unroll
+          for (int u = 0; u < CH; ++u)
+            dst[u] = (rr < rows && cc + u < cols) ? W[(int64_t)(i0 + rr) * ldw + j0 + cc + u] : T(0);
+        }
+      }
+      if (warp == 0) {
+        int ok = 1;
+        if (lane == 0) ok = wait_flag_eq(flags + jb, 1, status) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        __syncwarp();  // orders lane 0's acquire before every lane's reads
+        if (!ok) {
+          if (lane == 0) sm.flag = 0;
+        } else {
+          // the published solution block (written before the flag's release)
+          for (int e = lane; e < NR * TS_BS / CH; e += 32) {
+            const int q = e / (TS_BS / CH), cc = (e % (TS_BS / CH)) * CH;
+            T* dst = &sm.yb[st][q][cc];
+            if (q < nrhs && cc + CH <= cols) {
+              cp_async16(dst, Yout + (int64_t)q * ldy + j0 + cc);
+            } else {
+#pragma unroll
+              for (int u = 0; u < CH; ++u)
+                dst[u] = (q < nrhs && cc + u < cols) ? __ldcg(Yout + (int64_t)q * ldy + j0 + cc + u) : T(0);
+            }
+          }
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
+  // acc[rr][q]: partial sums of rows 8*warp + rr over this lane's columns
+  T acc[8][NR];
+#pragma unroll
+  for (int rr = 0; rr < 8; ++rr)
+#pragma unroll
+    for (int q = 0; q < NR; ++q) acc[rr][q] = T(0);
+
+#pragma unroll 1
+  for (int s0 = 0; s0 < STAGES - 1; ++s0) issue(s0);
+#pragma unroll 1
+  for (int it = 0; it < count; ++it) {
+    issue(it + STAGES - 1);
+    cp_async_wait<STAGES - 1>();
+    __syncthreads();
+    if (!sm.flag) {
+      cp_async_wait<0>();
+      return;
+    }
+    const int st = it % STAGES;
+    T y0[NR], y1[NR];
 #pragma unroll
     for (int q = 0; q < NR; ++q) {
-      const T tot = acc[q] + sm.red[0][q][r] + sm.red[1][q][r] + sm.red[2][q][r];
-      T v = T(0);
-      if (r < rows && q < nrhs) {
-        if (LOWER)
-          v = (T)B[(int64_t)q * ldb + rowid[i0 + r]] - tot;
-        else
-          v = Yin[(int64_t)q * n + i0 + r] - tot;
-      }
-      sm.ys[r][q] = v;
+      y0[q] = sm.yb[st][q][lane];
+      y1[q] = sm.yb[st][q][lane + 32];
+    }
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) {
+      const T l0 = sm.Lb[st][warp * 8 + rr][lane];
+      const T l1 = sm.Lb[st][warp * 8 + rr][lane + 32];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) acc[rr][q] = fma(l0, y0[q], fma(l1, y1[q], acc[rr][q]));
+    }
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+  // row sums: a fixed butterfly over the lanes (deterministic)
+#pragma unroll
+  for (int rr = 0; rr < 8; ++rr)
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      T v = acc[rr][q];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      acc[rr][q] = v;
+    }
+  if (lane < NR) {
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) {
+      T tot = T(0);
+#pragma unroll
+      for (int q = 0; q < NR; ++q)
+        if (q == lane) tot = acc[rr][q];
+      sm.v[lane][warp * 8 + rr] = tot;
     }
   }
   __syncthreads();
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int r = tid & 63, q = (tid >> 6) + 4 * u;
+    if (q < NR) sm.v[q][r] = (r < rows && q < nrhs) ? rhs[u] - sm.v[q][r] : T(0);
+  }
+  __syncthreads();
+  if (DINV) {
+    // x = inverse(diagonal block) * v: warp w computes rows 8w .. 8w+7
+    T xr[8][NR];
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr) {
+      const T d0 = sm.Ld[warp * 8 + rr][lane], d1 = sm.Ld[warp * 8 + rr][lane + 32];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        T v = d0 * sm.v[q][lane] + d1 * sm.v[q][lane + 32];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        xr[rr][q] = v;
+      }
+    }
+    __syncthreads();
+    if (lane < NR) {
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        T x = T(0);
+#pragma unroll
+        for (int q = 0; q < NR; ++q)
+          if (q == lane) x = xr[rr][q];
+        sm.v[lane][warp * 8 + rr] = x;
+      }
+    }
+  } else
   for (int q = warp; q < nrhs; q += 8) {
-    T x0 = sm.ys[lane][q], x1 = sm.ys[lane + 32][q];
+    T x0 = sm.v[q][lane], x1 = sm.v[q][lane + 32];
     if (LOWER) {
       for (int t = 0; t < rows; ++t) {
         const T xt = __shfl_sync(0xffffffffu, t < 32 ? x0 : x1, t & 31);
-        if (lane > t) x0 -= sm.Ls[lane][t] * xt;
-        if (lane + 32 > t) x1 -= sm.Ls[lane + 32][t] * xt;
+        if (lane > t) x0 -= sm.Ld[lane][t] * xt;
+        if (lane + 32 > t) x1 -= sm.Ld[lane + 32][t] * xt;
       }
     } else {
       for (int t = rows - 1; t >= 0; --t) {
         T xt;
         if (t >= 32) {
-          if (lane == t - 32) x1 = x1 / sm.Ls[t][t];
+          if (lane == t - 32) x1 = x1 / sm.Ld[t][t];
           xt = __shfl_sync(0xffffffffu, x1, t - 32);
         } else {
-          if (lane == t) x0 = x0 / sm.Ls[t][t];
+          if (lane == t) x0 = x0 / sm.Ld[t][t];
           xt = __shfl_sync(0xffffffffu, x0, t);
         }
-        if (lane < t) x0 -= sm.Ls[lane][t] * xt;
-        if (lane + 32 < t) x1 -= sm.Ls[lane + 32][t] * xt;
+        if (lane < t) x0 -= sm.Ld[lane][t] * xt;
+        if (lane + 32 < t) x1 -= sm.Ld[lane + 32][t] * xt;
       }
     }
-    sm.ys[lane][q] = x0;
-    sm.ys[lane + 32][q] = x1;
+    sm.v[q][lane] = x0;
+    sm.v[q][lane + 32] = x1;
   }
   __syncthreads();
   for (int e = tid; e < TS_BS * NR; e += 256) {
     const int rr = e & 63, q = e >> 6;
     if (rr < rows && q < nrhs) {
-      const T v = sm.ys[rr][q];
-      Yout[(int64_t)q * n + i0 + rr] = v;
+      const T v = sm.v[q][rr];
+      Yout[(int64_t)q * ldy + i0 + rr] = v;
       if (!LOWER) X[(int64_t)q * ldx + i0 + rr] = (double)v;
     }
   }
@@ -150,7 +291,7 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
 
 size_t solve_scratch_bytes(int n, int tsize) {
   const int nblk = (int)cdiv(n, TS_BS);
-  return 256 + (size_t)(nblk + 2) * sizeof(int) + 2 * (size_t)n * 32 * tsize + 512;
+  return 256 + (size_t)(nblk + 2) * sizeof(int) + 2 * (size_t)trsv_ldy(n) * TS_NRMAX * tsize + 512;
 }
 
 void solve_scratch_carve(SolveScratch* s, void* base, int n, int tsize) {
@@ -159,19 +300,21 @@ void solve_scratch_carve(SolveScratch* s, void* base, int n, int tsize) {
   s->sync = (int*)p;
   p += ((size_t)(nblk + 2) * sizeof(int) + 255) / 256 * 256;
   s->y = p;
-  p += ((size_t)n * 32 * tsize + 255) / 256 * 256;
+  p += ((size_t)trsv_ldy(n) * TS_NRMAX * tsize + 255) / 256 * 256;
   s->z = p;
   s->nblk_max = nblk;
 }
 
-template <typename T, int NR>
+template <typename T, int NR, bool DINV>
 static cudaError_t run_solve(const T* W, int64_t ldw, const int* rowid, int n, int nrhs, const double* B,
                              int64_t ldb, double* X, int64_t ldx, const SolveScratch& s, int* status,
                              cudaStream_t st) {
+  constexpr int STAGES = sizeof(T) == 8 ? 3 : 4;
   const int nblk = (int)cdiv(n, TS_BS);
-  const size_t smem = sizeof(TrsvSmem<T, NR>);
-  auto kl = trsv_kernel<T, NR, true>;
-  auto ku = trsv_kernel<T, NR, false>;
+  const size_t smem = sizeof(TrsvSmem<T, NR, STAGES>);
+  auto kl = trsv_kernel<T, NR, STAGES, true, DINV>;
+  auto ku = trsv_kernel<T, NR, STAGES, false, DINV>;
+  const T* Dinv = (const T*)s.dinv;
   cudaError_t e = cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -182,26 +325,99 @@ static cudaError_t run_solve(const T* W, int64_t ldw, const int* rowid, int n, i
   T* z = (T*)s.z;
   e = cudaMemsetAsync(s.sync, 0, (size_t)(nblk + 1) * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  kl<<<nblk, 256, smem, st>>>(W, ldw, n, nrhs, B, ldb, rowid, nullptr, y, nullptr, 0, flags, ticket, status);
+  kl<<<nblk, 256, smem, st>>>(W, ldw, n, nrhs, B, ldb, rowid, nullptr, y, nullptr, 0, flags, ticket, status, Dinv);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(s.sync, 0, (size_t)(nblk + 1) * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  ku<<<nblk, 256, smem, st>>>(W, ldw, n, nrhs, nullptr, 0, nullptr, y, z, X, ldx, flags, ticket, status);
+  ku<<<nblk, 256, smem, st>>>(W, ldw, n, nrhs, nullptr, 0, nullptr, y, z, X, ldx, flags, ticket, status, Dinv);
   return cudaGetLastError();
 }
 
+// Inverses of the 64 x 64 diagonal blocks of L (unit lower) and U (upper):
+// Dinv[(b*2 + 0)] = L_bb^-1, Dinv[(b*2 + 1)] = U_bb^-1, row-major 64 x 64,
+// zero outside a ragged last block.  Thread c computes column c of each
+// inverse by substitution.
+template <typename T>
+__global__ void __launch_bounds__(64) trinv_kernel(const T* __restrict__ W, int64_t ldw, int n, T* Dinv) {
+  __shared__ T Ab[TS_BS][TS_BS + 1];
+  __shared__ T Xb[TS_BS][TS_BS + 1];
+  const int b = blockIdx.x, upper = blockIdx.y;
+  const int i0 = b * TS_BS;
+  const int bs = min(TS_BS, n - i0);
+  const int c = threadIdx.x;
+  for (int r = 0; r < TS_BS; ++r) Ab[r][c] = (r < bs && c < bs) ? W[(int64_t)(i0 + r) * ldw + i0 + c] : T(0);
+  __syncthreads();
+  for (int r = 0; r < TS_BS; ++r) Xb[r][c] = T(0);
+  if (c < bs) {
+    if (!upper) {
+      Xb[c][c] = T(1);
+      for (int r = c + 1; r < bs; ++r) {
+        T sacc = T(0);
+        for (int k = c; k < r; ++k) sacc += Ab[r][k] * Xb[k][c];
+        Xb[r][c] = -sacc;
+      }
+    } else {
+      Xb[c][c] = T(1) / Ab[c][c];
+      for (int r = c - 1; r >= 0; --r) {
+        T sacc = T(0);
+        for (int k = r + 1; k <= c; ++k) sacc += Ab[r][k] * Xb[k][c];
+        Xb[r][c] = -sacc / Ab[r][r];
+      }
+    }
+  }
+  __syncthreads();
+  T* out = Dinv + ((int64_t)b * 2 + upper) * TS_BS * TS_BS;
+  for (int r = 0; r < TS_BS; ++r) out[r * TS_BS + c] = Xb[r][c];
+}
+
+size_t solve_dinv_bytes(int n, int tsize) { return (size_t)cdiv(n, TS_BS) * 2 * TS_BS * TS_BS * tsize; }
+
+template <typename T>
+cudaError_t launch_trinv(const T* W, int64_t ldw, int n, T* Dinv, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  trinv_kernel<T><<<dim3((unsigned)cdiv(n, TS_BS), 2), 64, 0, st>>>(W, ldw, n, Dinv);
+  return cudaGetLastError();
+}
+template cudaError_t launch_trinv<float>(const float*, int64_t, int, float*, cudaStream_t);
+template cudaError_t launch_trinv<double>(const double*, int64_t, int, double*, cudaStream_t);
+
+// One launch pair per chunk of <= 8 right-hand sides (callers pass <= 32).
 template <typename T>
 cudaError_t launch_lu_solve(const T* W, int64_t ldw, const int* rowid, int n, int nrhs, const double* B,
                             int64_t ldb, double* X, int64_t ldx, const SolveScratch& s, int* status,
                             cudaStream_t st) {
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
   if (nrhs > 32) return cudaErrorInvalidValue;
-  if (nrhs == 1) return run_solve<T, 1>(W, ldw, rowid, n, nrhs, B, ldb, X, ldx, s, status, st);
-  if (nrhs <= 4) return run_solve<T, 4>(W, ldw, rowid, n, nrhs, B, ldb, X, ldx, s, status, st);
-  if (nrhs <= 8) return run_solve<T, 8>(W, ldw, rowid, n, nrhs, B, ldb, X, ldx, s, status, st);
-  if (nrhs <= 16) return run_solve<T, 16>(W, ldw, rowid, n, nrhs, B, ldb, X, ldx, s, status, st);
-  return run_solve<T, 32>(W, ldw, rowid, n, nrhs, B, ldb, X, ldx, s, status, st);
+  if (((uintptr_t)W & 15u) || (ldw % (16 / sizeof(T))) != 0) return cudaErrorInvalidValue;
+  for (int q0 = 0; q0 < nrhs; q0 += TS_NRMAX) {
+    const int nr = (nrhs - q0) < TS_NRMAX ? (nrhs - q0) : TS_NRMAX;
+    const double* Bq = B + (int64_t)q0 * ldb;
+    double* Xq = X + (int64_t)q0 * ldx;
+    cudaError_t e;
+    const bool dinv = s.dinv != nullptr && s.dinv_ready;
+    if (dinv) {
+      if (nr == 1)
+        e = run_solve<T, 1, true>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
+      else if (nr == 2)
+        e = run_solve<T, 2, true>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
+      else if (nr <= 4)
+        e = run_solve<T, 4, true>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
+      else
+        e = run_solve<T, 8, true>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
+    } else {
+      if (nr == 1)
+        e = run_solve<T, 1, false>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
+      else if (nr == 2)
+        e = run_solve<T, 2, false>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
+      else if (nr <= 4)
+        e = run_solve<T, 4, false>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
+      else
+        e = run_solve<T, 8, false>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template cudaError_t launch_lu_solve<double>(const double*, int64_t, const int*, int, int, const double*, int64_t,
