@@ -43,6 +43,9 @@ WORKLOADS = {
     # smaller cases of the same shapes (profiling captures)
     "hpl_f64_n4096_nb256": dict(n=4096, nb=256, prec="f64", nrhs=1, seed=2, shift=0.0),
     "hpl_mixed_bf16_n8192": dict(n=8192, nb=0, prec="bf16", nrhs=1, seed=3, shift=0.25),
+    # the batched configuration: 4096 systems, n ~ U{32..512}, 1-8 right-hand
+    # sides, A + n I, FP32 factor + FP64 refinement, one persistent launch
+    "batched_4096": dict(count=4096, nmin=32, nmax=512, kmax=8, seed=5, prec="f32"),
 }
 DEFAULT = "hpl_f64_n16384_nb256"
 METRIC = "LU solve TFLOP/s (HPL count 2/3 n^3 + 2 n^2 nrhs) at scaled residual < 16"
@@ -151,6 +154,58 @@ def max_over_ranks(v: float, ws: int) -> float:
     return float(t.item())
 
 
+def default_nb(n: int, prec: str) -> int:
+    # mirrors the library's default block width (nb = 0)
+    if prec in ("f64", "f32"):
+        return 256 if n >= 4096 else 64
+    return 256 if n >= 2048 else 64
+
+
+def gemm_roofline(prof: dict, n: int, nb: int, prec: str, steps: int, peaks: dict, wname: str) -> dict:
+    """Roofline of the dominant kernel, the trailing update, from its summed
+    CUDA-event launch durations in the timed region.
+
+    FP64 (DFMA, CUDA cores): bound by the FP64 pipes; algorithmic FLOPs per
+    launch = 2 m'^2 nb.  BF16/FP16 (tcgen05): at nb = 256 the update's FP32
+    C read-modify-write makes it HBM-bound (64 FLOP per byte, below the
+    tensor ridge); algorithmic bytes per launch = 8 m' n' (C read + write)
+    + 2 (m' + n') kpad (the 16-bit operands)."""
+    gemm_ms, gemm_n = prof["gemm"]
+    nbx = nb or default_nb(n, prec)
+    kpad = -(-nbx // 64) * 64
+    flops = bytes_ = 0.0
+    for k in range(0, n, nbx):
+        w = min(nbx, n - k)
+        rest = n - k - w
+        if rest > 0:
+            flops += 2.0 * rest * rest * w
+            bytes_ += 8.0 * rest * rest + 2.0 * (2 * rest) * kpad
+    flops *= steps
+    bytes_ *= steps
+    sec = gemm_ms * 1e-3
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get(wname)
+        except Exception:
+            traffic = None
+    base = {"launches": gemm_n, "kernel_ms_per_step": gemm_ms / steps, "traffic": traffic,
+            "tflops": flops / sec / 1e12 if sec > 0 else None}
+    if prec == "f64":
+        peak = peaks.get("bf16_tflops", 1876.8) * NOMINAL["f64"] / NOMINAL["bf16"]
+        ach = flops / sec / 1e12 if sec > 0 else None
+        return dict(base, bound="alu", kernel="gemm_simt_kernel<double>", achieved=ach, peak=peak, unit="TFLOP/s",
+                    frac=(ach / peak) if ach else None,
+                    peak_source=f"bf16_tflops of {peaks['_source']} x nominal FP64/BF16 ratio 1.25/2250")
+    peak = peaks.get("hbm_gbs", 6800.0)
+    ach = bytes_ / sec / 1e9 if sec > 0 else None
+    return dict(base, bound="hbm", kernel="tc_gemm_kernel", achieved=ach, peak=peak, unit="GB/s",
+                frac=(ach / peak) if ach else None, peak_source=f"hbm_gbs of {peaks['_source']}",
+                tensor_frac_of_sustained=(flops / sec / 1e12 / peaks.get("bf16_tflops_sustained", 1701.1))
+                if sec > 0 else None)
+
+
 def _block_step_flops(n: int, nb: int, s: int) -> float:
     """Operation count of block iteration s (panel, top solve, inner update)."""
     m = n - s * nb
@@ -213,50 +268,43 @@ def run_reference(args, cfg, wname):
     return 0
 
 
-def run_ours(args, cfg, wname):
+def timed_solves(ctx, stream, cfg: dict, nb, steps: int, warmup: int, rank: int, ws: int, sampler=None) -> dict:
+    """Warm up, then time `steps` whole solves on the device (CUDA events on
+    the library's stream, a barrier and a synchronize on both sides)."""
     import torch
     from paper_2202_13995_gb300 import inputs as I
     from paper_2202_13995_gb300 import lu
-
-    rank, ws, local = dist_setup()
-    torch.cuda.set_device(local)
-    peaks = load_peaks()
-    n, nb, prec, nrhs = cfg["n"], cfg["nb"], cfg["prec"], cfg["nrhs"]
+    n, prec, nrhs = cfg["n"], cfg["prec"], cfg["nrhs"]
     shift = cfg["shift"] * n
     mixed = prec != "f64"
-    flops = hpl_flops(n, nrhs)
-
-    stream = torch.cuda.current_stream()
-    ctx = lu.Context(stream)
     A = I.hpl_matrix_torch(n, cfg["seed"] + 1000 * rank, diag_shift=shift, device="cuda")
     B = I.hpl_rhs_torch(n, nrhs, cfg["seed"] + 1000 * rank, device="cuda")
     X = lu.colmajor_empty(n, nrhs)
     torch.cuda.synchronize()
+    iters = []
 
     def step():
         f = ctx.factor(A, prec, nb, sync=False)
         if mixed:
-            f.refine(A, B, X, 16.0, 50)
+            iters.append(f.refine(A, B, X, 16.0, 50)[0])
         else:
             X.copy_(B)
             f.solve_(X)
         f.free()
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-
-    # ---- timed region (device time, CUDA events on the library's stream)
-    clocks = ClockSampler(local)
     barrier(ws)
     torch.cuda.synchronize()
-    clocks.start()
+    if sampler:
+        sampler.start()
     ctx.profile(True)
     l0 = ctx.launch_count()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -264,42 +312,74 @@ def run_ours(args, cfg, wname):
     prof = ctx.profile_read()
     ctx.profile(False)
     barrier(ws)
-    ck = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    ms = max_over_ranks(ms, ws)
-
-    # residual of the last solve (FP64, on the device)
+    ck = sampler.stop() if sampler else None
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / steps, ws)
     res = float(ctx.scaled_residual(A, X, B).max())
+    return {"A": A, "B": B, "X": X, "ms": ms, "prof": prof, "launches": launches, "res": res, "clocks": ck,
+            "refine_iters": iters[-1] if iters else None}
 
-    # ---- roofline of the dominant kernel: the trailing update (GEMM)
-    gemm_ms, gemm_n = prof["gemm"]
-    gemm_flops = 0.0
-    step_nb = nb or (256 if n >= 2048 else 64)
-    for k in range(0, n, step_nb):
-        rest = n - k - min(step_nb, n - k)
-        if rest > 0:
-            gemm_flops += 2.0 * rest * rest * min(step_nb, n - k)
-    gemm_flops *= args.steps
-    achieved = gemm_flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
-    if mixed:
-        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-        peak_note = f"bf16_tflops_sustained of {peaks['_source']}" + (" (fp16 at the same nominal rate)" if prec == "fp16" else "")
-        bound = "tensor"
-    else:
-        peak = peaks.get("bf16_tflops", 1876.8) * NOMINAL["f64"] / NOMINAL["bf16"]
-        peak_note = f"bf16_tflops of {peaks['_source']} x nominal FP64/BF16 ratio 1.25/2250"
-        bound = "alu"
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get(wname)
-        except Exception:
-            traffic = None
-    roofline = {"bound": bound, "kernel": "gemm_tc_kernel" if mixed else "gemm_simt_kernel<double>",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": (achieved / peak) if (achieved and peak) else None, "traffic": traffic,
-                "peak_source": peak_note, "launches": gemm_n, "kernel_ms": gemm_ms / args.steps}
+
+def batched_measure(ctx, stream, cfg: dict, steps: int, warmup: int, tune: bool = True) -> dict:
+    """Time `steps` runs of one planned batch (each run = one graph launch)."""
+    import torch
+    from paper_2202_13995_gb300 import inputs as I
+    from paper_2202_13995_gb300 import lu
+    ns, ks = I.batch_shapes(cfg["count"], cfg["seed"], cfg["nmin"], cfg["nmax"], cfg["kmax"])
+    As, Bs = I.hpl_batch_torch(ns, ks, cfg["seed"])
+    xbuf = torch.empty(int(sum(int(n) * int(k) for n, k in zip(ns, ks))), dtype=torch.float64, device="cuda")
+    Xs, o = [], 0
+    for n, k in zip(ns, ks):
+        Xs.append(xbuf[o:o + int(n) * int(k)].view(int(k), int(n)).t())
+        o += int(n) * int(k)
+    bt = lu.Batch(ctx, As, Bs, Xs, tune=tune)
+    cnt = len(As)
+    info = torch.zeros(cnt, dtype=torch.int32, device="cuda")
+    iters = torch.zeros(cnt, dtype=torch.int32, device="cuda")
+    resid = torch.zeros(cnt, dtype=torch.float64, device="cuda")
+    for _ in range(warmup):
+        bt.run(info, iters, resid)
+    torch.cuda.synchronize()
+    l0 = ctx.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        bt.run(info, iters, resid)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    flops = float(sum(2.0 / 3.0 * float(n) ** 3 + 2.0 * float(n) ** 2 * float(k) for n, k in zip(ns, ks)))
+    shape = bt.shape()
+    out = {"workload": "batched_4096", "systems": cnt, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+           "ms_per_step": ms, "solves_per_s": cnt / (ms * 1e-3), "all_converged": bool((info == 0).all().item()),
+           "max_scaled_residual": float(resid.max().item()), "max_refine_iters": int(iters.max().item()),
+           "launch_shape": {"threads": shape[0], "ctas_per_sm": shape[1]}, "launches": ctx.launch_count() - l0,
+           "bytes_a_fp64": int(sum(int(n) * int(n) for n in ns)) * 8}
+    bt.free()
+    return out
+
+
+def run_ours(args, cfg, wname):
+    import torch
+    from paper_2202_13995_gb300 import lu
+
+    rank, ws, local = dist_setup()
+    torch.cuda.set_device(local)
+    peaks = load_peaks()
+    n, nb, prec, nrhs = cfg["n"], cfg["nb"], cfg["prec"], cfg["nrhs"]
+    if args.nb is not None:
+        nb = args.nb
+    shift = cfg["shift"] * n
+    mixed = prec != "f64"
+    flops = hpl_flops(n, nrhs)
+
+    stream = torch.cuda.current_stream()
+    ctx = lu.Context(stream)
+    r = timed_solves(ctx, stream, cfg, nb, args.steps, args.warmup, rank, ws, ClockSampler(local))
+    A, B = r["A"], r["B"]
+    ms, prof, launches = r["ms"], r["prof"], r["launches"]
+    res, ck = r["res"], r["clocks"]
+    roofline = gemm_roofline(prof, n, nb, prec, args.steps, peaks, wname)
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -340,6 +420,32 @@ def run_ours(args, cfg, wname):
         e2e = {"value": flops * ws / (ems * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ems,
                "h2d_bytes_per_step": int(A.numel() * 8 + n * nrhs * 8), "d2h_bytes_per_step": int(n * nrhs * 8)}
         del Ah, Bh, Xh, Ad, Bd, Xd
+    del r, A, B
+    torch.cuda.empty_cache()
+
+    # ---- the mixed-precision companion: BF16 tensor-core factor + FP64
+    #      refinement on A + (n/4) I, n = 32768 (same timing rules)
+    mixed_line = None
+    if not mixed and not args.no_mixed and wname == DEFAULT:
+        mname = "hpl_mixed_bf16_n32768"
+        mc = WORKLOADS[mname]
+        mr = timed_solves(ctx, stream, mc, mc["nb"], args.steps, args.warmup, rank, ws)
+        mflops = hpl_flops(mc["n"], mc["nrhs"])
+        mv = mflops * ws / (mr["ms"] * 1e-3) / 1e12
+        mixed_line = {"workload": mname, "value": mv, "unit": "TFLOP/s", "ms_per_step": mr["ms"],
+                      "speedup_vs_f64": mv / (flops * ws / (ms * 1e-3) / 1e12), "scaled_residual": mr["res"],
+                      "refine_iters": mr["refine_iters"],
+                      "roofline": gemm_roofline(mr["prof"], mc["n"], mc["nb"], mc["prec"], args.steps, peaks, mname),
+                      "phases_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in mr["prof"].items()}}
+        launches += mr["launches"]
+        del mr
+        torch.cuda.empty_cache()
+
+    batched_line = None
+    if not mixed and not args.no_mixed and wname == DEFAULT:
+        batched_line = batched_measure(ctx, stream, WORKLOADS["batched_4096"], args.steps, args.warmup)
+        launches += batched_line["launches"]
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -353,7 +459,7 @@ def run_ours(args, cfg, wname):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if not mixed else f"{prec}+f32acc+f64refine", "data": "synthetic",
             "config": {"workload": wname, "n": n, "nb": nb or "auto", "nrhs": nrhs, "precision": prec,
-                       "matrix": f"uniform[-0.5,0.5]" + (f" + {cfg['shift']}*n*I" if shift else ""),
+                       "matrix": "uniform[-0.5,0.5]" + (f" + {cfg['shift']}*n*I" if shift else ""),
                        "l2": f"inputs larger than L2 (A = {n * n * 8 / 2 ** 30:.1f} GiB FP64)",
                        "parallelism": "replicas" if ws > 1 else "1 gpu"},
             "scaled_residual": res,
@@ -363,6 +469,8 @@ def run_ours(args, cfg, wname):
             "gpu_launches": launches,
             "phases_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in prof.items()},
             "clocks": ck,
+            "mixed": mixed_line,
+            "batched": batched_line,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -383,8 +491,29 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--ref-seconds", type=float, default=10.0)
+    ap.add_argument("--nb", type=int, default=None, help="block width override (0 = library default)")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision companion measurement")
     args = ap.parse_args()
     cfg = WORKLOADS[args.workload]
+    if args.workload == "batched_4096":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no CPU reference arm; "
+                              "the oracle solves each system in tests/test_gpu_batched.py"}))
+            return 0
+        import torch
+        from paper_2202_13995_gb300 import lu
+        torch.cuda.set_device(0)
+        stream = torch.cuda.current_stream()
+        ctx = lu.Context(stream)
+        r = batched_measure(ctx, stream, cfg, args.steps, args.warmup)
+        ctx.close()
+        line = {"metric": METRIC, "value": r["value"], "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64refine", "data": "synthetic",
+                "config": {"workload": "batched_4096", "systems": cfg["count"]}, "batched": r,
+                "gpu_launches": r["launches"]}
+        print(json.dumps(line), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args, cfg, args.workload)
     return run_ours(args, cfg, args.workload)

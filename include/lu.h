@@ -116,6 +116,11 @@ int lu_refine(lu_fact f, const double *dA, int lda, const double *dB, int ldb, d
 int lu_scaled_residual(lu_ctx ctx, int n, int nrhs, const double *dA, int lda, const double *dX, int ldx,
                        const double *dB, int ldb, double *out);
 
+/* Device bytes that lu_factor (block width nb, 0 = default) plus lu_refine
+ * with nrhs right-hand sides allocate for an n x n system on the current
+ * device (0 on an invalid argument).  For memory budgeting. */
+size_t lu_fact_bytes(int n, int nrhs, lu_prec prec, int nb);
+
 /* Release a factorization (stream-ordered: safe to call with work in flight). */
 void lu_fact_free(lu_fact f);
 

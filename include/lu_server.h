@@ -1,0 +1,95 @@
+/*
+ * lu_server.h -- a serving loop for dense solves (continuous batching).
+ *
+ * Each request is the HPL problem of arxiv 2202.13995 (section "High
+ * Performance Linpack": A x = b via A = L U, L y = b, U x = y), solved by
+ * lu_factor (the blocked right-looking LU with partial pivoting) in the
+ * server's factor precision plus lu_refine (FP64 iterative refinement to HPL
+ * scaled residual < 16).  The paper has no serving layer; this one follows the
+ * serving pattern of the solver's specification: requests that arrive while
+ * others run are admitted as slots and memory free up, and their work overlaps
+ * on the GPU.
+ *
+ * Slots: max_slots worker threads, each with its own library context and CUDA
+ * stream on the device current at lu_server_create.  A free slot takes the
+ * oldest queued request whose memory fits the HBM budget (factor working copy,
+ * operands, scratch and refinement vectors, counted exactly as the library
+ * allocates them), evicting least-recently-used resident factors first.
+ *
+ * Resident factors: a request with keep_factor != 0 leaves its factor resident
+ * under factor_key (counted in the budget).  A later request with the same
+ * key and use_resident != 0 skips the factorization; if the factor was evicted
+ * it is factored again and the result says so.
+ *
+ * Determinism: a request's kernels and launch shapes depend only on the
+ * request (n, nrhs, precision), so its result has the same bits whether it
+ * runs alone or among others.
+ *
+ * Thread safety: every lu_server_* call may come from any host thread.
+ * Buffers: the caller owns A, B and X (device, column-major FP64) and keeps
+ * them alive and unchanged until the request is done (and A while its factor
+ * is resident and may be reused).
+ */
+#ifndef GB300_LU_SERVER_H
+#define GB300_LU_SERVER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include "lu.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lu_server_s *lu_server;
+
+typedef struct {
+  int n, nrhs;            /* 1 <= nrhs <= 32 */
+  const double *dA;       /* n x n */
+  int lda;
+  const double *dB;       /* n x nrhs, read */
+  int ldb;
+  double *dX;             /* n x nrhs, written (must not alias dB) */
+  int ldx;
+  uint64_t factor_key;    /* resident-factor key (0 = none) */
+  int keep_factor;        /* keep this request's factor resident under factor_key */
+  int use_resident;       /* reuse the resident factor of factor_key if present */
+} lu_request;
+
+typedef struct {
+  int status;             /* LU_OK, LU_ENOTCONV, LU_ESINGULAR, LU_ENOMEM, LU_ERANGE, LU_ETIMEOUT, ... */
+  int iters;              /* refinement corrections applied */
+  double scaled_resid;    /* largest final HPL scaled residual */
+  int reused_factor;      /* 1 if a resident factor was used */
+  int refactored;         /* 1 if a requested resident factor had been evicted */
+  int slot;               /* slot that ran it */
+  uint64_t t_submit_ns, t_start_ns, t_done_ns; /* CLOCK_MONOTONIC */
+} lu_result;
+
+/* Start a server on the current device.  hbm_budget_bytes bounds the memory
+ * of running requests plus resident factors; prec is the factor precision
+ * (LU_BF16, LU_FP16, LU_F32 or LU_F64); max_slots in 1..64. */
+int lu_server_create(lu_server *out, size_t hbm_budget_bytes, lu_prec prec, int max_slots);
+
+/* Queue a request; *ticket identifies it.  Returns -k for an invalid
+ * argument k, LU_ENOMEM if the request alone exceeds the budget. */
+int lu_server_submit(lu_server s, const lu_request *req, uint64_t *ticket);
+
+/* LU_EAGAIN while the ticket is queued or running; LU_OK with *out filled once
+ * it is done (the result stays readable until the server is destroyed). */
+int lu_server_poll(lu_server s, uint64_t ticket, lu_result *out);
+
+/* Block until the ticket is done, then as lu_server_poll. */
+int lu_server_wait(lu_server s, uint64_t ticket, lu_result *out);
+
+/* Counters: requests done, resident factors, bytes in use, evictions. */
+int lu_server_stats(lu_server s, uint64_t *done, int *resident, size_t *bytes_in_use, uint64_t *evictions);
+
+/* Finish every queued request, stop the slots and free resident factors. */
+int lu_server_destroy(lu_server s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_LU_SERVER_H */

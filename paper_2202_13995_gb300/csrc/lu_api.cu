@@ -722,3 +722,42 @@ extern "C" int lu_step_gemm(lu_ctx c, lu_prec prec, int m, int n, int k, void* d
   CU_TRY(tc_gemm_run(kind, (float*)dC, ldc, aop, bop, m, n, kpad, c->d_status, c->dev, c->stream));
   return LU_OK;
 }
+
+// ------------------------------------------------------------------ context accessors (batched / server files)
+cudaStream_t gb_ctx_stream(lu_ctx c) { return c->stream; }
+int gb_ctx_sm_count(lu_ctx c) { return c->dev.sm_count; }
+int* gb_ctx_status(lu_ctx c) { return c->d_status; }
+void gb_ctx_count_launches(lu_ctx c, long long k) { c->launches += k; }
+
+// Bytes lu_factor (+ lu_refine's workspace for nrhs columns) allocates; the
+// server's admission counts requests with it.
+size_t gb_fact_bytes(int n, int nrhs, lu_prec prec, int nb, int sm_count) {
+  const int nn = n > 0 ? n : 1;
+  if (nb == 0) nb = default_nb(n, prec);
+  nb = nb < nn ? nb : nn;
+  const int tsize = prec == LU_F64 ? 8 : 4;
+  const size_t ldw = (size_t)round_up(nn, 64);
+  size_t b = ldw * nn * tsize + (size_t)(2 * nn + 64) * sizeof(int) + panel_scratch_bytes(sm_count, 32, nb, tsize) +
+             solve_scratch_bytes(nn, tsize);
+  if (prec != LU_F64) b += solve_dinv_bytes(nn, tsize);
+  if (prec == LU_BF16 || prec == LU_FP16) b += (size_t)2 * nn * round_up(nb, 64) * 2 + 1024;
+  const int nr = nrhs > 32 ? 32 : (nrhs < 1 ? 1 : nrhs);
+  b += 2 * (size_t)nn * nrhs * 8 + residual_partial_bytes(nn, nr) + 4096;
+  return b;
+}
+
+// Move a factorization to another context (its stream, status word and
+// pinned buffers).  The caller guarantees that no work on the old context
+// still uses it.
+void gb_fact_rebind(lu_fact f, lu_ctx c) { f->ctx = c; }
+
+extern "C" size_t lu_fact_bytes(int n, int nrhs, lu_prec prec, int nb) {
+  if (n < 1 || nrhs < 0 || prec < LU_F64 || prec > LU_F32 || nb < 0 || nb > 512) return 0;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return gb_fact_bytes(n, nrhs, prec, nb, sms);
+}

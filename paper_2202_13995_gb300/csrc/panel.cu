@@ -9,7 +9,9 @@
 // as one m x w panel here (LAPACK's dgetrf structure).
 //
 // The working matrix W is row-major (see kernels.h).
+#include <chrono>
 #include <climits>
+#include <thread>
 #include <cstdio>
 #include <cstdlib>
 
@@ -450,7 +452,17 @@ cudaError_t launch_panel(T* Wkk, int64_t ldw, int m, int w, int kabs, int* ipiv,
   P.xrowj = (T*)s.xrowj;
   P.perm = s.perm;
   void* args[] = {&P};
-  return cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(PNL_THREADS), args, smem, st);
+  // A cooperative launch is refused (without side effects) while other
+  // in-flight cooperative grids -- other streams' panels -- hold the resources
+  // it needs; those grids always finish, so retry with a short back-off.
+  const auto t0 = std::chrono::steady_clock::now();
+  while (true) {
+    e = cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(PNL_THREADS), args, smem, st);
+    if (e != cudaErrorCooperativeLaunchTooLarge && e != cudaErrorLaunchOutOfResources) return e;
+    cudaGetLastError();
+    if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(2)) return e;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
 }
 
 // ============================================================ laswp

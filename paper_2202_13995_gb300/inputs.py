@@ -33,7 +33,7 @@ STREAM_B = 1
 
 __all__ = [
     "mix64_int", "stream_state", "uniform_np", "hpl_matrix", "hpl_rhs",
-    "hpl_matrix_torch", "hpl_rhs_torch", "uniform_torch",
+    "hpl_matrix_torch", "hpl_rhs_torch", "uniform_torch", "batch_shapes", "hpl_batch_torch",
 ]
 
 
@@ -144,3 +144,33 @@ def hpl_rhs_torch(n: int, nrhs: int, seed: int, device="cpu"):
     import torch
     k = torch.arange(n * nrhs, dtype=torch.int64, device=device)
     return uniform_torch(seed, STREAM_B, k).reshape(nrhs, n).t()
+
+
+def batch_shapes(count: int, seed: int, nmin: int = 32, nmax: int = 512, kmax: int = 8):
+    """Sizes of a batched workload: n ~ U{nmin..nmax}, nrhs ~ U{1..kmax} (seeded)."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(nmin, nmax + 1, size=count), rng.integers(1, kmax + 1, size=count)
+
+
+def hpl_batch_torch(ns, ks, seed: int, shift_per_n: float = 1.0, device="cuda"):
+    """Systems i = 0..count-1: A_i = uniform + shift_per_n * n_i * I (matrix seed
+    seed * 100000 + i), B_i uniform (same seed), each a column-major view into
+    one device buffer per kind.  Returns (A list, B list)."""
+    import torch
+    na = int(sum(int(n) * int(n) for n in ns))
+    nb = int(sum(int(n) * int(k) for n, k in zip(ns, ks)))
+    abuf = torch.empty(na, dtype=torch.float64, device=device)
+    bbuf = torch.empty(nb, dtype=torch.float64, device=device)
+    As, Bs = [], []
+    oa = ob = 0
+    for i, (n, k) in enumerate(zip(ns, ks)):
+        n, k = int(n), int(k)
+        a = abuf[oa:oa + n * n].view(n, n).t()  # column-major view, strides (1, n)
+        a.copy_(hpl_matrix_torch(n, seed * 100000 + i, diag_shift=shift_per_n * n, device=device))
+        b = bbuf[ob:ob + n * k].view(k, n).t()
+        b.copy_(hpl_rhs_torch(n, k, seed * 100000 + i, device=device))
+        As.append(a)
+        Bs.append(b)
+        oa += n * n
+        ob += n * k
+    return As, Bs

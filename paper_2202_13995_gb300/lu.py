@@ -29,11 +29,26 @@ EXPORTED = [
     "lu_solve", "lu_refine", "lu_scaled_residual", "lu_fact_free",
     "lu_step_panel", "lu_step_trsm", "lu_step_gemm", "lu_ctx_status", "lu_device_sm_count", "lu_build_tag",
     "lu_profile_enable", "lu_profile_read", "lu_launch_count", "lu_step_panel_static",
+    "lu_batch_create", "lu_batch_run", "lu_batch_shape", "lu_batch_free", "lu_solve_batched",
+    "lu_server_create", "lu_server_submit", "lu_server_poll", "lu_server_wait", "lu_server_stats",
+    "lu_server_destroy", "lu_fact_bytes",
 ]
 PHASES = ["panel", "laswp", "trsm", "cast", "gemm", "solve", "residual", "other"]
 
 _lock = threading.Lock()
 _lib = None
+
+
+class LuRequest(C.Structure):
+    _fields_ = [("n", C.c_int), ("nrhs", C.c_int), ("dA", C.c_void_p), ("lda", C.c_int), ("dB", C.c_void_p),
+                ("ldb", C.c_int), ("dX", C.c_void_p), ("ldx", C.c_int), ("factor_key", C.c_uint64),
+                ("keep_factor", C.c_int), ("use_resident", C.c_int)]
+
+
+class LuResult(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("scaled_resid", C.c_double), ("reused_factor", C.c_int),
+                ("refactored", C.c_int), ("slot", C.c_int), ("t_submit_ns", C.c_uint64), ("t_start_ns", C.c_uint64),
+                ("t_done_ns", C.c_uint64)]
 
 
 class LuError(RuntimeError):
@@ -79,6 +94,18 @@ def load():
             "lu_profile_read": (I, [P, DP, C.POINTER(C.c_longlong)]),
             "lu_launch_count": (C.c_longlong, [P]),
             "lu_step_panel_static": (I, [P, I, I, I, P, I, P, P, P]),
+            "lu_batch_create": (I, [P, I, IP, IP, P, IP, P, IP, P, IP, I, D, I, I, PP]),
+            "lu_batch_run": (I, [P, P, P, P]),
+            "lu_batch_shape": (I, [P, IP, IP, C.POINTER(C.c_float)]),
+            "lu_batch_free": (None, [P]),
+            "lu_solve_batched": (I, [P, I, IP, IP, P, IP, P, IP, I, P]),
+            "lu_server_create": (I, [PP, C.c_size_t, I, I]),
+            "lu_server_submit": (I, [P, C.POINTER(LuRequest), C.POINTER(C.c_uint64)]),
+            "lu_server_poll": (I, [P, C.c_uint64, C.POINTER(LuResult)]),
+            "lu_server_wait": (I, [P, C.c_uint64, C.POINTER(LuResult)]),
+            "lu_server_stats": (I, [P, C.POINTER(C.c_uint64), IP, C.POINTER(C.c_size_t), C.POINTER(C.c_uint64)]),
+            "lu_server_destroy": (I, [P]),
+            "lu_fact_bytes": (C.c_size_t, [I, I, I, I]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -119,6 +146,11 @@ def _rowmajor(t, name: str):
         raise ValueError(f"{name}: expected a row-major (m, n) tensor with strides (ld, 1)")
     ld = t.stride(0) if t.shape[0] > 1 else max(1, t.shape[1])
     return t.data_ptr(), max(1, ld)
+
+
+def fact_bytes(n: int, nrhs: int, prec="fp16", nb: int = 0) -> int:
+    """Device bytes lu_factor + lu_refine allocate for this system (budgeting)."""
+    return int(load().lu_fact_bytes(int(n), int(nrhs), _prec(prec), int(nb)))
 
 
 def colmajor_empty(n: int, k: int, device="cuda", dtype=None):
@@ -305,3 +337,130 @@ class Factor:
             return it.value, sr.value
         _check(rc, "lu_refine")
         return it.value, sr.value
+
+
+def _iarr(v):
+    a = (C.c_int * max(1, len(v)))()
+    for i, x in enumerate(v):
+        a[i] = int(x)
+    return a
+
+
+def _parr(tensors):
+    a = (C.c_void_p * max(1, len(tensors)))()
+    for i, t in enumerate(tensors):
+        a[i] = t.data_ptr()
+    return a
+
+
+class Batch:
+    """A planned batch of independent solves A_i X_i = B_i (n_i <= 512, nrhs_i <= 8),
+    FP32 factor + FP64 refinement, one persistent graph launch per run().
+
+    A, B, X are lists of column-major CUDA FP64 tensors ((n, n), (n, k), (n, k))."""
+
+    def __init__(self, ctx: Context, A, B, X, tol: float = 16.0, max_iter: int = 50, tune: bool = False,
+                 prec="f32"):
+        self.ctx = ctx
+        self._keep = (list(A), list(B), list(X))
+        cnt = len(A)
+        n, nrhs, lda, ldb, ldx = [], [], [], [], []
+        for a, b, x in zip(A, B, X):
+            _, la, _ = _colmajor(a, "A")
+            _, lb, kb = _colmajor(b, "B")
+            _, lx, _ = _colmajor(x, "X")
+            n.append(a.shape[0]); nrhs.append(kb); lda.append(la); ldb.append(lb); ldx.append(lx)
+        h = C.c_void_p()
+        self._h = None
+        rc = load().lu_batch_create(ctx.handle, cnt, _iarr(n), _iarr(nrhs), _parr(A), _iarr(lda), _parr(B),
+                                    _iarr(ldb), _parr(X), _iarr(ldx), _prec(prec), float(tol), int(max_iter),
+                                    1 if tune else 0, C.byref(h))
+        _check(rc, "lu_batch_create")
+        self._h = h
+        self.count = cnt
+
+    def run(self, info, iters=None, resid=None):
+        _check(load().lu_batch_run(self._h, C.c_void_p(info.data_ptr()),
+                                   C.c_void_p(iters.data_ptr()) if iters is not None else None,
+                                   C.c_void_p(resid.data_ptr()) if resid is not None else None), "lu_batch_run")
+
+    def shape(self):
+        t, c, ms = C.c_int(0), C.c_int(0), C.c_float(0.0)
+        _check(load().lu_batch_shape(self._h, C.byref(t), C.byref(c), C.byref(ms)), "lu_batch_shape")
+        return t.value, c.value, ms.value
+
+    def free(self):
+        if getattr(self, "_h", None):
+            load().lu_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def solve_batched(ctx: Context, A, B, info, prec="f32"):
+    """lu_solve_batched: B (list of (n, k) column-major tensors) is overwritten with X."""
+    n, nrhs, lda, ldb = [], [], [], []
+    for a, b in zip(A, B):
+        _, la, _ = _colmajor(a, "A")
+        _, lb, kb = _colmajor(b, "B")
+        n.append(a.shape[0]); nrhs.append(kb); lda.append(la); ldb.append(lb)
+    _check(load().lu_solve_batched(ctx.handle, len(A), _iarr(n), _iarr(nrhs), _parr(A), _iarr(lda), _parr(B),
+                                   _iarr(ldb), _prec(prec), C.c_void_p(info.data_ptr())), "lu_solve_batched")
+
+
+class Server:
+    """lu_server_*: continuous-batching solve server on the current device."""
+
+    def __init__(self, hbm_budget_bytes: int, prec="fp16", max_slots: int = 8):
+        h = C.c_void_p()
+        self._h = None
+        _check(load().lu_server_create(C.byref(h), int(hbm_budget_bytes), _prec(prec), int(max_slots)),
+               "lu_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, A, B, X, factor_key: int = 0, keep_factor: bool = False, use_resident: bool = False) -> int:
+        pa, lda, _ = _colmajor(A, "A")
+        pb, ldb, nrhs = _colmajor(B, "B")
+        px, ldx, _ = _colmajor(X, "X")
+        req = LuRequest(A.shape[0], nrhs, pa, lda, pb, ldb, px, ldx, int(factor_key), 1 if keep_factor else 0,
+                        1 if use_resident else 0)
+        t = C.c_uint64(0)
+        _check(load().lu_server_submit(self._h, C.byref(req), C.byref(t)), "lu_server_submit")
+        self._keep[t.value] = (A, B, X)
+        return t.value
+
+    def poll(self, ticket: int):
+        r = LuResult()
+        rc = load().lu_server_poll(self._h, int(ticket), C.byref(r))
+        if rc == LU_EAGAIN:
+            return None
+        _check(rc, "lu_server_poll")
+        self._keep.pop(int(ticket), None)
+        return r
+
+    def wait(self, ticket: int) -> "LuResult":
+        r = LuResult()
+        _check(load().lu_server_wait(self._h, int(ticket), C.byref(r)), "lu_server_wait")
+        self._keep.pop(int(ticket), None)
+        return r
+
+    def stats(self) -> dict:
+        d, rsd, b, ev = C.c_uint64(0), C.c_int(0), C.c_size_t(0), C.c_uint64(0)
+        _check(load().lu_server_stats(self._h, C.byref(d), C.byref(rsd), C.byref(b), C.byref(ev)), "lu_server_stats")
+        return {"done": d.value, "resident": rsd.value, "bytes_in_use": b.value, "evictions": ev.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lu_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
