@@ -58,6 +58,9 @@ def _load():
                 "orc_getrf": (I, [I, P, I, P]),
                 "orc_getrf_blocked": (I, [I, I, P, I, P]),
                 "orc_getrf_blocked_steps": (I, [I, I, P, I, P, I]),
+                "orc_getf2_nopiv": (I, [I, I, P, I]),
+                "orc_getrf_nopiv_blocked": (I, [I, I, P, I]),
+                "orc_trsm_right_upper": (None, [I, I, P, I, P, I]),
                 "orc_laswp": (None, [P, I, I, I, I, I, P]),
                 "orc_trsm_unit_lower": (None, [I, I, P, I, P, I]),
                 "orc_gemm_update": (None, [I, I, I, P, I, P, I, P, I]),
@@ -126,6 +129,28 @@ def getrf(A, nb: int | None = None, ksteps: int = -1, timed: bool = False):
     if timed:
         return LU, ipiv[:n], int(info), dt
     return LU, ipiv[:n], int(info)
+
+
+def getrf_nopiv(A, nb: int | None = None):
+    """LU without pivoting (the paper's HPL-AI variant): unblocked (nb None) or
+    the paper's blocked four-kernel iteration.  Returns (LU, info)."""
+    LU = _f64(A)
+    n = LU.shape[0]
+    lib = _load()
+    if nb is None:
+        info = lib.orc_getf2_nopiv(n, n, _ptr(LU), max(1, n))
+    else:
+        info = lib.orc_getrf_nopiv_blocked(n, int(nb), _ptr(LU), max(1, n))
+    return LU, int(info)
+
+
+def trsm_right_upper(B, U):
+    """B U^-1 for the upper triangle of the square matrix U."""
+    X = _f64(B)
+    Um = _f64(U)
+    m, w = X.shape
+    _load().orc_trsm_right_upper(m, w, _ptr(Um), max(1, Um.shape[0]), _ptr(X), max(1, m))
+    return X
 
 
 def laswp(A, c0: int, c1: int, k1: int, k2: int, ipiv):

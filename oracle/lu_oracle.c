@@ -20,6 +20,9 @@
  *     partial pivoting form one panel), apply its row interchanges to the other
  *     columns, update the "top" blocks with L (a unit-lower triangular solve),
  *     then update the "inner" blocks by a matrix multiplication;
+ *   - orc_getf2_nopiv / orc_getrf_nopiv_blocked: the paper's own variant
+ *     (HPL-AI rules: diagonally dominant A, no pivoting), unblocked and as the
+ *     paper's four-kernel blocked iteration (LU, top, left, inner);
  *   - orc_getrs: y = L^-1 P b, x = U^-1 y (HPL section, first paragraph);
  *   - residual and norms: r = b - A x and the HPL scaled residual
  *     ||r||_inf / (eps (||A||_inf ||x||_inf + ||b||_inf) n); the paper's own
@@ -171,6 +174,62 @@ int orc_getrf_blocked_steps(int n, int nb, double *A, int lda, int *ipiv, int ks
 
 int orc_getrf_blocked(int n, int nb, double *A, int lda, int *ipiv) {
     return orc_getrf_blocked_steps(n, nb, A, lda, ipiv, -1);
+}
+
+/* The paper's own variant (section "High Performance Linpack": HPL-AI rules,
+ * a diagonally dominant A, so the LU needs no pivoting), unblocked: Gaussian
+ * elimination without interchanges.  Returns info (first zero pivot) or 0. */
+int orc_getf2_nopiv(int m, int n, double *A, int lda) {
+    int info = 0;
+    int kmax = m < n ? m : n;
+    for (int j = 0; j < kmax; ++j) {
+        double piv = A[IDX(j, j, lda)];
+        if (piv != 0.0) {
+            for (int i = j + 1; i < m; ++i) A[IDX(i, j, lda)] = A[IDX(i, j, lda)] / piv;
+        } else if (info == 0) {
+            info = j + 1;
+        }
+        for (int c = j + 1; c < n; ++c) {
+            double u = A[IDX(j, c, lda)];
+            for (int i = j + 1; i < m; ++i) A[IDX(i, c, lda)] -= A[IDX(i, j, lda)] * u;
+        }
+    }
+    return info;
+}
+
+/* B <- B U^-1 for the upper triangle U (w x w, non-unit) of Um; B is m x w.
+ * Row by row: the paper's "left" block update with U. */
+void orc_trsm_right_upper(int m, int w, const double *Um, int ldu, double *B, int ldb) {
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < m; ++i) {
+        for (int j = 0; j < w; ++j) {
+            double v = B[IDX(i, j, ldb)];
+            for (int t = 0; t < j; ++t) v -= B[IDX(i, t, ldb)] * Um[IDX(t, j, ldu)];
+            B[IDX(i, j, ldb)] = v / Um[IDX(j, j, ldu)];
+        }
+    }
+}
+
+/* The paper's blocked iteration without pivoting (section "Base
+ * Implementation", figure "lu_iteration"): per block, the LU kernel on the
+ * diagonal block, the top blocks updated with L (A12 <- L11^-1 A12), the left
+ * blocks updated with U (A21 <- A21 U11^-1), and the inner blocks by a matrix
+ * multiplication (A22 <- A22 - A21 A12). */
+int orc_getrf_nopiv_blocked(int n, int nb, double *A, int lda) {
+    int info = 0;
+    for (int k = 0; k < n; k += nb) {
+        int w = (n - k) < nb ? (n - k) : nb;
+        int dinfo = orc_getf2_nopiv(w, w, A + IDX(k, k, lda), lda);
+        if (dinfo != 0 && info == 0) info = k + dinfo;
+        int rest = n - k - w;
+        if (rest > 0) {
+            orc_trsm_unit_lower(w, rest, A + IDX(k, k, lda), lda, A + IDX(k, k + w, lda), lda);
+            orc_trsm_right_upper(rest, w, A + IDX(k, k, lda), lda, A + IDX(k + w, k, lda), lda);
+            orc_gemm_update(rest, rest, w, A + IDX(k + w, k, lda), lda, A + IDX(k, k + w, lda), lda,
+                            A + IDX(k + w, k + w, lda), lda);
+        }
+    }
+    return info;
 }
 
 /* Unblocked factorization of the whole matrix (the definition). */

@@ -280,3 +280,52 @@ def test_round_16bit_library_pin_and_special_values():
     assert O.round_fp16(np.array([one + np.float32(2.0 ** -11)]))[0] == 1.0
     assert O.round_fp16(np.array([np.float32(65520.0)]))[0] == np.inf
     assert O.round_fp16(np.array([np.float32(65519.0)]))[0] == 65504.0
+
+
+# ----------------------------------------------------------------- the paper's no-pivot variant
+
+def test_nopiv_recovers_constructed_lu_exactly():
+    # A = L U with short dyadic entries (no interchanges): every step is exact
+    for n, nb in [(8, None), (64, None), (64, 16), (50, 7)]:
+        rng = np.random.default_rng(n + (nb or 0))
+        L = np.tril(rng.integers(-7, 8, size=(n, n)) / 8.0, -1) + np.eye(n)
+        U = np.triu(rng.integers(-16, 17, size=(n, n)).astype(np.float64))
+        U[np.arange(n), np.arange(n)] = rng.integers(1, 17, size=n)
+        LU, info = O.getrf_nopiv(L @ U, nb)
+        assert info == 0
+        assert np.array_equal(np.tril(LU, -1) + np.eye(n), L)
+        assert np.array_equal(np.triu(LU), U)
+
+
+def test_nopiv_equals_gepp_when_pivots_are_diagonal():
+    # the diagonal shift makes every partial pivot the diagonal: GEPP performs
+    # exactly the no-pivot operations, so the factors agree bit for bit
+    n = 300
+    A = I.hpl_matrix(n, 31, diag_shift=n / 4)
+    LUp, ipiv, _ = O.getrf(A)
+    assert np.array_equal(ipiv, np.arange(1, n + 1))
+    for nb in (None, 32, 64, 299):
+        LUn, info = O.getrf_nopiv(A, nb)
+        assert info == 0 and np.array_equal(LUn, LUp)
+
+
+def test_nopiv_bruteforce_rational():
+    for n in (2, 3, 5, 7):
+        rng = np.random.default_rng(40 + n)
+        A = rng.integers(-9, 10, size=(n, n)) + np.diag(rng.integers(30, 40, size=n))
+        M = [[Fraction(int(v)) for v in row] for row in A]
+        for j in range(n):
+            for i in range(j + 1, n):
+                M[i][j] = M[i][j] / M[j][j]
+                for c in range(j + 1, n):
+                    M[i][c] -= M[i][j] * M[j][c]
+        LU, info = O.getrf_nopiv(A.astype(np.float64))
+        want = np.array([[float(v) for v in r] for r in M])
+        assert np.allclose(LU, want, rtol=0, atol=64 * n * EPS * 40)
+
+
+def test_trsm_right_upper_library_pin():
+    rng = np.random.default_rng(8)
+    U = np.triu(rng.uniform(-1, 1, (20, 20))) + 4 * np.eye(20)
+    B = rng.uniform(-1, 1, (13, 20))
+    assert np.allclose(O.trsm_right_upper(B, U), B @ np.linalg.inv(U), rtol=0, atol=1e-12)
