@@ -40,12 +40,23 @@ WORKLOADS = {
     "hpl_mixed_bf16_n32768": dict(n=32768, nb=0, prec="bf16", nrhs=1, seed=3, shift=0.25),
     "hpl_mixed_fp16_n32768": dict(n=32768, nb=0, prec="fp16", nrhs=1, seed=3, shift=0.25),
     "hpl_mixed_bf16_n32768_rhs32": dict(n=32768, nb=0, prec="bf16", nrhs=32, seed=3, shift=0.25),
+    # the paper's own variant (HPL-AI rules: no pivoting on a diagonally dominant
+    # A): BF16 tensor-core factor + FP64 refinement, and FP32 without refinement
+    "hpl_nopiv_bf16_n32768": dict(n=32768, nb=0, prec="bf16", nrhs=1, seed=3, shift=0.25, nopiv=True),
+    "hpl_nopiv_f32_n32768": dict(n=32768, nb=256, prec="f32", nrhs=1, seed=3, shift=0.25, nopiv=True,
+                                 norefine=True),
     # smaller cases of the same shapes (profiling captures)
     "hpl_f64_n4096_nb256": dict(n=4096, nb=256, prec="f64", nrhs=1, seed=2, shift=0.0),
     "hpl_mixed_bf16_n8192": dict(n=8192, nb=0, prec="bf16", nrhs=1, seed=3, shift=0.25),
+    "hpl_nopiv_bf16_n8192": dict(n=8192, nb=0, prec="bf16", nrhs=1, seed=3, shift=0.25, nopiv=True),
     # the batched configuration: 4096 systems, n ~ U{32..512}, 1-8 right-hand
     # sides, A + n I, FP32 factor + FP64 refinement, one persistent launch
     "batched_4096": dict(count=4096, nmin=32, nmax=512, kmax=8, seed=5, prec="f32"),
+    # the served configuration: Poisson arrivals, n log-uniform 64..8192, 1-16
+    # right-hand sides, 30% repeat-RHS on resident factors, FP16 factor + FP64
+    # refinement, admission by a 120 GB HBM budget
+    "served_2000": dict(rate=2000.0, seconds=5.0, nmin=64, nmax=8192, kmax=16, repeat=0.3, seed=6, prec="fp16",
+                        budget_gb=120, slots=8, pool=48),
 }
 DEFAULT = "hpl_f64_n16384_nb256"
 METRIC = "LU solve TFLOP/s (HPL count 2/3 n^3 + 2 n^2 nrhs) at scaled residual < 16"
@@ -283,9 +294,12 @@ def timed_solves(ctx, stream, cfg: dict, nb, steps: int, warmup: int, rank: int,
     torch.cuda.synchronize()
     iters = []
 
+    nopiv = bool(cfg.get("nopiv", False))
+    refine = mixed and not cfg.get("norefine", False)
+
     def step():
-        f = ctx.factor(A, prec, nb, sync=False)
-        if mixed:
+        f = ctx.factor(A, prec, nb, sync=False, nopiv=nopiv)
+        if refine:
             iters.append(f.refine(A, B, X, 16.0, 50)[0])
         else:
             X.copy_(B)
@@ -359,6 +373,69 @@ def batched_measure(ctx, stream, cfg: dict, steps: int, warmup: int, tune: bool 
     return out
 
 
+def served_measure(cfg: dict, rate: float = None, seconds: float = None) -> dict:
+    """Replay a seeded Poisson request stream against lu_server and report
+    throughput and latency (t_done - t_submit, queueing included)."""
+    import time as _t
+    import numpy as np
+    import torch
+    from paper_2202_13995_gb300 import inputs as I
+    from paper_2202_13995_gb300 import lu
+    rate = rate or cfg["rate"]
+    seconds = seconds or cfg["seconds"]
+    rng = np.random.default_rng(cfg["seed"])
+    # a pool of distinct systems (A + (n/4) I) the requests draw from
+    pool_n = np.exp(rng.uniform(np.log(cfg["nmin"]), np.log(cfg["nmax"]), cfg["pool"])).astype(int)
+    pool_A = [I.hpl_matrix_torch(int(n), 600000 + i, diag_shift=n / 4.0, device="cuda") for i, n in enumerate(pool_n)]
+    pool_B = [I.hpl_rhs_torch(int(n), cfg["kmax"], 600000 + i, device="cuda").contiguous().t().contiguous().t()
+              for i, n in enumerate(pool_n)]
+    torch.cuda.synchronize()
+    nreq = int(rate * seconds)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
+    picks = rng.integers(0, cfg["pool"], nreq)
+    ks = rng.integers(1, cfg["kmax"] + 1, nreq)
+    rep = rng.uniform(0, 1, nreq) < cfg["repeat"]
+    srv = lu.Server(int(cfg["budget_gb"]) << 30, cfg["prec"], max_slots=cfg["slots"])
+    kept = set()
+    tickets, flops = [], 0.0
+    t0 = _t.perf_counter()
+    for i in range(nreq):
+        while _t.perf_counter() - t0 < arrivals[i]:
+            _t.sleep(min(2e-4, max(0.0, arrivals[i] - (_t.perf_counter() - t0))))
+        p = int(picks[i])
+        n, k = int(pool_n[p]), int(ks[i])
+        X = lu.colmajor_empty(n, k)
+        B = pool_B[p][:, :k]
+        repeat = bool(rep[i]) and p in kept
+        if repeat:
+            t = srv.submit(pool_A[p], B, X, factor_key=p + 1, use_resident=True)
+        else:
+            t = srv.submit(pool_A[p], B, X, factor_key=p + 1, keep_factor=True)
+            kept.add(p)
+        tickets.append((t, n, k, repeat))
+    res = [srv.wait(t) for t, _, _, _ in tickets]
+    t_end = _t.perf_counter()
+    stats = srv.stats()
+    srv.close()
+    lat = np.array([(r.t_done_ns - r.t_submit_ns) * 1e-6 for r in res])
+    svc = np.array([(r.t_done_ns - r.t_start_ns) * 1e-6 for r in res])
+    span = (max(r.t_done_ns for r in res) - min(r.t_submit_ns for r in res)) * 1e-9
+    for r, (_, n, k, _) in zip(res, tickets):
+        flops += (0.0 if r.reused_factor else 2.0 / 3.0 * n ** 3) + 2.0 * n * n * k * (1 + r.iters)
+    ok = sum(1 for r in res if r.status == 0)
+    status_hist = {}
+    for r in res:
+        status_hist[str(r.status)] = status_hist.get(str(r.status), 0) + 1
+    return {"workload": "served", "offered_rate_per_s": rate, "seconds_of_arrivals": seconds, "requests": nreq,
+            "completed_ok": ok, "status_counts": status_hist, "solves_per_s": nreq / span, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "service_p50_ms": float(np.percentile(svc, 50)),
+            "reused_factor": int(sum(r.reused_factor for r in res)),
+            "refactored": int(sum(r.refactored for r in res)), "evictions": int(stats["evictions"]),
+            "max_scaled_residual": float(max(r.scaled_resid for r in res)), "tflops": flops / span / 1e12,
+            "slots": cfg["slots"], "budget_gb": cfg["budget_gb"], "prec": cfg["prec"],
+            "wall_s": t_end - t0}
+
+
 def run_ours(args, cfg, wname):
     import torch
     from paper_2202_13995_gb300 import lu
@@ -426,7 +503,20 @@ def run_ours(args, cfg, wname):
     # ---- the mixed-precision companion: BF16 tensor-core factor + FP64
     #      refinement on A + (n/4) I, n = 32768 (same timing rules)
     mixed_line = None
+    nopiv_line = None
     if not mixed and not args.no_mixed and wname == DEFAULT:
+        # the paper's own variant on the mixed configuration's matrix
+        pname = "hpl_nopiv_bf16_n32768"
+        pc = WORKLOADS[pname]
+        pr = timed_solves(ctx, stream, pc, pc["nb"], args.steps, args.warmup, rank, ws)
+        pv = hpl_flops(pc["n"], pc["nrhs"]) * ws / (pr["ms"] * 1e-3) / 1e12
+        nopiv_line = {"workload": pname, "value": pv, "unit": "TFLOP/s", "ms_per_step": pr["ms"],
+                      "lu_only_tflops": 2.0 / 3.0 * pc["n"] ** 3 * ws / (pr["ms"] * 1e-3) / 1e12,
+                      "scaled_residual": pr["res"], "refine_iters": pr["refine_iters"],
+                      "phases_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in pr["prof"].items()}}
+        launches += pr["launches"]
+        del pr
+        torch.cuda.empty_cache()
         mname = "hpl_mixed_bf16_n32768"
         mc = WORKLOADS[mname]
         mr = timed_solves(ctx, stream, mc, mc["nb"], args.steps, args.warmup, rank, ws)
@@ -470,6 +560,7 @@ def run_ours(args, cfg, wname):
             "phases_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in prof.items()},
             "clocks": ck,
             "mixed": mixed_line,
+            "paper_nopiv": nopiv_line,
             "batched": batched_line,
         }
         print(json.dumps(line), flush=True)
@@ -493,8 +584,23 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--nb", type=int, default=None, help="block width override (0 = library default)")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision companion measurement")
+    ap.add_argument("--rate", type=float, default=None, help="served: offered requests per second")
+    ap.add_argument("--seconds", type=float, default=None, help="served: seconds of arrivals")
     args = ap.parse_args()
     cfg = WORKLOADS[args.workload]
+    if args.workload.startswith("served"):
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the served workload has no CPU reference arm"}))
+            return 0
+        import torch
+        torch.cuda.set_device(0)
+        r = served_measure(cfg, args.rate, args.seconds)
+        line = {"metric": "served solves/s, p50/p99 latency ms", "value": r["solves_per_s"], "unit": "solves/s",
+                "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": r["wall_s"] * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "fp16+f32acc+f64refine", "data": "synthetic",
+                "config": {"workload": args.workload}, "served": r}
+        print(json.dumps(line), flush=True)
+        return 0
     if args.workload == "batched_4096":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no CPU reference arm; "

@@ -80,6 +80,27 @@ const char *lu_strerror(int code);
  * seen when info is non-NULL). */
 int lu_factor(lu_ctx ctx, int n, const double *dA, int lda, lu_prec prec, int nb, lu_fact *out, int *info);
 
+/* lu_factor with options.  flags = 0 is lu_factor.  LU_FACTOR_NOPIV: the
+ * paper's own variant (HPL-AI rules: A diagonally dominant, so no pivoting;
+ * section "High Performance Linpack"), with its four block operations per
+ * iteration: LU of the diagonal block, top blocks A12 <- L11^-1 A12, left
+ * blocks A21 <- A21 U11^-1, inner blocks A22 <- A22 - A21 A12.  ipiv is then
+ * the identity.  Without diagonal dominance this variant can be unstable or
+ * hit a zero pivot (info > 0).
+ * LU_FACTOR_OZAKI (prec = LU_F64 only, nb <= 256): the FP64 trailing update
+ * C -= L21 U12 (section "Base Implementation", the inner blocks) runs on the
+ * BF16 tensor cores by error-free splitting (Ozaki scheme): each operand row
+ * or column is scaled by a power of two and cut into 8 slices of 7-bit
+ * integers, the 36 slice products with p + q <= 7 are exact in the FP32
+ * accumulator, and they are combined exactly in 64-bit integers before one
+ * FP64 rounding.  The error of an update element is below about
+ * 1.2 * 2^-53 * k * 2^(e_i + f_j), with 2^e_i and 2^f_j the powers of two just
+ * above the largest |L21| of row i and |U12| of column j: the order of an FP64
+ * dot product's error bound.  Non-finite operands fail with LU_ERANGE. */
+enum { LU_FACTOR_NOPIV = 1, LU_FACTOR_OZAKI = 2 };
+int lu_factor_ex(lu_ctx ctx, int n, const double *dA, int lda, lu_prec prec, int nb, int flags, lu_fact *out,
+                 int *info);
+
 /* Synchronize and read the LAPACK info of a factorization (and the device
  * status: LU_ETIMEOUT / LU_ERANGE when raised). */
 int lu_fact_info(lu_fact f, int *info);

@@ -15,6 +15,10 @@
  * oldest queued request whose memory fits the HBM budget (factor working copy,
  * operands, scratch and refinement vectors, counted exactly as the library
  * allocates them), evicting least-recently-used resident factors first.
+ * Requests overlap on the device, factorizations included: the trailing-update
+ * CTAs leave room for a panel CTA on every SM, and a cooperative panel launch
+ * that finds no room retries (bounded).  The environment variable
+ * GB300LU_SERVER_SERIAL_FACTOR runs factorizations one at a time instead.
  *
  * Resident factors: a request with keep_factor != 0 leaves its factor resident
  * under factor_key (counted in the budget).  A later request with the same

@@ -68,6 +68,15 @@ int lu_step_trsm(lu_ctx ctx, lu_prec prec, int w, int N, const void *dL, int ldl
 int lu_step_gemm(lu_ctx ctx, lu_prec prec, int m, int n, int k, void *dC, int ldc, const void *dA, int lda,
                  const void *dB, int ldb);
 
+/* Inner-block update C -= A B in FP64 (row-major FP64 device arrays, C m x n,
+ * A m x k, B k x n, 1 <= k <= 256) with the products on the BF16 tensor cores
+ * by error-free splitting, as lu_factor_ex's LU_FACTOR_OZAKI (same error
+ * bound).  Workspace: the context's step scratch (grown as needed).  Returns
+ * -5 for k outside 1..256, LU_ERANGE (at the next lu_ctx_status) for
+ * non-finite operands. */
+int lu_step_gemm_ozaki(lu_ctx ctx, int m, int n, int k, double *dC, int ldc, const double *dA, int lda,
+                       const double *dB, int ldb);
+
 /* Read and clear the context's device status bits (synchronizes): returns
  * LU_OK, LU_ETIMEOUT or LU_ERANGE. */
 int lu_ctx_status(lu_ctx ctx);

@@ -64,6 +64,7 @@ def _load():
                 "orc_laswp": (None, [P, I, I, I, I, I, P]),
                 "orc_trsm_unit_lower": (None, [I, I, P, I, P, I]),
                 "orc_gemm_update": (None, [I, I, I, P, I, P, I, P, I]),
+                "orc_gemm_update_dot2": (None, [I, I, I, P, I, P, I, P, I]),
                 "orc_getrs": (None, [I, I, P, I, P, P, I]),
                 "orc_residual": (None, [I, I, P, I, P, I, P, I, P, I]),
                 "orc_norm_inf_mat": (D, [I, I, P, I]),
@@ -178,6 +179,18 @@ def gemm_update(Cm, A, B):
     k2, n = Bm.shape
     assert k == k2 and out.shape == (m, n)
     _load().orc_gemm_update(m, n, k, _ptr(Am), max(1, m), _ptr(Bm), max(1, k), _ptr(out), max(1, m))
+    return out
+
+
+def gemm_update_dot2(Cm, A, B):
+    """C - A B as if computed in twice FP64 precision and rounded once (Dot2)."""
+    out = _f64(Cm)
+    Am = _f64(A)
+    Bm = _f64(B)
+    m, k = Am.shape
+    k2, n = Bm.shape
+    assert k == k2 and out.shape == (m, n)
+    _load().orc_gemm_update_dot2(m, n, k, _ptr(Am), max(1, m), _ptr(Bm), max(1, k), _ptr(out), max(1, m))
     return out
 
 

@@ -35,6 +35,11 @@
  *   - orc_round_bf16 / orc_round_fp16: round-to-nearest-even of an FP32 value
  *     to bfloat16 / IEEE binary16, from the formats' definitions;
  *   - orc_gemm_update: C - A B in FP64, the inner-block update.
+ *   - orc_gemm_update_dot2: the same update as accurately as if computed in
+ *     twice the working precision and rounded once (the Dot2 algorithm of
+ *     T. Ogita, S. M. Rump, S. Oishi, "Accurate sum and dot product", SIAM J.
+ *     Sci. Comput. 26, 2005): the reference for an update whose own error is of
+ *     the order of FP64 rounding (the error-free-splitting update).
  *
  * Matrices are column-major with a leading dimension; sizes are int64 inside.
  * Compiled with -ffp-contract=off so that x86 and Arm builds round the same way.
@@ -132,6 +137,42 @@ void orc_trsm_unit_lower(int nb, int ncol, const double *Lm, int ldl, double *B,
 
 /* C <- C - A B with A m x k, B k x n, C m x n (the "inner" block update).  Each
  * element accumulates its k products in order of increasing k. */
+/* Error-free transformations: s + e = a + b exactly (Knuth's TwoSum), and
+ * p + e = a * b exactly (TwoProduct; fma() rounds once, so e is exact). */
+static void two_sum(double a, double b, double *s, double *e) {
+    const double x = a + b;
+    const double z = x - a;
+    *e = (a - (x - z)) + (b - z);
+    *s = x;
+}
+
+static void two_prod(double a, double b, double *p, double *e) {
+    const double x = a * b;
+    *e = fma(a, b, -x);
+    *p = x;
+}
+
+/* C <- C - A B, each element by Dot2 over the k + 1 terms C(i,j), -A(i,kk) B(kk,j):
+ * the running sum s and the compensation c (sum of every rounding error)
+ * are added at the end.  The result's error is below
+ * u |exact| + gamma_{k+1}^2 (|C| + |A| |B|), gamma_j = j u / (1 - j u). */
+void orc_gemm_update_dot2(int m, int n, int k, const double *Am, int lda, const double *Bm, int ldb,
+                          double *C, int ldc) {
+#pragma omp parallel for schedule(static)
+    for (int c = 0; c < n; ++c) {
+        for (int i = 0; i < m; ++i) {
+            double s = C[IDX(i, c, ldc)], comp = 0.0;
+            for (int kk = 0; kk < k; ++kk) {
+                double p, q, r;
+                two_prod(-Am[IDX(i, kk, lda)], Bm[IDX(kk, c, ldb)], &p, &q);
+                two_sum(s, p, &s, &r);
+                comp += q + r;
+            }
+            C[IDX(i, c, ldc)] = s + comp;
+        }
+    }
+}
+
 void orc_gemm_update(int m, int n, int k, const double *Am, int lda, const double *Bm, int ldb,
                      double *C, int ldc) {
 #pragma omp parallel for schedule(static)

@@ -452,10 +452,10 @@ static int occupancy(int threads) {
   int per = 0;
   const size_t smem = sizeof(BatchSmem);
   if (threads == 512) {
-    cudaFuncSetAttribute(batched_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem((const void*)batched_kernel<512>);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_kernel<512>, 512, smem);
   } else {
-    cudaFuncSetAttribute(batched_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem((const void*)batched_kernel<256>);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_kernel<256>, 256, smem);
   }
   return per;

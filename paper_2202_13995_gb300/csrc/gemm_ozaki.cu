@@ -1,0 +1,592 @@
+// FP64 trailing update C -= A B on the BF16 tensor cores by error-free
+// splitting (the Ozaki scheme: K. Ozaki, T. Ogita, S. Oishi, S. M. Rump,
+// "Error-free transformations of matrix multiplication by using fast routines
+// of matrix multiplication and its applications", Numer. Algorithms 59, 2012;
+// on tensor cores: D. Mukunoki, K. Ozaki, T. Ogita, T. Imamura, "DGEMM using
+// Tensor Cores, and Its Accurate and Reproducible Versions", ISC 2020).
+//
+// This is the paper's "inner" block update (arxiv 2202.13995, section "Base
+// Implementation") in FP64 accuracy without FP64 multiply-adds for the
+// products: GB300's FP64 rate is a small fraction of its BF16 tensor rate, and
+// tcgen05 has no FP64 kind.
+//
+// Splitting.  Row i of A is scaled by 2^-e_i (2^e_i the power of two just
+// above its largest |a|) and cut into S = 8 slices of 7-bit integers d_p:
+//   a = 2^e_i * sum_p d_p 2^(-7(p+1))  + (remainder below 2^(e_i - 56)).
+// Column j of B likewise (2^f_j, slices g_q).  Every slice is an integer in
+// [-127, 127], exact in BF16.
+//
+// Products.  For each slice pair (p, q) with t = p + q <= S - 1 (36 pairs) the
+// tensor cores form G = sum_k d_p(i,k) g_q(k,j) over the full k <= 256: an
+// integer of magnitude < 256 * 127^2 < 2^22, exact in the FP32 accumulator.
+//
+// Combination, exact and in integers.  G + 1.5 * 2^23 is exact in FP32 and
+// its bit pattern is 0x4B400000 + G; the epilogue adds that pattern, shifted
+// by 40 - 7t, into a 64-bit integer per element (the constant part is
+// subtracted once at the end).  The sum I is the product's scaled value with
+// 40 fraction bits below the t = 0 term; |I| < 2^63 by the bound on G.  The
+// two smallest terms (t = 6, 7) are shifted right, which truncates them below
+// 2^-40 of the t = 0 unit.  Finally C -= I * 2^(e_i + f_j - 54), one rounding.
+//
+// Error.  The dropped pairs (t >= 8) and the splitting remainders bound the
+// error by about 1.2 * 2^-53 * k * 2^(e_i + f_j), the same order as the
+// rounding error bound of a k-term FP64 dot product.
+//
+// Kernel.  Persistent CTAs (one per SM) walk 128 x 128 output tiles.  For a
+// tile, A's slice p (128 rows x k) sits in shared memory (double-buffered, the
+// next slice loads while the current one is used) while B's slices q stream
+// through a 6-stage ring; warp 0 issues the TMA loads, warp 1 the tcgen05.mma
+// (M = 128, N = 128, K = 16) into one of four TMEM accumulators per pair, and
+// warps 2..9 drain each finished accumulator into their 64 per-thread 64-bit
+// sums, then update C.  Every mbarrier wait is bounded; on timeout the kernel
+// raises ST_TIMEOUT, lets issued copies and MMAs land, frees TMEM and returns.
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_ptx.cuh"
+
+namespace gb {
+
+constexpr int OZ_S = 8;        // slices per operand
+constexpr int OZ_BITS = 7;     // bits per slice
+constexpr int OZ_KMAX = 256;   // exactness bound on k (k * 127^2 < 2^22)
+constexpr int OZ_F = 40;       // fraction bits of the integer sum below the t = 0 term
+constexpr int OZ_BM = 128, OZ_BN = 128, OZ_BK = 64;
+constexpr int OZ_CHUNK = OZ_BM * OZ_BK * 2;          // 16 KB: one 128 x 64 BF16 box (A or B)
+constexpr int OZ_ABUF = (OZ_KMAX / OZ_BK) * OZ_CHUNK;  // 64 KB: one resident A slice
+constexpr int OZ_BSTAGES = 6;
+constexpr int OZ_NACC = 4;     // TMEM accumulators of 128 columns
+constexpr int OZ_EPI_WARPS = 8;
+constexpr int OZ_THREADS = 32 * (2 + OZ_EPI_WARPS);
+constexpr int OZ_TMEM_COLS = OZ_NACC * OZ_BN;
+constexpr size_t OZ_SMEM = 1024 + 2 * (size_t)OZ_ABUF + (size_t)OZ_BSTAGES * OZ_CHUNK + 256;
+constexpr uint32_t OZ_MAGIC_BITS = 0x4B400000u;  // bit pattern of 1.5 * 2^23
+constexpr float OZ_MAGIC = 12582912.0f;
+
+static_assert(OZ_KMAX * 127 * 127 < (1 << 22), "a slice-pair product must stay below 2^22");
+static_assert(OZ_SMEM <= 232448, "shared memory per CTA");
+
+// ------------------------------------------------------------ splitting
+// A (m x k, row-major FP64) -> As[p][i][kpad] (BF16 integers), ea[i] = e_i.
+// One warp per row.
+__global__ void __launch_bounds__(256) oz_split_rows_kernel(const double* __restrict__ A, int64_t lda, int m, int k,
+                                                            int kpad, __nv_bfloat16* __restrict__ As,
+                                                            int* __restrict__ ea, int* status) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i >= m) return;
+  double v[OZ_KMAX / 32];
+  double mx = 0.0;
+  bool bad = false;
+#pragma unroll
+  for (int u = 0; u < OZ_KMAX / 32; ++u) {
+    const int c = lane + 32 * u;
+    v[u] = c < k ? A[(int64_t)i * lda + c] : 0.0;
+    bad |= !isfinite(v[u]);
+    mx = fmax(mx, fabs(v[u]));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if (__any_sync(0xffffffffu, bad)) {
+    if (lane == 0) atomicOr(status, ST_RANGE);
+    mx = 0.0;
+  }
+  const int e = mx > 0.0 ? ilogb(mx) + 1 : 0;  // mx < 2^e
+  if (lane == 0) ea[i] = e;
+#pragma unroll
+  for (int u = 0; u < OZ_KMAX / 32; ++u) {
+    const int c = lane + 32 * u;
+    if (c >= kpad) continue;
+    double r = mx > 0.0 ? ldexp(v[u], -e) : 0.0;  // |r| < 1
+#pragma unroll
+    for (int p = 0; p < OZ_S; ++p) {
+      r *= (double)(1 << OZ_BITS);
+      const double d = trunc(r);
+      r -= d;
+      As[((int64_t)p * m + i) * kpad + c] = __double2bfloat16(d);
+    }
+  }
+}
+
+// B (k x n, row-major FP64) -> Bs[q][j][kpad] (column j's slice, K contiguous),
+// fb[j] = f_j.  CTA = 32 columns.
+__global__ void __launch_bounds__(256) oz_split_cols_kernel(const double* __restrict__ B, int64_t ldb, int k, int n,
+                                                            int kpad, __nv_bfloat16* __restrict__ Bs,
+                                                            int* __restrict__ fb, int* status) {
+  __shared__ double tile[OZ_BK][33];
+  __shared__ double red[8][32];
+  __shared__ int fe[32];
+  constexpr int ZERO_COL = 1 << 20;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j0 = blockIdx.x * 32, j = j0 + lane;
+  double mx = 0.0;
+  bool bad = false;
+  for (int r = warp; r < k; r += 8) {
+    const double x = j < n ? B[(int64_t)r * ldb + j] : 0.0;
+    bad |= !isfinite(x);
+    mx = fmax(mx, fabs(x));
+  }
+  red[warp][lane] = bad ? -1.0 : mx;
+  __syncthreads();
+  if (warp == 0) {
+    bool b2 = false;
+    mx = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      b2 |= red[w][lane] < 0.0;
+      mx = fmax(mx, red[w][lane]);
+    }
+    if (b2) {
+      atomicOr(status, ST_RANGE);
+      mx = 0.0;
+    }
+    const int e = mx > 0.0 ? ilogb(mx) + 1 : 0;
+    fe[lane] = mx > 0.0 ? e : ZERO_COL;
+    if (j < n) fb[j] = e;
+  }
+  __syncthreads();
+  for (int r0 = 0; r0 < kpad; r0 += OZ_BK) {
+    for (int r = warp; r < OZ_BK; r += 8)
+      tile[r][lane] = (r0 + r < k && j < n) ? B[(int64_t)(r0 + r) * ldb + j] : 0.0;
+    __syncthreads();
+    for (int c = warp; c < 32; c += 8) {
+      const int jj = j0 + c;
+      if (jj >= n) continue;
+      const int e = fe[c];
+#pragma unroll
+      for (int h = 0; h < OZ_BK / 32; ++h) {
+        const int r = h * 32 + lane;
+        double x = e == ZERO_COL ? 0.0 : ldexp(tile[r][c], -e);
+#pragma unroll
+        for (int q = 0; q < OZ_S; ++q) {
+          x *= (double)(1 << OZ_BITS);
+          const double d = trunc(x);
+          x -= d;
+          Bs[((int64_t)q * n + jj) * kpad + r0 + r] = __double2bfloat16(d);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ the product kernel
+struct OzParams {
+  double* C;
+  int64_t ldc;
+  int m, n;        // rows and columns of this update
+  int a_rows;      // rows of one A slice in the slice array
+  int b_rows;      // columns of one B slice in the slice array
+  int b_col0;      // first column of this update within the split
+  int kchunks;
+  int tiles_m, tiles_n;
+  const int* ea;   // row exponents e_i
+  const int* fb;   // column exponents f_j of this update's columns
+  uint32_t idesc;
+  int* status;
+};
+
+// a[j] += (pattern of G + 1.5 * 2^23) shifted by SH (right for SH < 0)
+template <int SH>
+__device__ __forceinline__ void oz_acc32(unsigned long long* a, const uint32_t* v) {
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const uint32_t b = __float_as_uint(__uint_as_float(v[j]) + OZ_MAGIC);
+    if constexpr (SH >= 0)
+      a[j] += (unsigned long long)b << SH;
+    else
+      a[j] += (unsigned long long)(b >> (-SH));
+  }
+}
+
+__device__ __forceinline__ void oz_acc_t(int t, unsigned long long* a, const uint32_t* v) {
+  switch (t) {
+    case 0: oz_acc32<OZ_F>(a, v); break;
+    case 1: oz_acc32<OZ_F - 7>(a, v); break;
+    case 2: oz_acc32<OZ_F - 14>(a, v); break;
+    case 3: oz_acc32<OZ_F - 21>(a, v); break;
+    case 4: oz_acc32<OZ_F - 28>(a, v); break;
+    case 5: oz_acc32<OZ_F - 35>(a, v); break;
+    case 6: oz_acc32<OZ_F - 42>(a, v); break;
+    default: oz_acc32<OZ_F - 49>(a, v); break;
+  }
+}
+
+__device__ __forceinline__ unsigned long long oz_corr(int t) {
+  const int sh = OZ_F - OZ_BITS * t;
+  return sh >= 0 ? (unsigned long long)OZ_MAGIC_BITS << sh : (unsigned long long)(OZ_MAGIC_BITS >> (-sh));
+}
+
+__global__ void __maxnreg__(200)
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzParams P) {
+  extern __shared__ unsigned char smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = smem_raw + (base - raw);
+  const uint32_t sA = base;                 // 2 x OZ_ABUF
+  const uint32_t sB = base + 2 * OZ_ABUF;   // OZ_BSTAGES x OZ_CHUNK
+  unsigned char* ctl = gbase + 2 * OZ_ABUF + OZ_BSTAGES * OZ_CHUNK;
+  const uint32_t bar_afull = smem_u32(ctl);
+  const uint32_t bar_aempty = bar_afull + 16;
+  const uint32_t bar_bfull = bar_aempty + 16;
+  const uint32_t bar_bempty = bar_bfull + 8 * OZ_BSTAGES;
+  const uint32_t bar_tfull = bar_bempty + 8 * OZ_BSTAGES;
+  const uint32_t bar_tempty = bar_tfull + 8 * OZ_NACC;
+  const uint32_t bar_drain = bar_tempty + 8 * OZ_NACC;
+  constexpr int NBAR = 4 + 2 * OZ_BSTAGES + 2 * OZ_NACC + 1;
+  static_assert(8 * NBAR + 16 <= 256, "control block");
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ctl + 8 * NBAR);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(ctl + 8 * NBAR + 8);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntiles = P.tiles_m * P.tiles_n;
+
+  if (threadIdx.x == 0) {
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(bar_afull + 8 * a, 1);
+      mbar_init(bar_aempty + 8 * a, 1);
+    }
+    for (int s = 0; s < OZ_BSTAGES; ++s) {
+      mbar_init(bar_bfull + 8 * s, 1);
+      mbar_init(bar_bempty + 8 * s, 1);
+    }
+    for (int a = 0; a < OZ_NACC; ++a) {
+      mbar_init(bar_tfull + 8 * a, 1);
+      mbar_init(bar_tempty + 8 * a, OZ_EPI_WARPS);
+    }
+    mbar_init(bar_drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(OZ_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      int apar[2] = {-1, -1};
+      int bpar[OZ_BSTAGES];
+#pragma unroll
+      for (int s = 0; s < OZ_BSTAGES; ++s) bpar[s] = -1;
+      int s = 0, ab = 0;
+      uint32_t ph = 0, abph = 0;
+      bool ok = true;
+      // A slices load one slice ahead, into the buffer the MMA released last:
+      // slice (tile, p + 1) is issued once the B chunks of (p, q = 0) are.
+      auto load_a = [&](int tile, int p) -> bool {
+        if (!mbar_wait(bar_aempty + 8 * ab, abph ^ 1u, P.status, abort_flag)) return false;
+        const int tm = tile % P.tiles_m;
+        mbar_expect_tx(bar_afull + 8 * ab, (uint32_t)(P.kchunks * OZ_CHUNK));
+        for (int kc = 0; kc < P.kchunks; ++kc)
+          tma_load_2d(sA + ab * OZ_ABUF + kc * OZ_CHUNK, &tmA, kc * OZ_BK, p * P.a_rows + tm * OZ_BM,
+                      bar_afull + 8 * ab);
+        apar[ab] = (int)abph;
+        if (++ab == 2) {
+          ab = 0;
+          abph ^= 1u;
+        }
+        return true;
+      };
+      if ((int)blockIdx.x < ntiles) ok = load_a(blockIdx.x, 0);
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        const int tn = t / P.tiles_m;
+        for (int p = 0; p < OZ_S && ok; ++p) {
+          for (int q = 0; q < OZ_S - p && ok; ++q) {
+            for (int kc = 0; kc < P.kchunks; ++kc) {
+              if (!mbar_wait(bar_bempty + 8 * s, ph ^ 1u, P.status, abort_flag)) {
+                ok = false;
+                break;
+              }
+              mbar_expect_tx(bar_bfull + 8 * s, OZ_CHUNK);
+              tma_load_2d(sB + s * OZ_CHUNK, &tmB, kc * OZ_BK, q * P.b_rows + P.b_col0 + tn * OZ_BN,
+                          bar_bfull + 8 * s);
+              bpar[s] = (int)ph;
+              if (++s == OZ_BSTAGES) {
+                s = 0;
+                ph ^= 1u;
+              }
+            }
+            if (ok && q == 0) {
+              if (p + 1 < OZ_S)
+                ok = load_a(t, p + 1);
+              else if (t + (int)gridDim.x < ntiles)
+                ok = load_a(t + gridDim.x, 0);
+            }
+          }
+        }
+      }
+      if (!ok) {
+        // let every issued copy land before the CTA can exit
+        for (int a = 0; a < 2; ++a) {
+          if (apar[a] < 0) continue;
+          const uint64_t t0 = gtimer();
+          while (!mbar_try(bar_afull + 8 * a, (uint32_t)apar[a]) && gtimer() - t0 < GB_SPIN_LIMIT_NS) {
+          }
+        }
+        for (int q = 0; q < OZ_BSTAGES; ++q) {
+          if (bpar[q] < 0) continue;
+          const uint64_t t0 = gtimer();
+          while (!mbar_try(bar_bfull + 8 * q, (uint32_t)bpar[q]) && gtimer() - t0 < GB_SPIN_LIMIT_NS) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer: one TMEM accumulator per slice pair
+    if (lane == 0) {
+      int s = 0, ab = 0, acc = 0;
+      uint32_t ph = 0, abph = 0, tph = 0;
+      bool ok = true, issued = false;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        for (int p = 0; p < OZ_S && ok; ++p) {
+          if (!mbar_wait(bar_afull + 8 * ab, abph, P.status, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = sA + ab * OZ_ABUF;
+          for (int q = 0; q < OZ_S - p && ok; ++q) {
+            if (!mbar_wait(bar_tempty + 8 * acc, tph ^ 1u, P.status, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t dtm = tmem_base + (uint32_t)(acc * OZ_BN);
+            for (int kc = 0; kc < P.kchunks; ++kc) {
+              if (!mbar_wait(bar_bfull + 8 * s, ph, P.status, abort_flag)) {
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              const uint32_t b0 = sB + s * OZ_CHUNK;
+#pragma unroll
+              for (int kk = 0; kk < OZ_BK / 16; ++kk)
+                tc_mma(dtm, sw128_desc(a0 + kc * OZ_CHUNK + kk * 32), sw128_desc(b0 + kk * 32), P.idesc,
+                       (kc | kk) ? 1u : 0u);
+              issued = true;
+              tc_commit(bar_bempty + 8 * s);
+              if (++s == OZ_BSTAGES) {
+                s = 0;
+                ph ^= 1u;
+              }
+            }
+            if (!ok) break;
+            tc_commit(bar_tfull + 8 * acc);
+            if (++acc == OZ_NACC) {
+              acc = 0;
+              tph ^= 1u;
+            }
+          }
+          if (!ok) break;
+          tc_commit(bar_aempty + 8 * ab);
+          if (++ab == 2) {
+            ab = 0;
+            abph ^= 1u;
+          }
+        }
+      }
+      if (!ok && issued) {
+        // let the MMAs already issued finish before TMEM is freed
+        tc_commit(bar_drain);
+        const uint64_t t0 = gtimer();
+        while (!mbar_try(bar_drain, 0) && gtimer() - t0 < GB_SPIN_LIMIT_NS) {
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue: exact integer combination, then C -= I * 2^(e_i + f_j - 54)
+    const int quarter = warp & 3;          // TMEM lane quarter this warp may access
+    const int half = (warp - 2) >> 2;      // which 64 columns of the tile
+    const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+    int acc = 0;
+    uint32_t tph = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int tm = t % P.tiles_m, tn = t / P.tiles_m;
+      const int row = tm * OZ_BM + quarter * 32 + lane;
+      const bool rok = row < P.m;
+      const int col0 = tn * OZ_BN + half * 64;
+      double* crow = P.C + (int64_t)row * P.ldc + col0;
+      if (rok) {
+        // bring this thread's C segment into L2 while the products accumulate
+#pragma unroll
+        for (int c = 0; c < 64; c += 16)
+          if (col0 + c < P.n) asm volatile("prefetch.global.L2 [%0];" ::"l"(crow + c));
+      }
+      unsigned long long a[64];
+#pragma unroll
+      for (int j = 0; j < 64; ++j) a[j] = 0ull;
+      unsigned long long corr = 0ull;
+      for (int p = 0; p < OZ_S && ok; ++p) {
+        for (int q = 0; q < OZ_S - p; ++q) {
+          int okw = 1;
+          if (lane == 0) okw = mbar_wait(bar_tfull + 8 * acc, tph, P.status, abort_flag) ? 1 : 0;
+          okw = __shfl_sync(0xffffffffu, okw, 0);
+          if (!okw) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int tt = p + q;
+          const uint32_t taddr = tmem_base + lane_addr + (uint32_t)(acc * OZ_BN + half * 64);
+          uint32_t v[32];
+          TMEM_LD_X32(taddr, v);
+          tmem_wait_ld();
+          oz_acc_t(tt, a, v);
+          TMEM_LD_X32(taddr + 32, v);
+          tmem_wait_ld();
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(bar_tempty + 8 * acc);
+          oz_acc_t(tt, a + 32, v);
+          corr += oz_corr(tt);
+          if (++acc == OZ_NACC) {
+            acc = 0;
+            tph ^= 1u;
+          }
+        }
+      }
+      if (!ok) break;
+      if (rok) {
+        // the scale 2^(e_i + f_j - 54) goes into the exponent field by an
+        // integer add (the FP64 pipe does only the subtraction); results
+        // outside the normal range take ldexp
+        const int er = P.ea[row] - (OZ_F + 2 * OZ_BITS);
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+          if (col0 + j < P.n) {
+            const long long I = (long long)(a[j] - corr);
+            const int E = er + P.fb[col0 + j];
+            double d = __ll2double_rn(I);
+            const long long bits = __double_as_longlong(d);
+            const int ex = (int)((bits >> 52) & 0x7ff) + E;
+            if (I != 0) d = (ex >= 1 && ex <= 2046) ? __longlong_as_double(bits + ((long long)E << 52)) : ldexp(d, E);
+            crow[j] -= d;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(OZ_TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------ host side
+static size_t al1k(size_t b) { return (b + 1023) / 1024 * 1024; }
+
+size_t ozaki_ws_bytes(int m, int n, int k) {
+  const size_t kpad = (size_t)cdiv(k > 0 ? k : 1, OZ_BK) * OZ_BK;
+  return al1k((size_t)OZ_S * m * kpad * 2) + al1k((size_t)OZ_S * n * kpad * 2) + al1k((size_t)m * 4) +
+         al1k((size_t)n * 4);
+}
+
+struct OzLayout {
+  __nv_bfloat16 *As, *Bs;
+  int *ea, *fb;
+  int kpad;
+};
+
+static OzLayout oz_layout(void* ws, int m, int n, int k) {
+  OzLayout L;
+  L.kpad = (int)cdiv(k, OZ_BK) * OZ_BK;
+  char* p = (char*)ws;
+  L.As = (__nv_bfloat16*)p;
+  p += al1k((size_t)OZ_S * m * L.kpad * 2);
+  L.Bs = (__nv_bfloat16*)p;
+  p += al1k((size_t)OZ_S * n * L.kpad * 2);
+  L.ea = (int*)p;
+  p += al1k((size_t)m * 4);
+  L.fb = (int*)p;
+  return L;
+}
+
+cudaError_t ozaki_split(const double* A, int64_t lda, const double* B, int64_t ldb, int m, int n, int k, void* ws,
+                        int* status, cudaStream_t st) {
+  if (m <= 0 || n <= 0 || k <= 0) return cudaSuccess;
+  if (k > OZ_KMAX || ws == nullptr) return cudaErrorInvalidValue;
+  const OzLayout L = oz_layout(ws, m, n, k);
+  oz_split_rows_kernel<<<(unsigned)cdiv(m, 8), 256, 0, st>>>(A, lda, m, k, L.kpad, L.As, L.ea, status);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  oz_split_cols_kernel<<<(unsigned)cdiv(n, 32), 256, 0, st>>>(B, ldb, k, n, L.kpad, L.Bs, L.fb, status);
+  return cudaGetLastError();
+}
+
+typedef CUresult (*PFN_encodeTiled_oz)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                       const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                       CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                       CUtensorMapFloatOOBfill);
+
+static PFN_encodeTiled_oz oz_encode() {
+  static PFN_encodeTiled_oz fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_encodeTiled_oz)p;
+  });
+  return fn;
+}
+
+static bool oz_map(CUtensorMap* map, const void* ptr, int64_t rows, int kpad) {
+  PFN_encodeTiled_oz enc = oz_encode();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+  cuuint32_t box[2] = {(cuuint32_t)OZ_BK, (cuuint32_t)OZ_BM};
+  cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t ozaki_gemm(double* C, int64_t ldc, const void* ws, int m, int n, int k, int col0, int ncols, int* status,
+                       const DevInfo& dev, cudaStream_t st, int max_ctas) {
+  if (m <= 0 || ncols <= 0 || k <= 0) return cudaSuccess;
+  if (k > OZ_KMAX || col0 < 0 || col0 + ncols > n || ws == nullptr) return cudaErrorInvalidValue;
+  const OzLayout L = oz_layout(const_cast<void*>(ws), m, n, k);
+  CUtensorMap ma, mb;
+  if (!oz_map(&ma, L.As, (int64_t)OZ_S * m, L.kpad) || !oz_map(&mb, L.Bs, (int64_t)OZ_S * n, L.kpad))
+    return cudaErrorInvalidValue;
+  cudaError_t e = allow_max_smem((const void*)oz_gemm_kernel);
+  if (e != cudaSuccess) return e;
+  OzParams P;
+  P.C = C;
+  P.ldc = ldc;
+  P.m = m;
+  P.n = ncols;
+  P.a_rows = m;
+  P.b_rows = n;
+  P.b_col0 = col0;
+  P.kchunks = L.kpad / OZ_BK;
+  P.tiles_m = (int)cdiv(m, OZ_BM);
+  P.tiles_n = (int)cdiv(ncols, OZ_BN);
+  P.ea = L.ea;
+  P.fb = L.fb + col0;
+  P.idesc = tc_idesc_mn(1u, OZ_BM, OZ_BN);
+  P.status = status;
+  const int ntiles = P.tiles_m * P.tiles_n;
+  int grid = ntiles < dev.sm_count ? ntiles : dev.sm_count;
+  if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
+  oz_gemm_kernel<<<grid, OZ_THREADS, OZ_SMEM, st>>>(ma, mb, P);
+  return cudaGetLastError();
+}
+
+}  // namespace gb

@@ -15,6 +15,12 @@ struct DevInfo {
   int max_smem_optin;
 };
 
+// Raise a kernel's dynamic shared-memory limit to the device maximum, once per
+// kernel and device (thread-safe).  Launches then never depend on a per-call
+// attribute value, which concurrent host threads launching the same kernel
+// with different sizes would race on.
+cudaError_t allow_max_smem(const void* func);
+
 // ---------------------------------------------------------------- panel.cu
 // Scratch of the cooperative panel kernel (global memory, owned by the caller).
 struct PanelScratch {
@@ -27,12 +33,14 @@ struct PanelScratch {
   int gmax;        // capacity in CTAs
   int ibmax;
   int wmax;
+  int gtarget = 0; // preferred CTA count (0: the default for the element size)
 };
 size_t panel_scratch_bytes(int gmax, int ibmax, int wmax, int tsize);
 void panel_scratch_carve(PanelScratch* s, void* base, int gmax, int ibmax, int wmax, int tsize);
 
-// CTAs that launch_panel uses for an m x w panel of element size tsize.
-int panel_grid_size(int m, int w, int tsize, const DevInfo& dev, int gmax);
+// CTAs that launch_panel uses for an m x w panel of element size tsize
+// (gtarget > 0 replaces the default target count).
+int panel_grid_size(int m, int w, int tsize, const DevInfo& dev, int gmax, int gtarget = 0);
 
 // Factor the m x w panel whose (0,0) element is W(k,k) (row stride ldw) with
 // partial pivoting.  Writes ipiv[k..k+w) (1-based, absolute), lowers *info to
@@ -58,7 +66,15 @@ cudaError_t launch_to_working(const double* A, int64_t lda, T* W, int64_t ldw, i
 template <typename T>
 cudaError_t launch_from_working(const T* W, int64_t ldw, double* LU, int64_t ldlu, int n, cudaStream_t st);
 
-cudaError_t launch_iota(int* v, int n, cudaStream_t st);
+cudaError_t launch_iota(int* v, int n, cudaStream_t st, int base = 0);
+
+// ---------------------------------------------------------------- nopiv.cu
+// The no-pivot variant's block operations: LU of the w x w diagonal block at D
+// (one CTA), and X (m x w) <- X U^-1 with U the upper w x w block at U.
+template <typename T>
+cudaError_t launch_diag_lu(T* D, int64_t ld, int w, int kabs, int* info, cudaStream_t st);
+template <typename T>
+cudaError_t launch_trsm_right_upper(const T* U, T* X, int64_t ld, int m, int w, cudaStream_t st);
 
 // ---------------------------------------------------------------- gemm_simt.cu
 // C (m x n) -= A (m x k) * B (k x n), all row-major in T, CUDA-core FMA.
@@ -79,6 +95,19 @@ size_t tc_gemm_plan_bytes();
 // max_ctas > 0 caps the persistent grid (to leave SMs to a concurrent kernel).
 cudaError_t tc_gemm_run(int kind, float* C, int64_t ldc, const void* Aop, const void* Bop, int m, int n, int kpad,
                         int* status, const DevInfo& dev, cudaStream_t st, int max_ctas = 0);
+
+// ---------------------------------------------------------------- gemm_ozaki.cu
+// FP64 C -= A B with the products on BF16 tensor cores by error-free splitting
+// (Ozaki scheme, 8 slices of 7 bits, exact integer combination).  k <= 256.
+// ozaki_split cuts A (m x k) and B (k x n), both row-major FP64, into the
+// workspace (ozaki_ws_bytes(m, n, k) bytes); ozaki_gemm then updates columns
+// [col0, col0 + ncols) of the m x n product into C (row-major FP64, column 0
+// of C is column col0 of the product).  Non-finite operands set ST_RANGE.
+size_t ozaki_ws_bytes(int m, int n, int k);
+cudaError_t ozaki_split(const double* A, int64_t lda, const double* B, int64_t ldb, int m, int n, int k, void* ws,
+                        int* status, cudaStream_t st);
+cudaError_t ozaki_gemm(double* C, int64_t ldc, const void* ws, int m, int n, int k, int col0, int ncols, int* status,
+                       const DevInfo& dev, cudaStream_t st, int max_ctas = 0);
 
 // ---------------------------------------------------------------- solve.cu
 struct SolveScratch {

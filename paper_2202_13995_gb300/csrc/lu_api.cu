@@ -102,6 +102,8 @@ struct lu_fact_s {
   void* aop = nullptr;  // tensor-core operands (K-major, 16-bit)
   void* bop = nullptr;
   int kpad = 0;
+  bool ozaki = false;   // FP64 trailing update by error-free splitting
+  void* oz_ws = nullptr;
   void* solve_mem = nullptr;
   SolveScratch ss{};
   double* vec_ws = nullptr;  // refinement: R, D, partial sums
@@ -277,7 +279,7 @@ static int factor_loop(lu_fact f) {
   // with the update phase): the next panel's columns are updated first, then
   // that panel is factored on the side stream while the rest of the trailing
   // matrix is updated on the remaining SMs.
-  const bool lookahead = tc && c->lookahead && c->side != nullptr;
+  const bool lookahead = (tc || f->ozaki) && c->lookahead && c->side != nullptr;
   bool panel_ready = false;
   for (int k = 0; k < n; k += nb) {
     const int w = (n - k) < nb ? (n - k) : nb;
@@ -296,13 +298,34 @@ static int factor_loop(lu_fact f) {
     T* L21 = Wkk + (int64_t)w * ld;
     T* A22 = L21 + w;
     CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12, ld, w, rest, st)));
+    const int w2 = rest < nb ? rest : nb;
+    if (f->ozaki) {
+      double* C = (double*)A22;
+      CU_TRY(PHASE(c, PH_CAST, 2, ozaki_split((const double*)L21, ld, (const double*)U12, ld, rest, rest, w,
+                                               f->oz_ws, c->d_status, st)));
+      if (!lookahead || rest <= w2) {
+        CU_TRY(PHASE(c, PH_GEMM, 1, ozaki_gemm(C, ld, f->oz_ws, rest, rest, w, 0, rest, c->d_status, c->dev, st)));
+        continue;
+      }
+      CU_TRY(PHASE(c, PH_GEMM, 1, ozaki_gemm(C, ld, f->oz_ws, rest, rest, w, 0, w2, c->d_status, c->dev, st)));
+      CU_TRY(cudaEventRecord(c->ev_next, st));
+      CU_TRY(cudaStreamWaitEvent(c->side, c->ev_next, 0));
+      CU_TRY(PHASE_ON(c, c->side, PH_PANEL, 1, launch_panel<T>(A22, ld, rest, w2, k + w, f->ipiv, f->info_d,
+                                                               c->d_status, f->ps, c->dev, c->side)));
+      CU_TRY(cudaEventRecord(c->ev_panel, c->side));
+      panel_ready = true;
+      const int gp = panel_grid_size(rest, w2, sizeof(T), c->dev, f->ps.gmax, f->ps.gtarget);
+      const int cap = c->dev.sm_count - (gp > 0 ? gp : 0);
+      CU_TRY(PHASE(c, PH_GEMM, 1, ozaki_gemm(C + w2, ld, f->oz_ws, rest, rest, w, w2, rest - w2, c->d_status, c->dev,
+                                              st, cap > 8 ? cap : 8)));
+      continue;
+    }
     if (!tc) {
       CU_TRY(PHASE(c, PH_GEMM, 1, launch_gemm_simt<T>(A22, ld, L21, ld, U12, ld, rest, rest, w, st)));
       continue;
     }
     CU_TRY(PHASE(c, PH_CAST, 2, launch_cast_operands(kind, (const float*)L21, (const float*)U12, ld, rest, rest, w,
                                                       f->aop, f->bop, f->kpad, c->d_status, st)));
-    const int w2 = rest < nb ? rest : nb;
     if (!lookahead || rest <= w2) {
       CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)A22, ld, f->aop, f->bop, rest, rest, f->kpad,
                                                c->d_status, c->dev, st)));
@@ -318,7 +341,8 @@ static int factor_loop(lu_fact f) {
                                                              c->d_status, f->ps, c->dev, c->side)));
     CU_TRY(cudaEventRecord(c->ev_panel, c->side));
     panel_ready = true;
-    // the rest of the trailing matrix on the SMs the panel leaves free
+    // the rest of the trailing matrix on the SMs the panel leaves free (the
+    // latency-bound panel runs slower on SMs it shares with the update)
     const int gp = panel_grid_size(rest, w2, sizeof(T), c->dev, f->ps.gmax);
     const int cap = c->dev.sm_count - (gp > 0 ? gp : 0);
     const void* bop2 = (const char*)f->bop + (size_t)w2 * f->kpad * 2;
@@ -329,6 +353,45 @@ static int factor_loop(lu_fact f) {
   return LU_OK;
 }
 
+// The paper's no-pivot iteration: LU of the diagonal block, left and top
+// block solves, inner update.
+template <typename T>
+static int factor_loop_nopiv(lu_fact f) {
+  lu_ctx c = f->ctx;
+  cudaStream_t st = c->stream;
+  T* W = (T*)f->W;
+  const int n = f->n, nb = f->nb;
+  const int64_t ld = f->ldw;
+  const bool tc = f->prec == LU_BF16 || f->prec == LU_FP16;
+  const int kind = f->prec == LU_BF16 ? 1 : 2;
+  for (int k = 0; k < n; k += nb) {
+    const int w = (n - k) < nb ? (n - k) : nb;
+    T* Wkk = W + (int64_t)k * ld + k;
+    CU_TRY(PHASE(c, PH_PANEL, 1, launch_diag_lu<T>(Wkk, ld, w, k, f->info_d, st)));
+    const int rest = n - k - w;
+    if (rest <= 0) continue;
+    T* U12 = Wkk + w;
+    T* L21 = Wkk + (int64_t)w * ld;
+    T* A22 = L21 + w;
+    CU_TRY(PHASE(c, PH_PANEL, 1, launch_trsm_right_upper<T>(Wkk, L21, ld, rest, w, st)));
+    CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12, ld, w, rest, st)));
+    if (f->ozaki) {
+      CU_TRY(PHASE(c, PH_CAST, 2, ozaki_split((const double*)L21, ld, (const double*)U12, ld, rest, rest, w,
+                                               f->oz_ws, c->d_status, st)));
+      CU_TRY(PHASE(c, PH_GEMM, 1, ozaki_gemm((double*)A22, ld, f->oz_ws, rest, rest, w, 0, rest, c->d_status, c->dev,
+                                              st)));
+    } else if (tc) {
+      CU_TRY(PHASE(c, PH_CAST, 2, launch_cast_operands(kind, (const float*)L21, (const float*)U12, ld, rest, rest,
+                                                        w, f->aop, f->bop, f->kpad, c->d_status, st)));
+      CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)A22, ld, f->aop, f->bop, rest, rest, f->kpad,
+                                               c->d_status, c->dev, st)));
+    } else {
+      CU_TRY(PHASE(c, PH_GEMM, 1, launch_gemm_simt<T>(A22, ld, L21, ld, U12, ld, rest, rest, w, st)));
+    }
+  }
+  return LU_OK;
+}
+
 extern "C" void lu_fact_free(lu_fact f) {
   if (!f) return;
   lu_ctx c = f->ctx;
@@ -336,6 +399,7 @@ extern "C" void lu_fact_free(lu_fact f) {
   dfree(c, f->ipiv);
   dfree(c, f->panel_mem);
   dfree(c, f->aop);
+  dfree(c, f->oz_ws);
   dfree(c, f->solve_mem);
   dfree(c, f->ss.dinv);
   dfree(c, f->vec_ws);
@@ -344,15 +408,24 @@ extern "C" void lu_fact_free(lu_fact f) {
 
 extern "C" int lu_factor(lu_ctx c, int n, const double* dA, int lda, lu_prec prec, int nb, lu_fact* out,
                          int* info) {
+  return lu_factor_ex(c, n, dA, lda, prec, nb, 0, out, info);
+}
+
+extern "C" int lu_factor_ex(lu_ctx c, int n, const double* dA, int lda, lu_prec prec, int nb, int flags,
+                            lu_fact* out, int* info) {
   if (!c) return -1;
+  if (flags & ~(LU_FACTOR_NOPIV | LU_FACTOR_OZAKI)) return -7;
+  if ((flags & LU_FACTOR_OZAKI) && prec != LU_F64) return -7;
+  const bool nopiv = (flags & LU_FACTOR_NOPIV) != 0;
   if (n < 0) return -2;
   if (!dA && n > 0) return -3;
   if (lda < (n > 1 ? n : 1)) return -4;
   if (prec < LU_F64 || prec > LU_F32) return -5;
   if (nb < 0 || nb > 512) return -6;
-  if (!out) return -7;
+  if (!out) return -8;
   *out = nullptr;
   if (nb == 0) nb = default_nb(n, prec);
+  if ((flags & LU_FACTOR_OZAKI) && nb > 256) return -6;
   lu_fact f = new (std::nothrow) lu_fact_s();
   if (!f) return LU_ENOMEM;
   f->ctx = c;
@@ -383,6 +456,15 @@ extern "C" int lu_factor(lu_ctx c, int n, const double* dA, int lda, lu_prec pre
       return rc;
     }
   }
+  if (flags & LU_FACTOR_OZAKI) {
+    f->ozaki = true;
+    // a panel beside the concurrent update (lookahead) on fewer CTAs
+    f->ps.gtarget = 64;
+    if ((rc = dalloc(c, &f->oz_ws, ozaki_ws_bytes(nn, nn, f->nb)))) {
+      lu_fact_free(f);
+      return rc;
+    }
+  }
   if (prec == LU_BF16 || prec == LU_FP16) {
     f->kpad = round_up(f->nb, 64);
     if ((rc = dalloc(c, &f->aop, (size_t)2 * nn * f->kpad * 2 + 1024))) {
@@ -399,14 +481,15 @@ extern "C" int lu_factor(lu_ctx c, int n, const double* dA, int lda, lu_prec pre
   if (cudaMemsetAsync(f->info_d, 0x7f, sizeof(int), st) != cudaSuccess) return fail(LU_ECUDA);
   if (n > 0) {
     if (PHASE(c, PH_OTHER, 1, launch_iota(f->rowid, n, st)) != cudaSuccess) return fail(LU_ECUDA);
+    if (nopiv && PHASE(c, PH_OTHER, 1, launch_iota(f->ipiv, n, st, 1)) != cudaSuccess) return fail(LU_ECUDA);
     if (prec == LU_F64) {
       if (PHASE(c, PH_OTHER, 1, launch_to_working<double>(dA, lda, (double*)f->W, f->ldw, n, st)) != cudaSuccess)
         return fail(LU_ECUDA);
-      rc = factor_loop<double>(f);
+      rc = nopiv ? factor_loop_nopiv<double>(f) : factor_loop<double>(f);
     } else {
       if (PHASE(c, PH_OTHER, 1, launch_to_working<float>(dA, lda, (float*)f->W, f->ldw, n, st)) != cudaSuccess)
         return fail(LU_ECUDA);
-      rc = factor_loop<float>(f);
+      rc = nopiv ? factor_loop_nopiv<float>(f) : factor_loop<float>(f);
       if (!rc && f->ss.dinv) {
         if (PHASE(c, PH_OTHER, 1, launch_trinv<float>((const float*)f->W, f->ldw, n, (float*)f->ss.dinv, st)) !=
             cudaSuccess)
@@ -720,6 +803,27 @@ extern "C" int lu_step_gemm(lu_ctx c, lu_prec prec, int m, int n, int k, void* d
   CU_TRY(launch_cast_operands(kind, (const float*)dA, (const float*)dB, lda, m, n, k, aop, bop, kpad, c->d_status,
                               c->stream));
   CU_TRY(tc_gemm_run(kind, (float*)dC, ldc, aop, bop, m, n, kpad, c->d_status, c->dev, c->stream));
+  return LU_OK;
+}
+
+extern "C" int lu_step_gemm_ozaki(lu_ctx c, int m, int n, int k, double* dC, int ldc, const double* dA, int lda,
+                                  const double* dB, int ldb) {
+  if (!c) return -1;
+  if (m < 0) return -2;
+  if (n < 0) return -3;
+  if (k < 1 || k > 256) return -4;
+  if (m == 0 || n == 0) return LU_OK;
+  if (!dC) return -5;
+  if (ldc < n) return -6;
+  if (!dA) return -7;
+  if (lda < k) return -8;
+  if (!dB) return -9;
+  if (ldb < n) return -10;
+  int rc = ensure_step_ws(c, ozaki_ws_bytes(m, n, k));
+  if (rc) return rc;
+  CU_TRY(ozaki_split(dA, lda, dB, ldb, m, n, k, c->step_ws, c->d_status, c->stream));
+  CU_TRY(ozaki_gemm(dC, ldc, c->step_ws, m, n, k, 0, n, c->d_status, c->dev, c->stream));
+  c->launches += 3;
   return LU_OK;
 }
 

@@ -11,7 +11,10 @@
 // The working matrix W is row-major (see kernels.h).
 #include <chrono>
 #include <climits>
+#include <mutex>
+#include <set>
 #include <thread>
+#include <utility>
 #include <cstdio>
 #include <cstdlib>
 
@@ -19,6 +22,25 @@
 #include "kernels.h"
 
 namespace gb {
+
+cudaError_t allow_max_smem(const void* func) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({func, dev})) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, func);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) done.insert({func, dev});
+  return e;
+}
 
 template <typename T>
 __device__ __forceinline__ T tabs(T v) {
@@ -396,9 +418,10 @@ void panel_scratch_carve(PanelScratch* s, void* base, int gmax, int ibmax, int w
 // exchange, which is cheaper with fewer CTAs (one L2 round trip per column),
 // and leave the other SMs to the concurrent trailing update.  Each CTA's
 // sub-panel tile must fit in shared memory.
-int panel_grid_size(int m, int w, int tsize, const DevInfo& dev, int gmax) {
+int panel_grid_size(int m, int w, int tsize, const DevInfo& dev, int gmax, int gtarget) {
   const int cap = dev.sm_count < gmax ? dev.sm_count : gmax;
   int target = tsize == 8 ? cap : (64 < cap ? 64 : cap);
+  if (gtarget > 0) target = gtarget < cap ? gtarget : cap;
   static const int forced = getenv("GB300LU_PANEL_G") ? atoi(getenv("GB300LU_PANEL_G")) : 0;
   if (forced > 0) target = forced < cap ? forced : cap;
   const size_t budget = (size_t)dev.max_smem_optin - 48 * 1024;
@@ -419,13 +442,13 @@ cudaError_t launch_panel(T* Wkk, int64_t ldw, int m, int w, int kabs, int* ipiv,
   if (w <= 0 || m < w || w > s.wmax) return cudaErrorInvalidValue;
   if (s.gmax > PNL_XG) return cudaErrorInvalidValue;  // every candidate row fits the exchange buffer
   const int ib = PNL_IB < s.ibmax ? PNL_IB : s.ibmax;
-  const int G0 = panel_grid_size(m, w, sizeof(T), dev, s.gmax);
+  const int G0 = panel_grid_size(m, w, sizeof(T), dev, s.gmax, s.gtarget);
   if (G0 <= 0) return cudaErrorInvalidConfiguration;
   const int R = (int)cdiv(m, G0);
   const int G = (int)cdiv(m, R);  // <= G0; every CTA owns at least one row
   const size_t smem = panel_smem_bytes(R, ib, w, sizeof(T));
   auto kern = panel_getrf_kernel<T>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem((const void*)kern);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PNL_THREADS, smem);
@@ -454,13 +477,14 @@ cudaError_t launch_panel(T* Wkk, int64_t ldw, int m, int w, int kabs, int* ipiv,
   void* args[] = {&P};
   // A cooperative launch is refused (without side effects) while other
   // in-flight cooperative grids -- other streams' panels -- hold the resources
-  // it needs; those grids always finish, so retry with a short back-off.
+  // it needs; those grids always finish, so retry with a short back-off
+  // (bounded: 20 s).
   const auto t0 = std::chrono::steady_clock::now();
   while (true) {
     e = cudaLaunchCooperativeKernel((const void*)kern, dim3(G), dim3(PNL_THREADS), args, smem, st);
     if (e != cudaErrorCooperativeLaunchTooLarge && e != cudaErrorLaunchOutOfResources) return e;
     cudaGetLastError();
-    if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(2)) return e;
+    if (std::chrono::steady_clock::now() - t0 > std::chrono::seconds(20)) return e;
     std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
 }
@@ -506,7 +530,7 @@ cudaError_t launch_laswp(T* W, int64_t ldw, int n, int k, int w, const int* perm
   const int blocks = nout > 0 ? (int)cdiv(nout, CW) : 1;
   const size_t smem = (size_t)2 * w * CW * sizeof(T) + 2 * (size_t)w * sizeof(int) + 16;
   auto kern = laswp_kernel<T>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem((const void*)kern);
   if (e != cudaSuccess) return e;
   laswp_kernel<T><<<blocks, 256, smem, st>>>(W, ldw, n, k, w, perm, rowid);
   return cudaGetLastError();
@@ -568,7 +592,7 @@ cudaError_t launch_trsm_lower(const T* L11, T* A12, int64_t ldw, int w, int N, c
   if (N <= 0) return cudaSuccess;
   const size_t smem = ((size_t)w * 32 + 32 * 33) * sizeof(T);
   auto kern = trsm_lower_kernel<T>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem((const void*)kern);
   if (e != cudaSuccess) return e;
   trsm_lower_kernel<T><<<(int)cdiv(N, 32), 256, smem, st>>>(L11, A12, ldw, w, N);
   return cudaGetLastError();
@@ -622,13 +646,13 @@ cudaError_t launch_from_working(const T* W, int64_t ldw, double* LU, int64_t ldl
   return cudaGetLastError();
 }
 
-__global__ void iota_kernel(int* v, int n) {
+__global__ void iota_kernel(int* v, int n, int base) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) v[i] = i;
+  if (i < n) v[i] = i + base;
 }
 
-cudaError_t launch_iota(int* v, int n, cudaStream_t st) {
-  iota_kernel<<<(int)cdiv(n, 256), 256, 0, st>>>(v, n);
+cudaError_t launch_iota(int* v, int n, cudaStream_t st, int base) {
+  iota_kernel<<<(int)cdiv(n, 256), 256, 0, st>>>(v, n, base);
   return cudaGetLastError();
 }
 

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <atomic>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <list>
@@ -67,6 +68,12 @@ struct lu_server_s {
   std::vector<std::thread> slots;
   std::vector<lu_ctx> ctxs;            // per slot; destroyed after the resident factors
   std::vector<cudaStream_t> streams;
+  // Optionally one factorization at a time (GB300LU_SERVER_SERIAL_FACTOR):
+  // the partial-pivot panels are cooperative grids; the trailing-update CTAs
+  // leave room for a panel CTA on every SM, so by default factorizations
+  // overlap too, and a panel launch that finds no room retries.
+  std::mutex factor_mu;
+  bool serialize_factor = false;
 };
 
 static size_t request_bytes(lu_server s, const lu_request& r) {
@@ -109,15 +116,18 @@ static void slot_main(lu_server s, int slot) {
     // the oldest request whose memory fits (resident hits need the refinement part only)
     std::vector<lu_fact> freed;
     auto pick = s->queue.end();
+    // Oldest first.  A request whose resident factor is busy (one request at
+    // a time per factor) is passed over; the oldest other request is then
+    // the only candidate, so no request overtakes an older one for memory.
     for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
       size_t need = it->bytes;
       auto r = it->req.use_resident ? s->resident.find(it->req.factor_key) : s->resident.end();
       if (r != s->resident.end()) {
-        if (r->second.in_use > 0) break;  // one request at a time per factor: wait for it
+        if (r->second.in_use > 0) continue;
         need = 0;  // the resident factor covers it (refinement vectors live in it)
       }
       if (make_room(s, need, freed)) pick = it;
-      break;  // FIFO: do not overtake the oldest request
+      break;
     }
     if (!freed.empty()) {
       lk.unlock();
@@ -161,7 +171,13 @@ static void slot_main(lu_server s, int slot) {
     res.t_start_ns = now_ns();
     int rc = LU_OK;
     if (reused) gb_fact_rebind(f, ctx);  // its last user finished; it now runs on this slot's stream
-    if (!reused) rc = lu_factor(ctx, job.req.n, job.req.dA, job.req.lda, s->prec, 0, &f, nullptr);
+    if (!reused) {
+      std::unique_lock<std::mutex> flk(s->factor_mu, std::defer_lock);
+      if (s->serialize_factor) flk.lock();
+      int info = 0;
+      rc = lu_factor(ctx, job.req.n, job.req.dA, job.req.lda, s->prec, 0, &f, &info);  // synchronizes
+      if (rc == LU_OK && info > 0) rc = LU_ESINGULAR;
+    }
     int iters = 0;
     double sr = 0.0;
     if (rc == LU_OK)
@@ -216,6 +232,7 @@ extern "C" int lu_server_create(lu_server* out, size_t hbm_budget_bytes, lu_prec
   }
   s->prec = prec;
   s->budget = hbm_budget_bytes;
+  s->serialize_factor = getenv("GB300LU_SERVER_SERIAL_FACTOR") != nullptr;
   s->ctxs.assign(max_slots, nullptr);
   s->streams.assign(max_slots, nullptr);
   for (int i = 0; i < max_slots; ++i) s->slots.emplace_back(slot_main, s, i);

@@ -315,9 +315,9 @@ static cudaError_t run_solve(const T* W, int64_t ldw, const int* rowid, int n, i
   auto kl = trsv_kernel<T, NR, STAGES, true, DINV>;
   auto ku = trsv_kernel<T, NR, STAGES, false, DINV>;
   const T* Dinv = (const T*)s.dinv;
-  cudaError_t e = cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem((const void*)kl);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(ku, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = allow_max_smem((const void*)ku);
   if (e != cudaSuccess) return e;
   int* flags = s.sync;
   int* ticket = s.sync + nblk;

@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libgb300lu.so")
 LU_F64, LU_BF16, LU_FP16, LU_F32 = 0, 1, 2, 3
 PRECS = {"f64": LU_F64, "bf16": LU_BF16, "fp16": LU_FP16, "f32": LU_F32}
 LU_OK, LU_ESINGULAR, LU_ENOMEM, LU_ENOTCONV, LU_ERANGE, LU_ETIMEOUT, LU_EAGAIN, LU_ECUDA, LU_EINTERNAL = range(9)
+LU_FACTOR_NOPIV, LU_FACTOR_OZAKI = 1, 2
 
 EXPORTED = [
     "lu_create", "lu_destroy", "lu_strerror", "lu_factor", "lu_fact_info", "lu_fact_ipiv", "lu_fact_lu",
@@ -31,7 +32,7 @@ EXPORTED = [
     "lu_profile_enable", "lu_profile_read", "lu_launch_count", "lu_step_panel_static",
     "lu_batch_create", "lu_batch_run", "lu_batch_shape", "lu_batch_free", "lu_solve_batched",
     "lu_server_create", "lu_server_submit", "lu_server_poll", "lu_server_wait", "lu_server_stats",
-    "lu_server_destroy", "lu_fact_bytes",
+    "lu_server_destroy", "lu_fact_bytes", "lu_factor_ex", "lu_step_gemm_ozaki",
 ]
 PHASES = ["panel", "laswp", "trsm", "cast", "gemm", "solve", "residual", "other"]
 
@@ -87,6 +88,7 @@ def load():
             "lu_step_panel": (I, [P, I, I, I, P, I, P, P]),
             "lu_step_trsm": (I, [P, I, I, I, P, I, P, I]),
             "lu_step_gemm": (I, [P, I, I, I, I, P, I, P, I, P, I]),
+            "lu_step_gemm_ozaki": (I, [P, I, I, I, P, I, P, I, P, I]),
             "lu_ctx_status": (I, [P]),
             "lu_device_sm_count": (I, [P]),
             "lu_build_tag": (C.c_char_p, []),
@@ -106,6 +108,7 @@ def load():
             "lu_server_stats": (I, [P, C.POINTER(C.c_uint64), IP, C.POINTER(C.c_size_t), C.POINTER(C.c_uint64)]),
             "lu_server_destroy": (I, [P]),
             "lu_fact_bytes": (C.c_size_t, [I, I, I, I]),
+            "lu_factor_ex": (I, [P, I, P, I, I, I, I, PP, IP]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -217,16 +220,20 @@ class Context:
         _check(load().lu_profile_read(self._h, ms, nl), "lu_profile_read")
         return {p: (ms[i], int(nl[i])) for i, p in enumerate(PHASES)}
 
-    def factor(self, A, prec="f64", nb: int = 0, sync: bool = True) -> "Factor":
-        """Factor P A = L U of the column-major FP64 (n, n) tensor A."""
+    def factor(self, A, prec="f64", nb: int = 0, sync: bool = True, nopiv: bool = False,
+               ozaki: bool = False) -> "Factor":
+        """Factor P A = L U of the column-major FP64 (n, n) tensor A (nopiv: the
+        paper's no-pivot variant for diagonally dominant A; ozaki: FP64 trailing
+        update on the BF16 tensor cores by error-free splitting, prec f64)."""
         ptr, lda, ncol = _colmajor(A, "A")
         n = A.shape[0]
         if ncol != n:
             raise ValueError("A must be square")
         f = C.c_void_p()
         info = C.c_int(-1)
-        rc = load().lu_factor(self._h, n, C.c_void_p(ptr), lda, _prec(prec), int(nb), C.byref(f),
-                              C.byref(info) if sync else None)
+        flags = (LU_FACTOR_NOPIV if nopiv else 0) | (LU_FACTOR_OZAKI if ozaki else 0)
+        rc = load().lu_factor_ex(self._h, n, C.c_void_p(ptr), lda, _prec(prec), int(nb), flags,
+                                 C.byref(f), C.byref(info) if sync else None)
         if f.value:
             fac = Factor(self, f, n, _prec(prec))
             self._factors.add(fac)
@@ -276,6 +283,16 @@ class Context:
         n = B.shape[1]
         _check(load().lu_step_gemm(self._h, _prec(prec), m, n, k, C.c_void_p(pc), ldc, C.c_void_p(pa), lda,
                                    C.c_void_p(pb), ldb), "lu_step_gemm")
+
+    def step_gemm_ozaki(self, Cm, A, B):
+        """C -= A B in FP64 with the products on the BF16 tensor cores (row-major FP64, k <= 256)."""
+        pc, ldc = _rowmajor(Cm, "C")
+        pa, lda = _rowmajor(A, "A")
+        pb, ldb = _rowmajor(B, "B")
+        m, k = A.shape
+        n = B.shape[1]
+        _check(load().lu_step_gemm_ozaki(self._h, m, n, k, C.c_void_p(pc), ldc, C.c_void_p(pa), lda,
+                                         C.c_void_p(pb), ldb), "lu_step_gemm_ozaki")
 
 
 class Factor:

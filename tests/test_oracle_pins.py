@@ -329,3 +329,44 @@ def test_trsm_right_upper_library_pin():
     U = np.triu(rng.uniform(-1, 1, (20, 20))) + 4 * np.eye(20)
     B = rng.uniform(-1, 1, (13, 20))
     assert np.allclose(O.trsm_right_upper(B, U), B @ np.linalg.inv(U), rtol=0, atol=1e-12)
+
+
+# ----------------------------------------------------------------- compensated update (Dot2)
+
+def _exact_update(Cm, Am, Bm):
+    m, k = Am.shape
+    n = Bm.shape[1]
+    out = [[Fraction(Cm[i, j]) for j in range(n)] for i in range(m)]
+    for i in range(m):
+        for j in range(n):
+            acc = out[i][j]
+            for t in range(k):
+                acc -= Fraction(Am[i, t]) * Fraction(Bm[t, j])
+            out[i][j] = acc
+    return out
+
+
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (3, 4, 7), (9, 5, 33)])
+def test_dot2_update_is_correctly_rounded_up_to_gamma_squared(m, n, k):
+    """Against exact rational arithmetic: |dot2 - exact| <= u |exact| + 4 gamma^2 (|C| + |A||B|)."""
+    rng = np.random.default_rng(100 + k)
+    Cm = rng.standard_normal((m, n)) * 2.0 ** rng.integers(-20, 20, (m, n))
+    Am = rng.standard_normal((m, k)) * 2.0 ** rng.integers(-20, 20, (m, k))
+    Bm = rng.standard_normal((k, n)) * 2.0 ** rng.integers(-20, 20, (k, n))
+    got = O.gemm_update_dot2(Cm, Am, Bm)
+    ex = _exact_update(Cm, Am, Bm)
+    g = (k + 1) * EPS / (1 - (k + 1) * EPS)
+    mag = np.abs(Cm) + np.abs(Am) @ np.abs(Bm)
+    for i in range(m):
+        for j in range(n):
+            err = abs(Fraction(got[i, j]) - ex[i][j])
+            assert err <= EPS * abs(ex[i][j]) + 4 * Fraction(g * g) * Fraction(mag[i, j])
+
+
+def test_dot2_recovers_what_plain_fp64_cancels():
+    """1e16 + 1 - 1e16: plain FP64 loses the 1, the compensated sum keeps it."""
+    Am = np.array([[1e16, 1.0, -1e16]])
+    Bm = np.ones((3, 1))
+    Cm = np.zeros((1, 1))
+    assert O.gemm_update(Cm, Am, Bm)[0, 0] != -1.0
+    assert O.gemm_update_dot2(Cm, Am, Bm)[0, 0] == -1.0
