@@ -45,8 +45,12 @@ WORKLOADS = {
     "hpl_nopiv_bf16_n32768": dict(n=32768, nb=0, prec="bf16", nrhs=1, seed=3, shift=0.25, nopiv=True),
     "hpl_nopiv_f32_n32768": dict(n=32768, nb=256, prec="f32", nrhs=1, seed=3, shift=0.25, nopiv=True,
                                  norefine=True),
+    # the FP64 configuration with the trailing update on the BF16 tensor cores by
+    # error-free splitting (FP64-accurate products, 8 slices of 7 bits)
+    "hpl_f64ozaki_n16384_nb256": dict(n=16384, nb=256, prec="f64", nrhs=1, seed=2, shift=0.0, ozaki=True),
     # smaller cases of the same shapes (profiling captures)
     "hpl_f64_n4096_nb256": dict(n=4096, nb=256, prec="f64", nrhs=1, seed=2, shift=0.0),
+    "hpl_f64ozaki_n4096_nb256": dict(n=4096, nb=256, prec="f64", nrhs=1, seed=2, shift=0.0, ozaki=True),
     "hpl_mixed_bf16_n8192": dict(n=8192, nb=0, prec="bf16", nrhs=1, seed=3, shift=0.25),
     "hpl_nopiv_bf16_n8192": dict(n=8192, nb=0, prec="bf16", nrhs=1, seed=3, shift=0.25, nopiv=True),
     # the batched configuration: 4096 systems, n ~ U{32..512}, 1-8 right-hand
@@ -172,7 +176,8 @@ def default_nb(n: int, prec: str) -> int:
     return 256 if n >= 2048 else 64
 
 
-def gemm_roofline(prof: dict, n: int, nb: int, prec: str, steps: int, peaks: dict, wname: str) -> dict:
+def gemm_roofline(prof: dict, n: int, nb: int, prec: str, steps: int, peaks: dict, wname: str,
+                  ozaki: bool = False) -> dict:
     """Roofline of the dominant kernel, the trailing update, from its summed
     CUDA-event launch durations in the timed region.
 
@@ -180,7 +185,9 @@ def gemm_roofline(prof: dict, n: int, nb: int, prec: str, steps: int, peaks: dic
     launch = 2 m'^2 nb.  BF16/FP16 (tcgen05): at nb = 256 the update's FP32
     C read-modify-write makes it HBM-bound (64 FLOP per byte, below the
     tensor ridge); algorithmic bytes per launch = 8 m' n' (C read + write)
-    + 2 (m' + n') kpad (the 16-bit operands)."""
+    + 2 (m' + n') kpad (the 16-bit operands).  FP64 by error-free splitting
+    (tcgen05, BF16 slices): bound by the tensor pipe; algorithmic FLOPs per
+    launch = 36 slice pairs x 2 m' n' kpad."""
     gemm_ms, gemm_n = prof["gemm"]
     nbx = nb or default_nb(n, prec)
     kpad = -(-nbx // 64) * 64
@@ -203,6 +210,13 @@ def gemm_roofline(prof: dict, n: int, nb: int, prec: str, steps: int, peaks: dic
             traffic = None
     base = {"launches": gemm_n, "kernel_ms_per_step": gemm_ms / steps, "traffic": traffic,
             "tflops": flops / sec / 1e12 if sec > 0 else None}
+    if ozaki:
+        tflops_bf16 = 36.0 * flops / nbx * kpad / sec / 1e12 if sec > 0 else None
+        peak = peaks.get("bf16_tflops_sustained", 1701.1)
+        return dict(base, bound="tensor", kernel="oz_gemm_kernel", achieved=tflops_bf16, peak=peak,
+                    unit="TFLOP/s", frac=(tflops_bf16 / peak) if tflops_bf16 else None,
+                    peak_source=f"bf16_tflops_sustained of {peaks['_source']}",
+                    fp64_equiv_tflops=base["tflops"])
     if prec == "f64":
         peak = peaks.get("bf16_tflops", 1876.8) * NOMINAL["f64"] / NOMINAL["bf16"]
         ach = flops / sec / 1e12 if sec > 0 else None
@@ -295,10 +309,11 @@ def timed_solves(ctx, stream, cfg: dict, nb, steps: int, warmup: int, rank: int,
     iters = []
 
     nopiv = bool(cfg.get("nopiv", False))
+    ozaki = bool(cfg.get("ozaki", False))
     refine = mixed and not cfg.get("norefine", False)
 
     def step():
-        f = ctx.factor(A, prec, nb, sync=False, nopiv=nopiv)
+        f = ctx.factor(A, prec, nb, sync=False, nopiv=nopiv, ozaki=ozaki)
         if refine:
             iters.append(f.refine(A, B, X, 16.0, 50)[0])
         else:
@@ -456,7 +471,8 @@ def run_ours(args, cfg, wname):
     A, B = r["A"], r["B"]
     ms, prof, launches = r["ms"], r["prof"], r["launches"]
     res, ck = r["res"], r["clocks"]
-    roofline = gemm_roofline(prof, n, nb, prec, args.steps, peaks, wname)
+    ozaki = bool(cfg.get("ozaki", False))
+    roofline = gemm_roofline(prof, n, nb, prec, args.steps, peaks, wname, ozaki)
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -473,8 +489,8 @@ def run_ours(args, cfg, wname):
         def e2e_step():
             Ad.copy_(Ah, non_blocking=True)
             Bd.copy_(Bh, non_blocking=True)
-            f = ctx.factor(Ad, prec, nb, sync=False)
-            if mixed:
+            f = ctx.factor(Ad, prec, nb, sync=False, nopiv=bool(cfg.get("nopiv", False)), ozaki=ozaki)
+            if mixed and not cfg.get("norefine", False):
                 f.refine(Ad, Bd, Xd, 16.0, 50)
             else:
                 Xd.copy_(Bd)
@@ -531,6 +547,22 @@ def run_ours(args, cfg, wname):
         del mr
         torch.cuda.empty_cache()
 
+    ozaki_line = None
+    if not mixed and not args.no_mixed and wname == DEFAULT:
+        # the same FP64 configuration with the update by error-free splitting
+        oname = "hpl_f64ozaki_n16384_nb256"
+        oc = WORKLOADS[oname]
+        orr = timed_solves(ctx, stream, oc, oc["nb"], args.steps, args.warmup, rank, ws)
+        ov = hpl_flops(oc["n"], oc["nrhs"]) * ws / (orr["ms"] * 1e-3) / 1e12
+        ozaki_line = {"workload": oname, "value": ov, "unit": "TFLOP/s", "ms_per_step": orr["ms"],
+                      "speedup_vs_f64": ov / (flops * ws / (ms * 1e-3) / 1e12), "scaled_residual": orr["res"],
+                      "roofline": gemm_roofline(orr["prof"], oc["n"], oc["nb"], oc["prec"], args.steps, peaks, oname,
+                                                True),
+                      "phases_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in orr["prof"].items()}}
+        launches += orr["launches"]
+        del orr
+        torch.cuda.empty_cache()
+
     batched_line = None
     if not mixed and not args.no_mixed and wname == DEFAULT:
         batched_line = batched_measure(ctx, stream, WORKLOADS["batched_4096"], args.steps, args.warmup)
@@ -547,7 +579,7 @@ def run_ours(args, cfg, wname):
             "metric": METRIC,
             "value": flops * ws / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if not mixed else f"{prec}+f32acc+f64refine", "data": "synthetic",
+            "vs_baseline": None, "dtype": ("f64 (bf16-split products)" if ozaki else "f64") if not mixed else f"{prec}+f32acc+f64refine", "data": "synthetic",
             "config": {"workload": wname, "n": n, "nb": nb or "auto", "nrhs": nrhs, "precision": prec,
                        "matrix": "uniform[-0.5,0.5]" + (f" + {cfg['shift']}*n*I" if shift else ""),
                        "l2": f"inputs larger than L2 (A = {n * n * 8 / 2 ** 30:.1f} GiB FP64)",
@@ -561,6 +593,7 @@ def run_ours(args, cfg, wname):
             "clocks": ck,
             "mixed": mixed_line,
             "paper_nopiv": nopiv_line,
+            "f64_ozaki": ozaki_line,
             "batched": batched_line,
         }
         print(json.dumps(line), flush=True)

@@ -37,8 +37,8 @@
 // next slice loads while the current one is used) while B's slices q stream
 // through a 6-stage ring; warp 0 issues the TMA loads, warp 1 the tcgen05.mma
 // (M = 128, N = 128, K = 16) into one of four TMEM accumulators per pair, and
-// warps 2..9 drain each finished accumulator into their 64 per-thread 64-bit
-// sums, then update C.  Every mbarrier wait is bounded; on timeout the kernel
+// warps 4..11 drain each finished accumulator into their 64 per-thread 64-bit
+// sums (registers moved to them from warps 0..3 by setmaxnreg), then update C.  Every mbarrier wait is bounded; on timeout the kernel
 // raises ST_TIMEOUT, lets issued copies and MMAs land, frees TMEM and returns.
 #include <cuda_bf16.h>
 
@@ -59,8 +59,14 @@ constexpr int OZ_CHUNK = OZ_BM * OZ_BK * 2;          // 16 KB: one 128 x 64 BF16
 constexpr int OZ_ABUF = (OZ_KMAX / OZ_BK) * OZ_CHUNK;  // 64 KB: one resident A slice
 constexpr int OZ_BSTAGES = 6;
 constexpr int OZ_NACC = 4;     // TMEM accumulators of 128 columns
-constexpr int OZ_EPI_WARPS = 8;
-constexpr int OZ_THREADS = 32 * (2 + OZ_EPI_WARPS);
+constexpr int OZ_EPI_WARPS = 8;                  // warpgroups 1 and 2
+constexpr int OZ_THREADS = 32 * (4 + OZ_EPI_WARPS);  // warpgroup 0: TMA warp, MMA warp, two idle warps
+// Register split (setmaxnreg): warpgroup 0 gives registers to the two epilogue
+// warpgroups, which hold 64 64-bit sums per thread.  The split must fit the
+// block's launch allocation (OZ_THREADS x the kernel's register count); the
+// launcher checks that before every launch, so an increase never waits.
+constexpr int OZ_REG_LOW = 56, OZ_REG_HIGH = 224;
+constexpr int OZ_REG_POOL = OZ_REG_LOW * 128 + OZ_REG_HIGH * 256;
 constexpr int OZ_TMEM_COLS = OZ_NACC * OZ_BN;
 constexpr size_t OZ_SMEM = 1024 + 2 * (size_t)OZ_ABUF + (size_t)OZ_BSTAGES * OZ_CHUNK + 256;
 constexpr uint32_t OZ_MAGIC_BITS = 0x4B400000u;  // bit pattern of 1.5 * 2^23
@@ -190,9 +196,9 @@ struct OzParams {
 
 // a[j] += (pattern of G + 1.5 * 2^23) shifted by SH (right for SH < 0)
 template <int SH>
-__device__ __forceinline__ void oz_acc32(unsigned long long* a, const uint32_t* v) {
+__device__ __forceinline__ void oz_acc16(unsigned long long* a, const uint32_t* v) {
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
+  for (int j = 0; j < 16; ++j) {
     const uint32_t b = __float_as_uint(__uint_as_float(v[j]) + OZ_MAGIC);
     if constexpr (SH >= 0)
       a[j] += (unsigned long long)b << SH;
@@ -203,14 +209,14 @@ __device__ __forceinline__ void oz_acc32(unsigned long long* a, const uint32_t* 
 
 __device__ __forceinline__ void oz_acc_t(int t, unsigned long long* a, const uint32_t* v) {
   switch (t) {
-    case 0: oz_acc32<OZ_F>(a, v); break;
-    case 1: oz_acc32<OZ_F - 7>(a, v); break;
-    case 2: oz_acc32<OZ_F - 14>(a, v); break;
-    case 3: oz_acc32<OZ_F - 21>(a, v); break;
-    case 4: oz_acc32<OZ_F - 28>(a, v); break;
-    case 5: oz_acc32<OZ_F - 35>(a, v); break;
-    case 6: oz_acc32<OZ_F - 42>(a, v); break;
-    default: oz_acc32<OZ_F - 49>(a, v); break;
+    case 0: oz_acc16<OZ_F>(a, v); break;
+    case 1: oz_acc16<OZ_F - 7>(a, v); break;
+    case 2: oz_acc16<OZ_F - 14>(a, v); break;
+    case 3: oz_acc16<OZ_F - 21>(a, v); break;
+    case 4: oz_acc16<OZ_F - 28>(a, v); break;
+    case 5: oz_acc16<OZ_F - 35>(a, v); break;
+    case 6: oz_acc16<OZ_F - 42>(a, v); break;
+    default: oz_acc16<OZ_F - 49>(a, v); break;
   }
 }
 
@@ -219,7 +225,7 @@ __device__ __forceinline__ unsigned long long oz_corr(int t) {
   return sh >= 0 ? (unsigned long long)OZ_MAGIC_BITS << sh : (unsigned long long)(OZ_MAGIC_BITS >> (-sh));
 }
 
-__global__ void __maxnreg__(200)
+__global__ void __launch_bounds__(OZ_THREADS, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzParams P) {
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -271,7 +277,10 @@ __global__ void __maxnreg__(200)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  if (warp == 0) {
+  if (warp < 4) {
+   // warpgroup 0 (one setmaxnreg site for all four warps)
+   asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(OZ_REG_LOW));
+   if (warp == 0) {
     // ---------------- TMA producer
     if (lane == 0) {
       int apar[2] = {-1, -1};
@@ -341,7 +350,7 @@ __global__ void __maxnreg__(200)
         }
       }
     }
-  } else if (warp == 1) {
+   } else if (warp == 1) {
     // ---------------- MMA issuer: one TMEM accumulator per slice pair
     if (lane == 0) {
       int s = 0, ab = 0, acc = 0;
@@ -403,10 +412,13 @@ __global__ void __maxnreg__(200)
         }
       }
     }
+   }
   } else {
     // ---------------- epilogue: exact integer combination, then C -= I * 2^(e_i + f_j - 54)
+    // (warpgroups 1 and 2, one setmaxnreg site)
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(OZ_REG_HIGH));
     const int quarter = warp & 3;          // TMEM lane quarter this warp may access
-    const int half = (warp - 2) >> 2;      // which 64 columns of the tile
+    const int half = (warp - 4) >> 2;      // which 64 columns of the tile
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
     int acc = 0;
     uint32_t tph = 0;
@@ -439,16 +451,19 @@ __global__ void __maxnreg__(200)
           tc_fence_after();
           const int tt = p + q;
           const uint32_t taddr = tmem_base + lane_addr + (uint32_t)(acc * OZ_BN + half * 64);
-          uint32_t v[32];
-          TMEM_LD_X32(taddr, v);
-          tmem_wait_ld();
-          oz_acc_t(tt, a, v);
-          TMEM_LD_X32(taddr + 32, v);
+          uint32_t v[16];
+#pragma unroll
+          for (int c = 0; c < 48; c += 16) {
+            TMEM_LD_X16(taddr + c, v);
+            tmem_wait_ld();
+            oz_acc_t(tt, a + c, v);
+          }
+          TMEM_LD_X16(taddr + 48, v);
           tmem_wait_ld();
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(bar_tempty + 8 * acc);
-          oz_acc_t(tt, a + 32, v);
+          oz_acc_t(tt, a + 48, v);
           corr += oz_corr(tt);
           if (++acc == OZ_NACC) {
             acc = 0;
@@ -470,7 +485,16 @@ __global__ void __maxnreg__(200)
             double d = __ll2double_rn(I);
             const long long bits = __double_as_longlong(d);
             const int ex = (int)((bits >> 52) & 0x7ff) + E;
-            if (I != 0) d = (ex >= 1 && ex <= 2046) ? __longlong_as_double(bits + ((long long)E << 52)) : ldexp(d, E);
+            if (I != 0) {
+              if (ex >= 1 && ex <= 2046) {
+                d = __longlong_as_double(bits + ((long long)E << 52));
+              } else {
+                // out of the normal range: two exact power-of-two factors
+                const int e1 = E / 2, e2 = E - e1;
+                d = (d * __longlong_as_double((long long)(1023 + e1) << 52)) *
+                    __longlong_as_double((long long)(1023 + e2) << 52);
+              }
+            }
             crow[j] -= d;
           }
         }
@@ -567,6 +591,12 @@ cudaError_t ozaki_gemm(double* C, int64_t ldc, const void* ws, int m, int n, int
     return cudaErrorInvalidValue;
   cudaError_t e = allow_max_smem((const void*)oz_gemm_kernel);
   if (e != cudaSuccess) return e;
+  {
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, (const void*)oz_gemm_kernel);
+    if (e != cudaSuccess) return e;
+    if (fa.numRegs * OZ_THREADS < OZ_REG_POOL) return cudaErrorInvalidConfiguration;
+  }
   OzParams P;
   P.C = C;
   P.ldc = ldc;
