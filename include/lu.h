@@ -93,10 +93,11 @@ int lu_factor(lu_ctx ctx, int n, const double *dA, int lda, lu_prec prec, int nb
  * or column is scaled by a power of two and cut into 8 slices of 7-bit
  * integers, the 36 slice products with p + q <= 7 are exact in the FP32
  * accumulator, and they are combined exactly in 64-bit integers before one
- * FP64 rounding.  The error of an update element is below about
- * 1.2 * 2^-53 * k * 2^(e_i + f_j), with 2^e_i and 2^f_j the powers of two just
- * above the largest |L21| of row i and |U12| of column j: the order of an FP64
- * dot product's error bound.  Non-finite operands fail with LU_ERANGE. */
+ * FP64 rounding.  The error of an update element C - sum_k a b is below
+ * 2^-53 * ((1.13 k + 4) * 2^(e_i + f_j) + sum_k |a b| + |result|), with 2^e_i and
+ * 2^f_j the powers of two just above the largest |L21| of row i and |U12| of
+ * column j: the order of an FP64 dot product's error bound.  Non-finite
+ * operands fail with LU_ERANGE. */
 enum { LU_FACTOR_NOPIV = 1, LU_FACTOR_OZAKI = 2 };
 int lu_factor_ex(lu_ctx ctx, int n, const double *dA, int lda, lu_prec prec, int nb, int flags, lu_fact *out,
                  int *info);

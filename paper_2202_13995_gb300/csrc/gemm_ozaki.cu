@@ -23,14 +23,17 @@
 // Combination, exact and in integers.  G + 1.5 * 2^23 is exact in FP32 and
 // its bit pattern is 0x4B400000 + G; the epilogue adds that pattern, shifted
 // by 40 - 7t, into a 64-bit integer per element (the constant part is
-// subtracted once at the end).  The sum I is the product's scaled value with
-// 40 fraction bits below the t = 0 term; |I| < 2^63 by the bound on G.  The
-// two smallest terms (t = 6, 7) are shifted right, which truncates them below
-// 2^-40 of the t = 0 unit.  Finally C -= I * 2^(e_i + f_j - 54), one rounding.
+// subtracted once at the end).  The sum I is the product's scaled value in
+// units of 2^(e_i + f_j - 54); |I| < 2^63 by the bound on G.  The 15 pairs of
+// the two smallest orders (t = 6, 7) are shifted right, rounded to nearest.
+// Finally C -= I * 2^(e_i + f_j - 54): one rounding in the conversion of I and
+// one in the subtraction.
 //
-// Error.  The dropped pairs (t >= 8) and the splitting remainders bound the
-// error by about 1.2 * 2^-53 * k * 2^(e_i + f_j), the same order as the
-// rounding error bound of a k-term FP64 dot product.
+// Error of I * 2^(e_i + f_j - 54) against the exact sum of products, in units
+// of 2^-53 * 2^(e_i + f_j): dropped pairs (t >= 8) < 0.87 k, splitting
+// remainders < 0.25 k, rounded shifts <= 3.75; so below (1.13 k + 4).  The
+// conversion adds at most 2^-53 sum_k |a b|, the subtraction 2^-53 |result|:
+// the order of the rounding error bound of a k-term FP64 dot product.
 //
 // Kernel.  Persistent CTAs (one per SM) walk 128 x 128 output tiles.  For a
 // tile, A's slice p (128 rows x k) sits in shared memory (double-buffered, the
@@ -194,12 +197,17 @@ struct OzParams {
   int* status;
 };
 
-// a[j] += (pattern of G + 1.5 * 2^23) shifted by SH (right for SH < 0)
+// a[j] += (pattern of G + 1.5 * 2^23) shifted by SH.  A right shift (SH < 0)
+// rounds to nearest: half a unit of the shifted result rides in the float
+// constant (G + 1.5 * 2^23 + 2^(-SH-1) is still exact), and since the
+// constant's pattern has 22 low zero bits the shift of the pattern is the
+// shifted constant plus floor((G + 2^(-SH-1)) / 2^-SH).
 template <int SH>
 __device__ __forceinline__ void oz_acc16(unsigned long long* a, const uint32_t* v) {
+  constexpr float M = SH >= 0 ? OZ_MAGIC : OZ_MAGIC + (float)(1 << (-SH - 1));
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
-    const uint32_t b = __float_as_uint(__uint_as_float(v[j]) + OZ_MAGIC);
+    const uint32_t b = __float_as_uint(__uint_as_float(v[j]) + M);
     if constexpr (SH >= 0)
       a[j] += (unsigned long long)b << SH;
     else

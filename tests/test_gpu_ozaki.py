@@ -4,11 +4,13 @@
 Bars:
   - operands that the slices represent exactly (7-bit integers times a power
     of two): the update equals C - A B bit for bit (every step is exact);
-  - any FP64 operands: |C_oz - C_ref| <= 2^-52 k 2^(e_i + f_j) + 2u |C_ref|,
-    C_ref the compensated (Dot2) update of the oracle and 2^e_i, 2^f_j the
-    powers of two just above the largest |A(i, :)| and |B(:, j)|: the dropped
-    slice pairs (p + q >= 8) and the splitting remainders stay below
-    1.2 * 2^-53 k 2^(e_i + f_j), the rounding of the result adds u |C|;
+  - any FP64 operands: |C_oz - C_ref| <= u ((1.13 k + 4) 2^(e_i + f_j)
+    + (|A||B|)_ij) + 2u |C_ref|, C_ref the compensated (Dot2) update of the
+    oracle, u = 2^-53 and 2^e_i, 2^f_j the powers of two just above the
+    largest |A(i, :)| and |B(:, j)|: dropped slice pairs (p + q >= 8) < 0.87 k,
+    splitting remainders < 0.25 k, the 15 rounded right shifts <= 3.75 (in
+    units of u 2^(e_i + f_j)), then the conversion of the integer sum and the
+    subtraction round once each;
   - the factorization with this update: the FP64 bars (pivots equal to the
     oracle's, factors and x within the roundoff bounds, scaled residual < 16).
 """
@@ -55,6 +57,12 @@ def _expo(x, axis):
     return e
 
 
+def _bound(Am, Bm, ref):
+    k = Am.shape[1]
+    sc = np.ldexp(1.0, (_expo(Am, 1)[:, None] + _expo(Bm, 0)[None, :]).astype(np.int64))
+    return EPS * ((1.13 * k + 4) * sc + np.abs(Am) @ np.abs(Bm)) + 2 * EPS * np.abs(ref)
+
+
 def _run(ctx, Cm, Am, Bm):
     c = _rm(Cm)
     ctx.step_gemm_ozaki(c, _rm(Am), _rm(Bm))
@@ -81,11 +89,11 @@ def test_error_bound_against_dot2(ctx, m, n, k):
     Cm = rng.standard_normal((m, n))
     ref = O.gemm_update_dot2(Cm, Am, Bm)
     got = _run(ctx, Cm, Am, Bm)
-    scale = k * np.ldexp(1.0, (_expo(Am, 1)[:, None] + _expo(Bm, 0)[None, :]).astype(np.int64))
-    bound = 2.0 ** -52 * scale + 2 * EPS * np.abs(ref)
+    bound = _bound(Am, Bm, ref)
     err = np.abs(got - ref)
     assert (err <= bound).all(), float((err / bound).max())
-    # the plain FP64 update (the oracle's) is of the same order
+    # the plain FP64 update (the oracle's) errs by the same order
+    scale = k * np.ldexp(1.0, (_expo(Am, 1)[:, None] + _expo(Bm, 0)[None, :]).astype(np.int64))
     plain = np.abs(O.gemm_update(Cm, Am, Bm) - ref)
     assert (err / scale).max() <= 8 * max((plain / scale).max(), 2.0 ** -56)
 
@@ -101,9 +109,7 @@ def test_wide_dynamic_range_zero_lines(ctx):
     Cm = rng.standard_normal((m, n))
     ref = O.gemm_update_dot2(Cm, Am, Bm)
     got = _run(ctx, Cm, Am, Bm)
-    scale = k * np.ldexp(1.0, (_expo(Am, 1)[:, None] + _expo(Bm, 0)[None, :]).astype(np.int64))
-    bound = 2.0 ** -52 * scale + 2 * EPS * np.abs(ref)
-    assert (np.abs(got - ref) <= bound).all()
+    assert (np.abs(got - ref) <= _bound(Am, Bm, ref)).all()
     assert np.array_equal(got[7, :], Cm[7, :])
     assert np.array_equal(got[:, 11], Cm[:, 11])
 
