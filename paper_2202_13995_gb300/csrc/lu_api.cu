@@ -279,7 +279,10 @@ static int factor_loop(lu_fact f) {
   // with the update phase): the next panel's columns are updated first, then
   // that panel is factored on the side stream while the rest of the trailing
   // matrix is updated on the remaining SMs.
-  const bool lookahead = (tc || f->ozaki) && c->lookahead && c->side != nullptr;
+  // (the split FP64 update is not overlapped: its panel is FP64-bound and
+  // runs fastest on every SM, and the update needs whole SMs for its shared
+  // memory, so a concurrent panel would slow both)
+  const bool lookahead = tc && c->lookahead && c->side != nullptr;
   bool panel_ready = false;
   for (int k = 0; k < n; k += nb) {
     const int w = (n - k) < nb ? (n - k) : nb;
@@ -300,24 +303,10 @@ static int factor_loop(lu_fact f) {
     CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12, ld, w, rest, st)));
     const int w2 = rest < nb ? rest : nb;
     if (f->ozaki) {
-      double* C = (double*)A22;
       CU_TRY(PHASE(c, PH_CAST, 2, ozaki_split((const double*)L21, ld, (const double*)U12, ld, rest, rest, w,
                                                f->oz_ws, c->d_status, st)));
-      if (!lookahead || rest <= w2) {
-        CU_TRY(PHASE(c, PH_GEMM, 1, ozaki_gemm(C, ld, f->oz_ws, rest, rest, w, 0, rest, c->d_status, c->dev, st)));
-        continue;
-      }
-      CU_TRY(PHASE(c, PH_GEMM, 1, ozaki_gemm(C, ld, f->oz_ws, rest, rest, w, 0, w2, c->d_status, c->dev, st)));
-      CU_TRY(cudaEventRecord(c->ev_next, st));
-      CU_TRY(cudaStreamWaitEvent(c->side, c->ev_next, 0));
-      CU_TRY(PHASE_ON(c, c->side, PH_PANEL, 1, launch_panel<T>(A22, ld, rest, w2, k + w, f->ipiv, f->info_d,
-                                                               c->d_status, f->ps, c->dev, c->side)));
-      CU_TRY(cudaEventRecord(c->ev_panel, c->side));
-      panel_ready = true;
-      const int gp = panel_grid_size(rest, w2, sizeof(T), c->dev, f->ps.gmax, f->ps.gtarget);
-      const int cap = c->dev.sm_count - (gp > 0 ? gp : 0);
-      CU_TRY(PHASE(c, PH_GEMM, 1, ozaki_gemm(C + w2, ld, f->oz_ws, rest, rest, w, w2, rest - w2, c->d_status, c->dev,
-                                              st, cap > 8 ? cap : 8)));
+      CU_TRY(PHASE(c, PH_GEMM, 1, ozaki_gemm((double*)A22, ld, f->oz_ws, rest, rest, w, 0, rest, c->d_status, c->dev,
+                                              st)));
       continue;
     }
     if (!tc) {
@@ -458,8 +447,6 @@ extern "C" int lu_factor_ex(lu_ctx c, int n, const double* dA, int lda, lu_prec 
   }
   if (flags & LU_FACTOR_OZAKI) {
     f->ozaki = true;
-    // a panel beside the concurrent update (lookahead) on fewer CTAs
-    f->ps.gtarget = 64;
     if ((rc = dalloc(c, &f->oz_ws, ozaki_ws_bytes(nn, nn, f->nb)))) {
       lu_fact_free(f);
       return rc;
