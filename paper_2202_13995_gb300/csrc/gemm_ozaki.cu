@@ -79,102 +79,140 @@ static_assert(OZ_KMAX * 127 * 127 < (1 << 22), "a slice-pair product must stay b
 static_assert(OZ_SMEM <= 232448, "shared memory per CTA");
 
 // ------------------------------------------------------------ splitting
+// The slices of x with |x| < 2^e: d_p = trunc(128 r_p), r_{p+1} = 128 r_p - d_p,
+// r_0 = x 2^-e.  Every step is exact in FP64, so d_p is digit p of the base-128
+// expansion of |x| 2^-e with x's sign; it is taken here from the bit pattern
+// (integer operations only: GB300's FP64 rate would make the FP64 form the
+// cost of the split).  The 56-bit magnitude M = floor(|x| 2^(56 - e)) holds the
+// eight digits, d_p = (M >> (49 - 7p)) & 127.
+__device__ __forceinline__ uint64_t oz_fixed56(uint64_t bits, int e) {
+  const int field = (int)((bits >> 52) & 0x7ff);
+  uint64_t mant = bits & 0xfffffffffffffull;
+  if (field) mant |= 1ull << 52;
+  const int sh = (field ? field : 1) - 1075 + 56 - e;  // |x| = mant 2^(field' - 1075)
+  if (sh >= 0) return sh < 64 ? mant << sh : 0ull;
+  return -sh < 64 ? mant >> (-sh) : 0ull;
+}
+
+// BF16 pattern of the integer sign * d, 0 <= d <= 127 (exact: <= 7 significant bits)
+__device__ __forceinline__ uint32_t oz_bf16_digit(uint32_t d, uint32_t sign) {
+  if (d == 0) return 0u;
+  const int k = 31 - __clz(d);  // leading bit
+  return sign | ((127u + (uint32_t)k) << 7) | ((d << (7 - k)) & 0x7fu);
+}
+
+// e with |x| < 2^e <= 2|x| for the largest |x| of a line, from its pattern (0 for 0)
+__device__ __forceinline__ int oz_expo(uint64_t absbits) {
+  if (absbits == 0) return 0;
+  const int field = (int)(absbits >> 52);
+  if (field) return field - 1022;
+  return (63 - __clzll((long long)absbits)) - 1074 + 1;  // subnormal
+}
+
 // A (m x k, row-major FP64) -> As[p][i][kpad] (BF16 integers), ea[i] = e_i.
-// One warp per row.
+// One warp per row; a lane takes element pairs (2 lane + 64 u, + 1).
 __global__ void __launch_bounds__(256) oz_split_rows_kernel(const double* __restrict__ A, int64_t lda, int m, int k,
                                                             int kpad, __nv_bfloat16* __restrict__ As,
                                                             int* __restrict__ ea, int* status) {
   const int lane = threadIdx.x & 31;
   const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
   if (i >= m) return;
-  double v[OZ_KMAX / 32];
-  double mx = 0.0;
+  constexpr int U = OZ_KMAX / 64;
+  uint64_t v[U][2];
+  uint64_t mx = 0;
   bool bad = false;
+  const double* row = A + (int64_t)i * lda;
 #pragma unroll
-  for (int u = 0; u < OZ_KMAX / 32; ++u) {
-    const int c = lane + 32 * u;
-    v[u] = c < k ? A[(int64_t)i * lda + c] : 0.0;
-    bad |= !isfinite(v[u]);
-    mx = fmax(mx, fabs(v[u]));
+  for (int u = 0; u < U; ++u) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = 64 * u + 2 * lane + h;
+      v[u][h] = c < k ? (uint64_t)__double_as_longlong(row[c]) : 0ull;
+      const uint64_t a = v[u][h] & 0x7fffffffffffffffull;
+      bad |= (a >> 52) == 0x7ff;
+      mx = a > mx ? a : mx;
+    }
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-  if (__any_sync(0xffffffffu, bad)) {
-    if (lane == 0) atomicOr(status, ST_RANGE);
-    mx = 0.0;
+  for (int off = 16; off > 0; off >>= 1) {
+    const uint64_t o = __shfl_xor_sync(0xffffffffu, mx, off);
+    mx = o > mx ? o : mx;
   }
-  const int e = mx > 0.0 ? ilogb(mx) + 1 : 0;  // mx < 2^e
+  const bool zero = __any_sync(0xffffffffu, bad);
+  if (zero && lane == 0) atomicOr(status, ST_RANGE);
+  const int e = zero ? 0 : oz_expo(mx);
   if (lane == 0) ea[i] = e;
+  uint32_t* out = reinterpret_cast<uint32_t*>(As);
 #pragma unroll
-  for (int u = 0; u < OZ_KMAX / 32; ++u) {
-    const int c = lane + 32 * u;
-    if (c >= kpad) continue;
-    double r = mx > 0.0 ? ldexp(v[u], -e) : 0.0;  // |r| < 1
+  for (int u = 0; u < U; ++u) {
+    const int c = 64 * u + 2 * lane;
+    if (c >= kpad) break;
+    const uint64_t M0 = zero ? 0ull : oz_fixed56(v[u][0], e);
+    const uint64_t M1 = zero ? 0ull : oz_fixed56(v[u][1], e);
+    const uint32_t s0 = (uint32_t)(v[u][0] >> 48) & 0x8000u, s1 = (uint32_t)(v[u][1] >> 48) & 0x8000u;
 #pragma unroll
     for (int p = 0; p < OZ_S; ++p) {
-      r *= (double)(1 << OZ_BITS);
-      const double d = trunc(r);
-      r -= d;
-      As[((int64_t)p * m + i) * kpad + c] = __double2bfloat16(d);
+      const int sh = 49 - OZ_BITS * p;
+      const uint32_t w = oz_bf16_digit((uint32_t)(M0 >> sh) & 127u, s0) |
+                         (oz_bf16_digit((uint32_t)(M1 >> sh) & 127u, s1) << 16);
+      out[(((int64_t)p * m + i) * kpad + c) >> 1] = w;
     }
   }
 }
 
 // B (k x n, row-major FP64) -> Bs[q][j][kpad] (column j's slice, K contiguous),
-// fb[j] = f_j.  CTA = 32 columns.
+// fb[j] = f_j.  CTA = 32 columns; 64-row blocks go through shared memory.
 __global__ void __launch_bounds__(256) oz_split_cols_kernel(const double* __restrict__ B, int64_t ldb, int k, int n,
                                                             int kpad, __nv_bfloat16* __restrict__ Bs,
                                                             int* __restrict__ fb, int* status) {
-  __shared__ double tile[OZ_BK][33];
-  __shared__ double red[8][32];
+  __shared__ uint64_t tile[OZ_BK][33];
+  __shared__ uint64_t red[8][32];
   __shared__ int fe[32];
   constexpr int ZERO_COL = 1 << 20;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j0 = blockIdx.x * 32, j = j0 + lane;
-  double mx = 0.0;
+  uint64_t mx = 0;
   bool bad = false;
   for (int r = warp; r < k; r += 8) {
-    const double x = j < n ? B[(int64_t)r * ldb + j] : 0.0;
-    bad |= !isfinite(x);
-    mx = fmax(mx, fabs(x));
+    const uint64_t a = j < n ? ((uint64_t)__double_as_longlong(B[(int64_t)r * ldb + j]) & 0x7fffffffffffffffull) : 0ull;
+    bad |= (a >> 52) == 0x7ff;
+    mx = a > mx ? a : mx;
   }
-  red[warp][lane] = bad ? -1.0 : mx;
+  red[warp][lane] = bad ? ~0ull : mx;
   __syncthreads();
   if (warp == 0) {
     bool b2 = false;
-    mx = 0.0;
+    mx = 0;
     for (int w = 0; w < 8; ++w) {
-      b2 |= red[w][lane] < 0.0;
-      mx = fmax(mx, red[w][lane]);
+      const uint64_t o = red[w][lane];
+      b2 |= o == ~0ull;
+      if (o != ~0ull) mx = o > mx ? o : mx;
     }
-    if (b2) {
-      atomicOr(status, ST_RANGE);
-      mx = 0.0;
-    }
-    const int e = mx > 0.0 ? ilogb(mx) + 1 : 0;
-    fe[lane] = mx > 0.0 ? e : ZERO_COL;
+    if (b2) atomicOr(status, ST_RANGE);
+    const int e = b2 ? 0 : oz_expo(mx);
+    fe[lane] = (b2 || mx == 0) ? ZERO_COL : e;
     if (j < n) fb[j] = e;
   }
   __syncthreads();
+  uint32_t* out = reinterpret_cast<uint32_t*>(Bs);
   for (int r0 = 0; r0 < kpad; r0 += OZ_BK) {
     for (int r = warp; r < OZ_BK; r += 8)
-      tile[r][lane] = (r0 + r < k && j < n) ? B[(int64_t)(r0 + r) * ldb + j] : 0.0;
+      tile[r][lane] = (r0 + r < k && j < n) ? (uint64_t)__double_as_longlong(B[(int64_t)(r0 + r) * ldb + j]) : 0ull;
     __syncthreads();
     for (int c = warp; c < 32; c += 8) {
       const int jj = j0 + c;
       if (jj >= n) continue;
       const int e = fe[c];
+      const uint64_t x0 = tile[2 * lane][c], x1 = tile[2 * lane + 1][c];
+      const uint64_t M0 = e == ZERO_COL ? 0ull : oz_fixed56(x0, e);
+      const uint64_t M1 = e == ZERO_COL ? 0ull : oz_fixed56(x1, e);
+      const uint32_t s0 = (uint32_t)(x0 >> 48) & 0x8000u, s1 = (uint32_t)(x1 >> 48) & 0x8000u;
 #pragma unroll
-      for (int h = 0; h < OZ_BK / 32; ++h) {
-        const int r = h * 32 + lane;
-        double x = e == ZERO_COL ? 0.0 : ldexp(tile[r][c], -e);
-#pragma unroll
-        for (int q = 0; q < OZ_S; ++q) {
-          x *= (double)(1 << OZ_BITS);
-          const double d = trunc(x);
-          x -= d;
-          Bs[((int64_t)q * n + jj) * kpad + r0 + r] = __double2bfloat16(d);
-        }
+      for (int q = 0; q < OZ_S; ++q) {
+        const int sh = 49 - OZ_BITS * q;
+        const uint32_t w = oz_bf16_digit((uint32_t)(M0 >> sh) & 127u, s0) |
+                           (oz_bf16_digit((uint32_t)(M1 >> sh) & 127u, s1) << 16);
+        out[(((int64_t)q * n + jj) * kpad + r0 + 2 * lane) >> 1] = w;
       }
     }
     __syncthreads();
@@ -231,6 +269,26 @@ __device__ __forceinline__ void oz_acc_t(int t, unsigned long long* a, const uin
 __device__ __forceinline__ unsigned long long oz_corr(int t) {
   const int sh = OZ_F - OZ_BITS * t;
   return sh >= 0 ? (unsigned long long)OZ_MAGIC_BITS << sh : (unsigned long long)(OZ_MAGIC_BITS >> (-sh));
+}
+
+// I * 2^E rounded to nearest even (I != 0), from integer operations: the
+// leading one goes to bit 63, the top 53 bits round on the 11 below them, and
+// the exponent takes E.  Results outside the normal range (never for
+// LU-scaled data) multiply the converted I by two exact powers of two.
+__device__ __forceinline__ double oz_scaled(long long I, int E) {
+  const unsigned long long sgn = (unsigned long long)I & 0x8000000000000000ull;
+  unsigned long long u = I < 0 ? 0ull - (unsigned long long)I : (unsigned long long)I;
+  const int lz = __clzll((long long)u);
+  u <<= lz;
+  unsigned long long mant = u >> 11;
+  const unsigned rem = (unsigned)(u & 0x7ffu);
+  mant += (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) ? 1ull : 0ull;
+  const int ex = 1023 + 63 - lz + E;  // biased exponent of the leading one
+  if (ex >= 1 && ex <= 2046)
+    return __longlong_as_double((long long)(sgn | (((unsigned long long)(ex - 1) << 52) + mant)));
+  const double d = __longlong_as_double((long long)(sgn | (((unsigned long long)(1023 + 63 - lz - 1) << 52) + mant)));
+  const int e1 = E / 2, e2 = E - e1;
+  return (d * __longlong_as_double((long long)(1023 + e1) << 52)) * __longlong_as_double((long long)(1023 + e2) << 52);
 }
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
@@ -459,19 +517,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           tc_fence_after();
           const int tt = p + q;
           const uint32_t taddr = tmem_base + lane_addr + (uint32_t)(acc * OZ_BN + half * 64);
-          uint32_t v[16];
-#pragma unroll
-          for (int c = 0; c < 48; c += 16) {
-            TMEM_LD_X16(taddr + c, v);
-            tmem_wait_ld();
-            oz_acc_t(tt, a + c, v);
-          }
-          TMEM_LD_X16(taddr + 48, v);
+          uint32_t v[64];  // all four loads in flight, one wait
+          TMEM_LD_X16(taddr, v);
+          TMEM_LD_X16(taddr + 16, (v + 16));
+          TMEM_LD_X16(taddr + 32, (v + 32));
+          TMEM_LD_X16(taddr + 48, (v + 48));
           tmem_wait_ld();
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(bar_tempty + 8 * acc);
-          oz_acc_t(tt, a + 48, v);
+#pragma unroll
+          for (int c = 0; c < 64; c += 16) oz_acc_t(tt, a + c, v + c);
           corr += oz_corr(tt);
           if (++acc == OZ_NACC) {
             acc = 0;
@@ -481,29 +537,26 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       }
       if (!ok) break;
       if (rok) {
-        // the scale 2^(e_i + f_j - 54) goes into the exponent field by an
-        // integer add (the FP64 pipe does only the subtraction); results
-        // outside the normal range take ldexp
+        // C -= I 2^(e_i + f_j - 54), 16 columns at a time with their loads
+        // batched; the conversion and the scaling are integer operations
+        // (oz_scaled), the FP64 pipe does only the subtraction
         const int er = P.ea[row] - (OZ_F + 2 * OZ_BITS);
 #pragma unroll
-        for (int j = 0; j < 64; ++j) {
-          if (col0 + j < P.n) {
-            const long long I = (long long)(a[j] - corr);
-            const int E = er + P.fb[col0 + j];
-            double d = __ll2double_rn(I);
-            const long long bits = __double_as_longlong(d);
-            const int ex = (int)((bits >> 52) & 0x7ff) + E;
-            if (I != 0) {
-              if (ex >= 1 && ex <= 2046) {
-                d = __longlong_as_double(bits + ((long long)E << 52));
-              } else {
-                // out of the normal range: two exact power-of-two factors
-                const int e1 = E / 2, e2 = E - e1;
-                d = (d * __longlong_as_double((long long)(1023 + e1) << 52)) *
-                    __longlong_as_double((long long)(1023 + e2) << 52);
-              }
+        for (int c = 0; c < 64; c += 16) {
+          double cv[16];
+          int fv[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const bool in = col0 + c + j < P.n;
+            cv[j] = in ? crow[c + j] : 0.0;
+            fv[j] = in ? P.fb[col0 + c + j] : 0;
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            if (col0 + c + j < P.n) {
+              const long long I = (long long)(a[c + j] - corr);
+              crow[c + j] = I != 0 ? cv[j] - oz_scaled(I, er + fv[j]) : cv[j];
             }
-            crow[j] -= d;
           }
         }
       }
