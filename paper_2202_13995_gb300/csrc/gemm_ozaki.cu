@@ -231,38 +231,43 @@ struct OzParams {
   int tiles_m, tiles_n;
   const int* ea;   // row exponents e_i
   const int* fb;   // column exponents f_j of this update's columns
+  int vec_ok;      // C rows 32-byte aligned (vector loads and stores)
   uint32_t idesc;
   int* status;
 };
 
-// a[j] += (pattern of G + 1.5 * 2^23) shifted by SH.  A right shift (SH < 0)
-// rounds to nearest: half a unit of the shifted result rides in the float
-// constant (G + 1.5 * 2^23 + 2^(-SH-1) is still exact), and since the
-// constant's pattern has 22 low zero bits the shift of the pattern is the
-// shifted constant plus floor((G + 2^(-SH-1)) / 2^-SH).
-template <int SH>
-__device__ __forceinline__ void oz_acc16(unsigned long long* a, const uint32_t* v) {
-  constexpr float M = SH >= 0 ? OZ_MAGIC : OZ_MAGIC + (float)(1 << (-SH - 1));
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const uint32_t b = __float_as_uint(__uint_as_float(v[j]) + M);
-    if constexpr (SH >= 0)
-      a[j] += (unsigned long long)b << SH;
-    else
-      a[j] += (unsigned long long)(b >> (-SH));
-  }
+// 64-bit add of (xh:xl) into (h:l) through the carry flag.
+__device__ __forceinline__ void oz_add64(uint32_t& l, uint32_t& h, uint32_t xl, uint32_t xh) {
+  asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, %3;" : "+r"(l), "+r"(h) : "r"(xl), "r"(xh));
 }
 
-__device__ __forceinline__ void oz_acc_t(int t, unsigned long long* a, const uint32_t* v) {
-  switch (t) {
-    case 0: oz_acc16<OZ_F>(a, v); break;
-    case 1: oz_acc16<OZ_F - 7>(a, v); break;
-    case 2: oz_acc16<OZ_F - 14>(a, v); break;
-    case 3: oz_acc16<OZ_F - 21>(a, v); break;
-    case 4: oz_acc16<OZ_F - 28>(a, v); break;
-    case 5: oz_acc16<OZ_F - 35>(a, v); break;
-    case 6: oz_acc16<OZ_F - 42>(a, v); break;
-    default: oz_acc16<OZ_F - 49>(a, v); break;
+// (hi:lo)[j] += pattern of (G_j + 1.5 * 2^23) shifted by 40 - 7t (64-bit sums
+// kept as two 32-bit words).  t <= 1 touches the high word only; t = 6, 7 are
+// right shifts rounded to nearest: half a unit of the shifted result rides in
+// the float constant (G + 1.5 * 2^23 + 2^(r-1) is still exact), and since the
+// constant's pattern has 22 low zero bits, the shifted pattern is the shifted
+// constant plus floor((G + 2^(r-1)) / 2^r).
+__device__ __forceinline__ void oz_acc64(uint32_t* lo, uint32_t* hi, const uint32_t* v, int t) {
+  const int sh = OZ_F - OZ_BITS * t;
+  if (sh >= 32) {
+    const uint32_t mul = 1u << (sh - 32);
+#pragma unroll
+    for (int j = 0; j < 64; ++j) hi[j] += __float_as_uint(__uint_as_float(v[j]) + OZ_MAGIC) * mul;
+  } else if (sh >= 0) {
+    const int rs = 32 - sh;
+#pragma unroll
+    for (int j = 0; j < 64; ++j) {
+      const uint32_t b = __float_as_uint(__uint_as_float(v[j]) + OZ_MAGIC);
+      oz_add64(lo[j], hi[j], b << sh, b >> rs);
+    }
+  } else {
+    const int r = -sh;
+    const float M = OZ_MAGIC + (float)(1 << (r - 1));
+#pragma unroll
+    for (int j = 0; j < 64; ++j) {
+      const uint32_t b = __float_as_uint(__uint_as_float(v[j]) + M);
+      oz_add64(lo[j], hi[j], b >> r, 0u);
+    }
   }
 }
 
@@ -289,6 +294,45 @@ __device__ __forceinline__ double oz_scaled(long long I, int E) {
   const double d = __longlong_as_double((long long)(sgn | (((unsigned long long)(1023 + 63 - lz - 1) << 52) + mant)));
   const int e1 = E / 2, e2 = E - e1;
   return (d * __longlong_as_double((long long)(1023 + e1) << 52)) * __longlong_as_double((long long)(1023 + e2) << 52);
+}
+
+// C - I 2^E for one element.  When C and I 2^E have a common unit 2^E' with
+// both multiples below 2^62 (the usual case: the trailing matrix and the
+// update are of one order) the difference is exact in 64-bit integers
+// (|I| < 2^62.1 by the slice bounds) and is rounded once; otherwise the
+// converted product is subtracted in FP64.
+__device__ __forceinline__ double oz_sub(double c, long long I, int E) {
+  const unsigned long long cb = (unsigned long long)__double_as_longlong(c);
+  const int field = (int)((cb >> 52) & 0x7ff);
+  unsigned long long mant = cb & 0xfffffffffffffull;
+  if (mant == 0 && field == 0) return I != 0 ? oz_scaled(-I, E) : c;  // c = +-0
+  if (field) mant |= 1ull << 52;
+  const int sh = (field ? field : 1) - 1075 - E;  // c = mant 2^(E + sh)
+  if (field != 0x7ff) {
+    if (sh >= 0 && sh <= 8) {  // unit 2^E: |c| 2^-E < 2^61
+      long long ic = (long long)(mant << sh);
+      if (cb >> 63) ic = -ic;
+      const long long J = ic - I;
+      return J != 0 ? oz_scaled(J, E) : 0.0;
+    }
+    if (sh < 0 && sh >= -10) {  // unit 2^(E + sh) when |I| 2^-sh < 2^62
+      const unsigned long long ua = I < 0 ? 0ull - (unsigned long long)I : (unsigned long long)I;
+      if ((ua >> (62 + sh)) == 0) {
+        const long long ic = (cb >> 63) ? -(long long)mant : (long long)mant;
+        const long long J = ic - (long long)((unsigned long long)I << (-sh));
+        return J != 0 ? oz_scaled(J, E + sh) : 0.0;
+      }
+    }
+  }
+  return I != 0 ? c - oz_scaled(I, E) : c;
+}
+
+__device__ __forceinline__ void ld_v4(const double* p, double* d) {
+  asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];" : "=d"(d[0]), "=d"(d[1]), "=d"(d[2]), "=d"(d[3]) : "l"(p));
+}
+__device__ __forceinline__ void st_v4(double* p, const double* d) {
+  asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(d[0]), "d"(d[1]), "d"(d[2]), "d"(d[3])
+               : "memory");
 }
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
@@ -501,9 +545,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         for (int c = 0; c < 64; c += 16)
           if (col0 + c < P.n) asm volatile("prefetch.global.L2 [%0];" ::"l"(crow + c));
       }
-      unsigned long long a[64];
+      uint32_t lo[64], hi[64];
 #pragma unroll
-      for (int j = 0; j < 64; ++j) a[j] = 0ull;
+      for (int j = 0; j < 64; ++j) lo[j] = hi[j] = 0u;
       unsigned long long corr = 0ull;
       for (int p = 0; p < OZ_S && ok; ++p) {
         for (int q = 0; q < OZ_S - p; ++q) {
@@ -527,7 +571,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           __syncwarp();
           if (lane == 0) mbar_arrive(bar_tempty + 8 * acc);
 #pragma unroll
-          for (int c = 0; c < 64; c += 16) oz_acc_t(tt, a + c, v + c);
+          oz_acc64(lo, hi, v, tt);
           corr += oz_corr(tt);
           if (++acc == OZ_NACC) {
             acc = 0;
@@ -537,26 +581,51 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       }
       if (!ok) break;
       if (rok) {
-        // C -= I 2^(e_i + f_j - 54), 16 columns at a time with their loads
-        // batched; the conversion and the scaling are integer operations
-        // (oz_scaled), the FP64 pipe does only the subtraction
+        // C -= I 2^(e_i + f_j - 54), 8 columns at a time: the chunk's sums
+        // are copied out by a switch (static register indices, one copy of
+        // the code below), C moves in 32-byte vectors when aligned
         const int er = P.ea[row] - (OZ_F + 2 * OZ_BITS);
+#pragma unroll 1
+        for (int c = 0; c < 8; ++c) {
+          const int gc = col0 + 8 * c;
+          if (gc >= P.n) break;
+          uint32_t tl[8], th[8];
+          switch (c) {
+#define OZ_CP(K)                                    \
+  case K:                                           \
+    _Pragma("unroll") for (int j = 0; j < 8; ++j) { \
+      tl[j] = lo[8 * K + j];                        \
+      th[j] = hi[8 * K + j];                        \
+    }                                               \
+    break;
+            OZ_CP(0) OZ_CP(1) OZ_CP(2) OZ_CP(3) OZ_CP(4) OZ_CP(5) OZ_CP(6) OZ_CP(7)
+#undef OZ_CP
+          }
+          double* cp = crow + 8 * c;
+          const bool full = P.vec_ok && gc + 8 <= P.n;
+          double cv[8];
+          int fv[8];
+          if (full) {
+            ld_v4(cp, cv);
+            ld_v4(cp + 4, cv + 4);
+          } else {
 #pragma unroll
-        for (int c = 0; c < 64; c += 16) {
-          double cv[16];
-          int fv[16];
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const bool in = col0 + c + j < P.n;
-            cv[j] = in ? crow[c + j] : 0.0;
-            fv[j] = in ? P.fb[col0 + c + j] : 0;
+            for (int j = 0; j < 8; ++j) cv[j] = gc + j < P.n ? cp[j] : 0.0;
           }
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            if (col0 + c + j < P.n) {
-              const long long I = (long long)(a[c + j] - corr);
-              crow[c + j] = I != 0 ? cv[j] - oz_scaled(I, er + fv[j]) : cv[j];
-            }
+          for (int j = 0; j < 8; ++j) fv[j] = gc + j < P.n ? P.fb[gc + j] : 0;
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const long long I = (long long)((((unsigned long long)th[j] << 32) | tl[j]) - corr);
+            cv[j] = oz_sub(cv[j], I, er + fv[j]);
+          }
+          if (full) {
+            st_v4(cp, cv);
+            st_v4(cp + 4, cv + 4);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (gc + j < P.n) cp[j] = cv[j];
           }
         }
       }
@@ -672,6 +741,7 @@ cudaError_t ozaki_gemm(double* C, int64_t ldc, const void* ws, int m, int n, int
   P.ea = L.ea;
   P.fb = L.fb + col0;
   P.idesc = tc_idesc_mn(1u, OZ_BM, OZ_BN);
+  P.vec_ok = (((uintptr_t)C & 31u) == 0 && (ldc % 4) == 0) ? 1 : 0;
   P.status = status;
   const int ntiles = P.tiles_m * P.tiles_n;
   int grid = ntiles < dev.sm_count ? ntiles : dev.sm_count;
