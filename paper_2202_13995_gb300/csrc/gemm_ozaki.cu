@@ -327,14 +327,6 @@ __device__ __forceinline__ double oz_sub(double c, long long I, int E) {
   return I != 0 ? c - oz_scaled(I, E) : c;
 }
 
-__device__ __forceinline__ void ld_v4(const double* p, double* d) {
-  asm volatile("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];" : "=d"(d[0]), "=d"(d[1]), "=d"(d[2]), "=d"(d[3]) : "l"(p));
-}
-__device__ __forceinline__ void st_v4(double* p, const double* d) {
-  asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(d[0]), "d"(d[1]), "d"(d[2]), "d"(d[3])
-               : "memory");
-}
-
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzParams P) {
   extern __shared__ unsigned char smem_raw[];
@@ -539,17 +531,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const bool rok = row < P.m;
       const int col0 = tn * OZ_BN + half * 64;
       double* crow = P.C + (int64_t)row * P.ldc + col0;
-      if (rok) {
-        // bring this thread's C segment into L2 while the products accumulate
-#pragma unroll
-        for (int c = 0; c < 64; c += 16)
-          if (col0 + c < P.n) asm volatile("prefetch.global.L2 [%0];" ::"l"(crow + c));
-      }
       uint32_t lo[64], hi[64];
 #pragma unroll
       for (int j = 0; j < 64; ++j) lo[j] = hi[j] = 0u;
       unsigned long long corr = 0ull;
       for (int p = 0; p < OZ_S && ok; ++p) {
+        if (p == 4 && rok) {
+          // bring this thread's C segment into L2 for the update at the end
+          // of the tile (10 of the 36 slice pairs remain)
+#pragma unroll
+          for (int c = 0; c < 64; c += 16)
+            if (col0 + c < P.n) asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(crow + c));
+        }
         for (int q = 0; q < OZ_S - p; ++q) {
           int okw = 1;
           if (lane == 0) okw = mbar_wait(bar_tfull + 8 * acc, tph, P.status, abort_flag) ? 1 : 0;
@@ -570,7 +563,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(bar_tempty + 8 * acc);
-#pragma unroll
           oz_acc64(lo, hi, v, tt);
           corr += oz_corr(tt);
           if (++acc == OZ_NACC) {
@@ -581,14 +573,33 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       }
       if (!ok) break;
       if (rok) {
-        // C -= I 2^(e_i + f_j - 54), 8 columns at a time: the chunk's sums
-        // are copied out by a switch (static register indices, one copy of
-        // the code below), C moves in 32-byte vectors when aligned
+        // C -= I 2^(e_i + f_j - 54), 8 columns at a time, the next chunk's
+        // loads in flight while one is computed; the chunk's sums are copied
+        // out by a switch (static register indices, one copy of the code)
         const int er = P.ea[row] - (OZ_F + 2 * OZ_BITS);
+        double cv[8], nv[8];
+        int fv[8], nf[8];
+        auto load_chunk = [&](int c, double* dv, int* df) {
+          const int gc = col0 + 8 * c;
+          const double* cp = crow + 8 * c;
+          if (P.vec_ok && gc + 8 <= P.n) {
+            const double4_32a x0 = *reinterpret_cast<const double4_32a*>(cp);
+            const double4_32a x1 = *reinterpret_cast<const double4_32a*>(cp + 4);
+            dv[0] = x0.x; dv[1] = x0.y; dv[2] = x0.z; dv[3] = x0.w;
+            dv[4] = x1.x; dv[5] = x1.y; dv[6] = x1.z; dv[7] = x1.w;
+          } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) dv[j] = gc + j < P.n ? cp[j] : 0.0;
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) df[j] = gc + j < P.n ? P.fb[gc + j] : 0;
+        };
+        load_chunk(0, cv, fv);
 #pragma unroll 1
         for (int c = 0; c < 8; ++c) {
           const int gc = col0 + 8 * c;
           if (gc >= P.n) break;
+          if (c + 1 < 8 && gc + 8 < P.n) load_chunk(c + 1, nv, nf);
           uint32_t tl[8], th[8];
           switch (c) {
 #define OZ_CP(K)                                    \
@@ -601,31 +612,24 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             OZ_CP(0) OZ_CP(1) OZ_CP(2) OZ_CP(3) OZ_CP(4) OZ_CP(5) OZ_CP(6) OZ_CP(7)
 #undef OZ_CP
           }
-          double* cp = crow + 8 * c;
-          const bool full = P.vec_ok && gc + 8 <= P.n;
-          double cv[8];
-          int fv[8];
-          if (full) {
-            ld_v4(cp, cv);
-            ld_v4(cp + 4, cv + 4);
-          } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) cv[j] = gc + j < P.n ? cp[j] : 0.0;
-          }
-#pragma unroll
-          for (int j = 0; j < 8; ++j) fv[j] = gc + j < P.n ? P.fb[gc + j] : 0;
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const long long I = (long long)((((unsigned long long)th[j] << 32) | tl[j]) - corr);
             cv[j] = oz_sub(cv[j], I, er + fv[j]);
           }
-          if (full) {
-            st_v4(cp, cv);
-            st_v4(cp + 4, cv + 4);
+          double* cp = crow + 8 * c;
+          if (P.vec_ok && gc + 8 <= P.n) {
+            *reinterpret_cast<double4_32a*>(cp) = make_double4_32a(cv[0], cv[1], cv[2], cv[3]);
+            *reinterpret_cast<double4_32a*>(cp + 4) = make_double4_32a(cv[4], cv[5], cv[6], cv[7]);
           } else {
 #pragma unroll
             for (int j = 0; j < 8; ++j)
               if (gc + j < P.n) cp[j] = cv[j];
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            cv[j] = nv[j];
+            fv[j] = nf[j];
           }
         }
       }
