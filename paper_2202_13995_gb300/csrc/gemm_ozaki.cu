@@ -41,7 +41,11 @@
 // through a 6-stage ring; warp 0 issues the TMA loads, warp 1 the tcgen05.mma
 // (M = 128, N = 128, K = 16) into one of four TMEM accumulators per pair, and
 // warps 4..11 drain each finished accumulator into their 64 per-thread 64-bit
-// sums (registers moved to them from warps 0..3 by setmaxnreg), then update C.  Every mbarrier wait is bounded; on timeout the kernel
+// sums (registers moved to them from warps 0..3 by setmaxnreg).  A finished
+// tile's sums are parked in a per-CTA scratch (L2-resident) and applied to C
+// two columns per slice pair of the next tile, so the FP64 conversion and
+// subtraction (GB300 runs about two FP64 operations per clock per SM) overlap
+// the next tile's products instead of stalling them.  Every mbarrier wait is bounded; on timeout the kernel
 // raises ST_TIMEOUT, lets issued copies and MMAs land, frees TMEM and returns.
 #include <cuda_bf16.h>
 
@@ -231,7 +235,8 @@ struct OzParams {
   int tiles_m, tiles_n;
   const int* ea;   // row exponents e_i
   const int* fb;   // column exponents f_j of this update's columns
-  int vec_ok;      // C rows 32-byte aligned (vector loads and stores)
+  int vec_ok;      // C rows 16-byte aligned (vector loads and stores)
+  long long* scratch;  // per CTA: the previous tile's sums (OZ_BM x OZ_BN)
   uint32_t idesc;
   int* status;
 };
@@ -247,16 +252,16 @@ __device__ __forceinline__ void oz_add64(uint32_t& l, uint32_t& h, uint32_t xl, 
 // the float constant (G + 1.5 * 2^23 + 2^(r-1) is still exact), and since the
 // constant's pattern has 22 low zero bits, the shifted pattern is the shifted
 // constant plus floor((G + 2^(r-1)) / 2^r).
-__device__ __forceinline__ void oz_acc64(uint32_t* lo, uint32_t* hi, const uint32_t* v, int t) {
+__device__ __forceinline__ void oz_acc32(uint32_t* lo, uint32_t* hi, const uint32_t* v, int t) {
   const int sh = OZ_F - OZ_BITS * t;
   if (sh >= 32) {
     const uint32_t mul = 1u << (sh - 32);
 #pragma unroll
-    for (int j = 0; j < 64; ++j) hi[j] += __float_as_uint(__uint_as_float(v[j]) + OZ_MAGIC) * mul;
+    for (int j = 0; j < 32; ++j) hi[j] += __float_as_uint(__uint_as_float(v[j]) + OZ_MAGIC) * mul;
   } else if (sh >= 0) {
     const int rs = 32 - sh;
 #pragma unroll
-    for (int j = 0; j < 64; ++j) {
+    for (int j = 0; j < 32; ++j) {
       const uint32_t b = __float_as_uint(__uint_as_float(v[j]) + OZ_MAGIC);
       oz_add64(lo[j], hi[j], b << sh, b >> rs);
     }
@@ -264,7 +269,7 @@ __device__ __forceinline__ void oz_acc64(uint32_t* lo, uint32_t* hi, const uint3
     const int r = -sh;
     const float M = OZ_MAGIC + (float)(1 << (r - 1));
 #pragma unroll
-    for (int j = 0; j < 64; ++j) {
+    for (int j = 0; j < 32; ++j) {
       const uint32_t b = __float_as_uint(__uint_as_float(v[j]) + M);
       oz_add64(lo[j], hi[j], b >> r, 0u);
     }
@@ -276,55 +281,21 @@ __device__ __forceinline__ unsigned long long oz_corr(int t) {
   return sh >= 0 ? (unsigned long long)OZ_MAGIC_BITS << sh : (unsigned long long)(OZ_MAGIC_BITS >> (-sh));
 }
 
-// I * 2^E rounded to nearest even (I != 0), from integer operations: the
-// leading one goes to bit 63, the top 53 bits round on the 11 below them, and
-// the exponent takes E.  Results outside the normal range (never for
-// LU-scaled data) multiply the converted I by two exact powers of two.
-__device__ __forceinline__ double oz_scaled(long long I, int E) {
-  const unsigned long long sgn = (unsigned long long)I & 0x8000000000000000ull;
-  unsigned long long u = I < 0 ? 0ull - (unsigned long long)I : (unsigned long long)I;
-  const int lz = __clzll((long long)u);
-  u <<= lz;
-  unsigned long long mant = u >> 11;
-  const unsigned rem = (unsigned)(u & 0x7ffu);
-  mant += (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) ? 1ull : 0ull;
-  const int ex = 1023 + 63 - lz + E;  // biased exponent of the leading one
-  if (ex >= 1 && ex <= 2046)
-    return __longlong_as_double((long long)(sgn | (((unsigned long long)(ex - 1) << 52) + mant)));
-  const double d = __longlong_as_double((long long)(sgn | (((unsigned long long)(1023 + 63 - lz - 1) << 52) + mant)));
-  const int e1 = E / 2, e2 = E - e1;
-  return (d * __longlong_as_double((long long)(1023 + e1) << 52)) * __longlong_as_double((long long)(1023 + e2) << 52);
-}
-
-// C - I 2^E for one element.  When C and I 2^E have a common unit 2^E' with
-// both multiples below 2^62 (the usual case: the trailing matrix and the
-// update are of one order) the difference is exact in 64-bit integers
-// (|I| < 2^62.1 by the slice bounds) and is rounded once; otherwise the
-// converted product is subtracted in FP64.
+// C - I 2^E: I converted to FP64 (one rounding), scaled by 2^E through its
+// exponent field (exact; two exact power-of-two products outside the normal
+// range), then subtracted (one rounding).
 __device__ __forceinline__ double oz_sub(double c, long long I, int E) {
-  const unsigned long long cb = (unsigned long long)__double_as_longlong(c);
-  const int field = (int)((cb >> 52) & 0x7ff);
-  unsigned long long mant = cb & 0xfffffffffffffull;
-  if (mant == 0 && field == 0) return I != 0 ? oz_scaled(-I, E) : c;  // c = +-0
-  if (field) mant |= 1ull << 52;
-  const int sh = (field ? field : 1) - 1075 - E;  // c = mant 2^(E + sh)
-  if (field != 0x7ff) {
-    if (sh >= 0 && sh <= 8) {  // unit 2^E: |c| 2^-E < 2^61
-      long long ic = (long long)(mant << sh);
-      if (cb >> 63) ic = -ic;
-      const long long J = ic - I;
-      return J != 0 ? oz_scaled(J, E) : 0.0;
-    }
-    if (sh < 0 && sh >= -10) {  // unit 2^(E + sh) when |I| 2^-sh < 2^62
-      const unsigned long long ua = I < 0 ? 0ull - (unsigned long long)I : (unsigned long long)I;
-      if ((ua >> (62 + sh)) == 0) {
-        const long long ic = (cb >> 63) ? -(long long)mant : (long long)mant;
-        const long long J = ic - (long long)((unsigned long long)I << (-sh));
-        return J != 0 ? oz_scaled(J, E + sh) : 0.0;
-      }
-    }
+  if (I == 0) return c;
+  double d = __ll2double_rn(I);
+  const long long bits = __double_as_longlong(d);
+  const int ex = (int)((bits >> 52) & 0x7ff) + E;
+  if (ex >= 1 && ex <= 2046) {
+    d = __longlong_as_double(bits + ((long long)E << 52));
+  } else {
+    const int e1 = E / 2, e2 = E - e1;
+    d = (d * __longlong_as_double((long long)(1023 + e1) << 52)) * __longlong_as_double((long long)(1023 + e2) << 52);
   }
-  return I != 0 ? c - oz_scaled(I, E) : c;
+  return c - d;
 }
 
 __global__ void __launch_bounds__(OZ_THREADS, 1)
@@ -521,7 +492,50 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(OZ_REG_HIGH));
     const int quarter = warp & 3;          // TMEM lane quarter this warp may access
     const int half = (warp - 4) >> 2;      // which 64 columns of the tile
+    const int et = threadIdx.x - 128;      // 0 .. 255
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+    // This thread's 64 sums of the previous tile, parked in the CTA's scratch
+    // ([pair of columns][thread][2]: a warp's accesses are contiguous) and
+    // applied to C two columns per slice pair of the next tile, so that the
+    // FP64 work of the update runs under that tile's products.
+    long long* scr = P.scratch + (size_t)blockIdx.x * (OZ_BM * OZ_BN) + 2 * et;
+    double* dcrow = nullptr;  // previous tile's C row segment (null: nothing pending)
+    int dcol0 = 0, der = 0;
+    long long qI[2];          // the chunk in flight: sums, C values, column exponents
+    double qC[2];
+    int qF[2], qk = -1;
+    auto defer_issue = [&](int k) {  // columns 2k, 2k + 1 of the pending segment
+      qk = -1;
+      if (dcrow == nullptr || dcol0 + 2 * k >= P.n) return;
+      qk = k;
+      const longlong2 iv = *reinterpret_cast<const longlong2*>(scr + (size_t)k * (2 * 256));
+      qI[0] = iv.x;
+      qI[1] = iv.y;
+      const int gc = dcol0 + 2 * k;
+      if (P.vec_ok && gc + 2 <= P.n) {
+        const double2 cv = *reinterpret_cast<const double2*>(dcrow + 2 * k);
+        qC[0] = cv.x;
+        qC[1] = cv.y;
+      } else {
+        qC[0] = dcrow[2 * k];
+        qC[1] = gc + 1 < P.n ? dcrow[2 * k + 1] : 0.0;
+      }
+      qF[0] = P.fb[gc];
+      qF[1] = gc + 1 < P.n ? P.fb[gc + 1] : 0;
+    };
+    auto defer_complete = [&]() {
+      if (qk < 0) return;
+      const int gc = dcol0 + 2 * qk;
+      const double r0 = oz_sub(qC[0], qI[0], der + qF[0]);
+      const double r1 = oz_sub(qC[1], qI[1], der + qF[1]);
+      if (P.vec_ok && gc + 2 <= P.n) {
+        *reinterpret_cast<double2*>(dcrow + 2 * qk) = make_double2(r0, r1);
+      } else {
+        dcrow[2 * qk] = r0;
+        if (gc + 1 < P.n) dcrow[2 * qk + 1] = r1;
+      }
+      qk = -1;
+    };
     int acc = 0;
     uint32_t tph = 0;
     bool ok = true;
@@ -535,15 +549,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
       for (int j = 0; j < 64; ++j) lo[j] = hi[j] = 0u;
       unsigned long long corr = 0ull;
+      int pi = 0;  // slice pair index within the tile
       for (int p = 0; p < OZ_S && ok; ++p) {
-        if (p == 4 && rok) {
-          // bring this thread's C segment into L2 for the update at the end
-          // of the tile (10 of the 36 slice pairs remain)
+        if (p == 6 && rok) {
+          // bring this tile's C segment into L2 for its deferred update
 #pragma unroll
           for (int c = 0; c < 64; c += 16)
             if (col0 + c < P.n) asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(crow + c));
         }
-        for (int q = 0; q < OZ_S - p; ++q) {
+        for (int q = 0; q < OZ_S - p; ++q, ++pi) {
           int okw = 1;
           if (lane == 0) okw = mbar_wait(bar_tfull + 8 * acc, tph, P.status, abort_flag) ? 1 : 0;
           okw = __shfl_sync(0xffffffffu, okw, 0);
@@ -554,84 +568,47 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
           tc_fence_after();
           const int tt = p + q;
           const uint32_t taddr = tmem_base + lane_addr + (uint32_t)(acc * OZ_BN + half * 64);
-          uint32_t v[64];  // all four loads in flight, one wait
+          uint32_t v[32];
           TMEM_LD_X16(taddr, v);
           TMEM_LD_X16(taddr + 16, (v + 16));
-          TMEM_LD_X16(taddr + 32, (v + 32));
-          TMEM_LD_X16(taddr + 48, (v + 48));
+          tmem_wait_ld();
+          oz_acc32(lo, hi, v, tt);
+          TMEM_LD_X16(taddr + 32, v);
+          TMEM_LD_X16(taddr + 48, (v + 16));
           tmem_wait_ld();
           tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(bar_tempty + 8 * acc);
-          oz_acc64(lo, hi, v, tt);
+          oz_acc32(lo + 32, hi + 32, v, tt);
           corr += oz_corr(tt);
           if (++acc == OZ_NACC) {
             acc = 0;
             tph ^= 1u;
           }
+          // the previous tile's update, two columns per pair, loads one pair ahead
+          defer_complete();
+          if (pi < 32) defer_issue(pi);
         }
       }
       if (!ok) break;
-      if (rok) {
-        // C -= I 2^(e_i + f_j - 54), 8 columns at a time, the next chunk's
-        // loads in flight while one is computed; the chunk's sums are copied
-        // out by a switch (static register indices, one copy of the code)
-        const int er = P.ea[row] - (OZ_F + 2 * OZ_BITS);
-        double cv[8], nv[8];
-        int fv[8], nf[8];
-        auto load_chunk = [&](int c, double* dv, int* df) {
-          const int gc = col0 + 8 * c;
-          const double* cp = crow + 8 * c;
-          if (P.vec_ok && gc + 8 <= P.n) {
-            const double4_32a x0 = *reinterpret_cast<const double4_32a*>(cp);
-            const double4_32a x1 = *reinterpret_cast<const double4_32a*>(cp + 4);
-            dv[0] = x0.x; dv[1] = x0.y; dv[2] = x0.z; dv[3] = x0.w;
-            dv[4] = x1.x; dv[5] = x1.y; dv[6] = x1.z; dv[7] = x1.w;
-          } else {
+      defer_complete();
+      // park this tile's sums; their update runs during the next tile
 #pragma unroll
-            for (int j = 0; j < 8; ++j) dv[j] = gc + j < P.n ? cp[j] : 0.0;
-          }
-#pragma unroll
-          for (int j = 0; j < 8; ++j) df[j] = gc + j < P.n ? P.fb[gc + j] : 0;
-        };
-        load_chunk(0, cv, fv);
+      for (int k = 0; k < 32; ++k) {
+        const unsigned long long i0 = (((unsigned long long)hi[2 * k] << 32) | lo[2 * k]) - corr;
+        const unsigned long long i1 = (((unsigned long long)hi[2 * k + 1] << 32) | lo[2 * k + 1]) - corr;
+        *reinterpret_cast<longlong2*>(scr + (size_t)k * (2 * 256)) = make_longlong2((long long)i0, (long long)i1);
+      }
+      dcrow = rok ? crow : nullptr;
+      dcol0 = col0;
+      der = rok ? P.ea[row] - (OZ_F + 2 * OZ_BITS) : 0;
+    }
+    if (ok && dcrow != nullptr) {
+      // the last tile's update
 #pragma unroll 1
-        for (int c = 0; c < 8; ++c) {
-          const int gc = col0 + 8 * c;
-          if (gc >= P.n) break;
-          if (c + 1 < 8 && gc + 8 < P.n) load_chunk(c + 1, nv, nf);
-          uint32_t tl[8], th[8];
-          switch (c) {
-#define OZ_CP(K)                                    \
-  case K:                                           \
-    _Pragma("unroll") for (int j = 0; j < 8; ++j) { \
-      tl[j] = lo[8 * K + j];                        \
-      th[j] = hi[8 * K + j];                        \
-    }                                               \
-    break;
-            OZ_CP(0) OZ_CP(1) OZ_CP(2) OZ_CP(3) OZ_CP(4) OZ_CP(5) OZ_CP(6) OZ_CP(7)
-#undef OZ_CP
-          }
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const long long I = (long long)((((unsigned long long)th[j] << 32) | tl[j]) - corr);
-            cv[j] = oz_sub(cv[j], I, er + fv[j]);
-          }
-          double* cp = crow + 8 * c;
-          if (P.vec_ok && gc + 8 <= P.n) {
-            *reinterpret_cast<double4_32a*>(cp) = make_double4_32a(cv[0], cv[1], cv[2], cv[3]);
-            *reinterpret_cast<double4_32a*>(cp + 4) = make_double4_32a(cv[4], cv[5], cv[6], cv[7]);
-          } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              if (gc + j < P.n) cp[j] = cv[j];
-          }
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            cv[j] = nv[j];
-            fv[j] = nf[j];
-          }
-        }
+      for (int k = 0; k < 32; ++k) {
+        defer_issue(k);
+        defer_complete();
       }
     }
   }
@@ -647,15 +624,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 // ------------------------------------------------------------ host side
 static size_t al1k(size_t b) { return (b + 1023) / 1024 * 1024; }
 
-size_t ozaki_ws_bytes(int m, int n, int k) {
+size_t ozaki_ws_bytes(int m, int n, int k, int sm_count) {
   const size_t kpad = (size_t)cdiv(k > 0 ? k : 1, OZ_BK) * OZ_BK;
   return al1k((size_t)OZ_S * m * kpad * 2) + al1k((size_t)OZ_S * n * kpad * 2) + al1k((size_t)m * 4) +
-         al1k((size_t)n * 4);
+         al1k((size_t)n * 4) + (size_t)sm_count * OZ_BM * OZ_BN * 8;
 }
 
 struct OzLayout {
   __nv_bfloat16 *As, *Bs;
   int *ea, *fb;
+  long long* scratch;
   int kpad;
 };
 
@@ -670,6 +648,8 @@ static OzLayout oz_layout(void* ws, int m, int n, int k) {
   L.ea = (int*)p;
   p += al1k((size_t)m * 4);
   L.fb = (int*)p;
+  p += al1k((size_t)n * 4);
+  L.scratch = (long long*)p;
   return L;
 }
 
@@ -744,8 +724,9 @@ cudaError_t ozaki_gemm(double* C, int64_t ldc, const void* ws, int m, int n, int
   P.tiles_n = (int)cdiv(ncols, OZ_BN);
   P.ea = L.ea;
   P.fb = L.fb + col0;
+  P.scratch = L.scratch;
   P.idesc = tc_idesc_mn(1u, OZ_BM, OZ_BN);
-  P.vec_ok = (((uintptr_t)C & 31u) == 0 && (ldc % 4) == 0) ? 1 : 0;
+  P.vec_ok = (((uintptr_t)C & 15u) == 0 && (ldc % 2) == 0) ? 1 : 0;
   P.status = status;
   const int ntiles = P.tiles_m * P.tiles_n;
   int grid = ntiles < dev.sm_count ? ntiles : dev.sm_count;

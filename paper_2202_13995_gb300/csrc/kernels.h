@@ -100,10 +100,11 @@ cudaError_t tc_gemm_run(int kind, float* C, int64_t ldc, const void* Aop, const 
 // FP64 C -= A B with the products on BF16 tensor cores by error-free splitting
 // (Ozaki scheme, 8 slices of 7 bits, exact integer combination).  k <= 256.
 // ozaki_split cuts A (m x k) and B (k x n), both row-major FP64, into the
-// workspace (ozaki_ws_bytes(m, n, k) bytes); ozaki_gemm then updates columns
+// workspace (ozaki_ws_bytes(m, n, k, sm_count) bytes, sm_count of the device
+// that runs it); ozaki_gemm then updates columns
 // [col0, col0 + ncols) of the m x n product into C (row-major FP64, column 0
 // of C is column col0 of the product).  Non-finite operands set ST_RANGE.
-size_t ozaki_ws_bytes(int m, int n, int k);
+size_t ozaki_ws_bytes(int m, int n, int k, int sm_count);
 cudaError_t ozaki_split(const double* A, int64_t lda, const double* B, int64_t ldb, int m, int n, int k, void* ws,
                         int* status, cudaStream_t st);
 cudaError_t ozaki_gemm(double* C, int64_t ldc, const void* ws, int m, int n, int k, int col0, int ncols, int* status,

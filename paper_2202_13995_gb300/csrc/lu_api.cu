@@ -447,7 +447,7 @@ extern "C" int lu_factor_ex(lu_ctx c, int n, const double* dA, int lda, lu_prec 
   }
   if (flags & LU_FACTOR_OZAKI) {
     f->ozaki = true;
-    if ((rc = dalloc(c, &f->oz_ws, ozaki_ws_bytes(nn, nn, f->nb)))) {
+    if ((rc = dalloc(c, &f->oz_ws, ozaki_ws_bytes(nn, nn, f->nb, c->dev.sm_count)))) {
       lu_fact_free(f);
       return rc;
     }
@@ -806,7 +806,7 @@ extern "C" int lu_step_gemm_ozaki(lu_ctx c, int m, int n, int k, double* dC, int
   if (lda < k) return -8;
   if (!dB) return -9;
   if (ldb < n) return -10;
-  int rc = ensure_step_ws(c, ozaki_ws_bytes(m, n, k));
+  int rc = ensure_step_ws(c, ozaki_ws_bytes(m, n, k, c->dev.sm_count));
   if (rc) return rc;
   CU_TRY(ozaki_split(dA, lda, dB, ldb, m, n, k, c->step_ws, c->d_status, c->stream));
   CU_TRY(ozaki_gemm(dC, ldc, c->step_ws, m, n, k, 0, n, c->d_status, c->dev, c->stream));
