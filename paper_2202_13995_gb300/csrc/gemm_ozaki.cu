@@ -736,3 +736,40 @@ cudaError_t ozaki_gemm(double* C, int64_t ldc, const void* ws, int m, int n, int
 }
 
 }  // namespace gb
+
+namespace gb {
+
+// M = I - L^-1 for the unit-lower w x w block L (row-major, ld ldl): the top
+// block solve U12 = L^-1 A12 then becomes the update A12 - M A12, which the
+// split product runs on the tensor cores.  One warp per column j of L^-1:
+// forward substitution x_i = -sum_{k=j}^{i-1} L(i,k) x_k (x_j = 1), the sum
+// split over the lanes and reduced by shuffles; M(i,j) = -x_i below the
+// diagonal, 0 on and above it.
+__global__ void __launch_bounds__(256) unit_lower_inv_comp_kernel(const double* __restrict__ L, int64_t ldl, int w,
+                                                                  double* __restrict__ M, int64_t ldm) {
+  __shared__ double xs[8][OZ_KMAX];
+  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+  const int j = blockIdx.x * 8 + wl;
+  if (j >= w) return;
+  double* x = xs[wl];
+  for (int i = lane; i < w; i += 32) x[i] = i == j ? 1.0 : 0.0;
+  __syncwarp();
+  for (int i = j + 1; i < w; ++i) {
+    double part = 0.0;
+    for (int k = j + lane; k < i; k += 32) part = fma(L[(int64_t)i * ldl + k], x[k], part);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    if (lane == 0) x[i] = -part;
+    __syncwarp();
+  }
+  for (int i = lane; i < w; i += 32) M[(int64_t)i * ldm + j] = i > j ? -x[i] : 0.0;
+}
+
+cudaError_t launch_unit_lower_inv_comp(const double* L, int64_t ldl, int w, double* M, int64_t ldm, cudaStream_t st) {
+  if (w <= 0) return cudaSuccess;
+  if (w > OZ_KMAX) return cudaErrorInvalidValue;
+  unit_lower_inv_comp_kernel<<<(unsigned)cdiv(w, 8), 256, 0, st>>>(L, ldl, w, M, ldm);
+  return cudaGetLastError();
+}
+
+}  // namespace gb

@@ -109,6 +109,9 @@ cudaError_t ozaki_split(const double* A, int64_t lda, const double* B, int64_t l
                         int* status, cudaStream_t st);
 cudaError_t ozaki_gemm(double* C, int64_t ldc, const void* ws, int m, int n, int k, int col0, int ncols, int* status,
                        const DevInfo& dev, cudaStream_t st, int max_ctas = 0);
+// M (w x w, row-major) = I - L^-1 for the unit-lower block L (w <= 256), so that
+// the top block solve L^-1 A12 is the split update A12 - M A12.
+cudaError_t launch_unit_lower_inv_comp(const double* L, int64_t ldl, int w, double* M, int64_t ldm, cudaStream_t st);
 
 // ---------------------------------------------------------------- solve.cu
 struct SolveScratch {

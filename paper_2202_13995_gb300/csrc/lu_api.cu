@@ -104,6 +104,7 @@ struct lu_fact_s {
   int kpad = 0;
   bool ozaki = false;   // FP64 trailing update by error-free splitting
   void* oz_ws = nullptr;
+  double* oz_minv = nullptr;  // nb x nb: I - L11^-1 of the current block
   void* solve_mem = nullptr;
   SolveScratch ss{};
   double* vec_ws = nullptr;  // refinement: R, D, partial sums
@@ -266,6 +267,19 @@ static int default_nb(int n, lu_prec prec) {
 static int round_up(int v, int a) { return (v + a - 1) / a * a; }
 
 // ------------------------------------------------------------------ factor
+// The top block solve U12 = L11^-1 A12 with the split update: M = I - L11^-1
+// in FP64, then A12 -= M A12 on the tensor cores (the split reads A12 before
+// the product overwrites it, so the update runs in place).
+static cudaError_t top_solve_split(lu_fact f, const double* L11, double* A12, int64_t ld, int w, int N) {
+  lu_ctx c = f->ctx;
+  cudaStream_t st = c->stream;
+  cudaError_t e = PHASE(c, PH_TRSM, 1, launch_unit_lower_inv_comp(L11, ld, w, f->oz_minv, w, st));
+  if (e != cudaSuccess) return e;
+  e = PHASE(c, PH_TRSM, 2, ozaki_split(f->oz_minv, w, A12, ld, w, N, w, f->oz_ws, c->d_status, st));
+  if (e != cudaSuccess) return e;
+  return PHASE(c, PH_TRSM, 1, ozaki_gemm(A12, ld, f->oz_ws, w, N, w, 0, N, c->d_status, c->dev, st));
+}
+
 template <typename T>
 static int factor_loop(lu_fact f) {
   lu_ctx c = f->ctx;
@@ -300,7 +314,11 @@ static int factor_loop(lu_fact f) {
     T* U12 = Wkk + w;
     T* L21 = Wkk + (int64_t)w * ld;
     T* A22 = L21 + w;
-    CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12, ld, w, rest, st)));
+    if (f->ozaki) {
+      CU_TRY(top_solve_split(f, (double*)Wkk, (double*)U12, ld, w, rest));
+    } else {
+      CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12, ld, w, rest, st)));
+    }
     const int w2 = rest < nb ? rest : nb;
     if (f->ozaki) {
       CU_TRY(PHASE(c, PH_CAST, 2, ozaki_split((const double*)L21, ld, (const double*)U12, ld, rest, rest, w,
@@ -363,7 +381,11 @@ static int factor_loop_nopiv(lu_fact f) {
     T* L21 = Wkk + (int64_t)w * ld;
     T* A22 = L21 + w;
     CU_TRY(PHASE(c, PH_PANEL, 1, launch_trsm_right_upper<T>(Wkk, L21, ld, rest, w, st)));
-    CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12, ld, w, rest, st)));
+    if (f->ozaki) {
+      CU_TRY(top_solve_split(f, (double*)Wkk, (double*)U12, ld, w, rest));
+    } else {
+      CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12, ld, w, rest, st)));
+    }
     if (f->ozaki) {
       CU_TRY(PHASE(c, PH_CAST, 2, ozaki_split((const double*)L21, ld, (const double*)U12, ld, rest, rest, w,
                                                f->oz_ws, c->d_status, st)));
@@ -389,6 +411,7 @@ extern "C" void lu_fact_free(lu_fact f) {
   dfree(c, f->panel_mem);
   dfree(c, f->aop);
   dfree(c, f->oz_ws);
+  dfree(c, f->oz_minv);
   dfree(c, f->solve_mem);
   dfree(c, f->ss.dinv);
   dfree(c, f->vec_ws);
@@ -447,7 +470,8 @@ extern "C" int lu_factor_ex(lu_ctx c, int n, const double* dA, int lda, lu_prec 
   }
   if (flags & LU_FACTOR_OZAKI) {
     f->ozaki = true;
-    if ((rc = dalloc(c, &f->oz_ws, ozaki_ws_bytes(nn, nn, f->nb, c->dev.sm_count)))) {
+    if ((rc = dalloc(c, &f->oz_ws, ozaki_ws_bytes(nn, nn, f->nb, c->dev.sm_count))) ||
+        (rc = dalloc(c, (void**)&f->oz_minv, (size_t)f->nb * f->nb * sizeof(double)))) {
       lu_fact_free(f);
       return rc;
     }
