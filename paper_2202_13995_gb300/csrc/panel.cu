@@ -285,157 +285,73 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
       } else if (warp == 1) {
         if (jg >= row0 && jg < row0 + rloc && lane < ibs) put_value<T>(rowj + lane * NV, stamp, S[lane * Rs + (jg - row0)]);
       }
-      // ---- 2. read the candidates: poll the words until each carries this
-      //      column's stamp (bounded; every retry re-issues all words still
-      //      stale, so each retry costs one round trip).  Units: per slot |a|,
-      //      row index and ibs values, then the ibs values of row jg; a
-      //      double's two words are read by the same thread.  FP32: every
-      //      slot in full at once (one round trip).  FP64 (more CTAs, twice
-      //      the words): the slot headers first, then only the pivot's row.
+      // ---- 2. read every candidate slot and row jg: poll the words until
+      //      each carries this column's stamp (bounded).  Units: per slot
+      //      |a|, row index, ibs values; then the ibs values of row jg; a
+      //      double's two words are read by the same thread.
       {
         const int upslot = 2 + ibs;
-        const unsigned long long want = (unsigned long long)stamp;
-        int ok = 1;
-        auto unit_src = [&](int kind, int c, int col) -> const unsigned long long* {
-          return kind == 3 ? rowj + col * NV
-                           : slots + (size_t)c * xw + (kind == 0 ? 0 : (kind == 1 ? NV : NV + 1 + col * NV));
-        };
-        auto unit_value = [&](unsigned long long a, unsigned long long b2) -> T {
-          if constexpr (sizeof(T) == 4) {
-            return __uint_as_float((uint32_t)a);
-          } else {
-            return __longlong_as_double((long long)(((a & 0xffffffffull) << 32) | (b2 & 0xffffffffull)));
-          }
-        };
-        // unit u of this column's exchange -> (kind, slot, column)
         const int nslotu = G * upslot;
-        auto decode = [&](int u, int& kind, int& c, int& col) {
-          if (u < nslotu) {
-            c = u / upslot;
-            const int k = u - c * upslot;
-            kind = k < 2 ? k : 2;
-            col = k - 2;
-          } else {
-            kind = 3;
-            c = 0;
-            col = u - nslotu;
-          }
-        };
-        // poll units unit(q) (q < QB, -1 = none) until all are valid; false on timeout
-        constexpr int QB = 12;
-        auto poll_batch = [&](const int* uq, unsigned long long* wa, unsigned long long* wb, int fixed_c) -> bool {
-          auto src_of = [&](int q) -> const unsigned long long* {
-            int kind, c, col;
-            decode(uq[q], kind, c, col);
-            if (fixed_c >= 0 && kind == 2) c = fixed_c;
-            return unit_src(kind, c, col);
-          };
-          auto two = [&](int q) -> bool {
-            int kind, c, col;
-            decode(uq[q], kind, c, col);
-            return NV == 2 && kind != 1;
-          };
+        const int total = nslotu + ibs;
+        const unsigned long long want = (unsigned long long)stamp;
+        constexpr int QB = 8;
+        int ok = 1;
+        for (int base = tid; base < total && ok; base += PNL_THREADS * QB) {
+          unsigned long long wa[QB], wb[QB];
+          int kind[QB], cs[QB], col[QB];
 #pragma unroll
           for (int q = 0; q < QB; ++q) {
-            wa[q] = wb[q] = want << 32;
-            if (uq[q] < 0) continue;
-            const unsigned long long* src = src_of(q);
-            wa[q] = get_word(src);
-            if (two(q)) wb[q] = get_word(src + 1);
-          }
-          const uint64_t t0 = gtimer();
-          while (true) {
-            bool all = true;
-#pragma unroll
-            for (int q = 0; q < QB; ++q)
-              if ((wa[q] >> 32) != want || (wb[q] >> 32) != want) all = false;
-            if (all) return true;
-            if (gtimer() - t0 > GB_SPIN_LIMIT_NS) return false;
-#pragma unroll
-            for (int q = 0; q < QB; ++q) {
-              if ((wa[q] >> 32) == want && (wb[q] >> 32) == want) continue;
-              const unsigned long long* src = src_of(q);
-              wa[q] = get_word(src);
-              if (two(q)) wb[q] = get_word(src + 1);
+            const int u = base + q * PNL_THREADS;
+            kind[q] = -1;
+            cs[q] = 0;
+            col[q] = 0;
+            const unsigned long long* src = nullptr;
+            if (u < nslotu) {
+              cs[q] = u / upslot;
+              const int k = u % upslot;
+              kind[q] = k < 2 ? k : 2;
+              col[q] = k - 2;
+              src = slots + (size_t)cs[q] * xw + (k == 0 ? 0 : (k == 1 ? NV : NV + 1 + (k - 2) * NV));
+            } else if (u < total) {
+              kind[q] = 3;
+              col[q] = u - nslotu;
+              src = rowj + col[q] * NV;
             }
+            wa[q] = src ? get_word(src) : (want << 32);
+            wb[q] = (src && NV == 2 && kind[q] != 1) ? get_word(src + 1) : (want << 32);
           }
-        };
-        auto store_unit = [&](int u, unsigned long long a, unsigned long long b2, int fixed_c) {
-          int kind, c, col;
-          decode(u, kind, c, col);
-          if (fixed_c >= 0 && kind == 2) c = fixed_c;
-          const T v = unit_value(a, b2);
-          switch (kind) {
-            case 0: xv[c] = v; break;
-            case 1: xi[c] = (int)(uint32_t)a; break;
-            case 2: xall[c * ib + col] = v; break;
-            default: xrj[col] = v; break;
-          }
-        };
-        if constexpr (sizeof(T) == 4) {
-          const int total = nslotu + ibs;
-          for (int base = tid; base < total && ok; base += PNL_THREADS * QB) {
-            int uq[QB];
-            unsigned long long wa[QB], wb[QB];
 #pragma unroll
-            for (int q = 0; q < QB; ++q) {
-              const int u = base + q * PNL_THREADS;
-              uq[q] = u < total ? u : -1;
+          for (int q = 0; q < QB; ++q) {
+            if (kind[q] < 0 || !ok) continue;
+            if ((wa[q] >> 32) != want || (wb[q] >> 32) != want) {
+              const int k = kind[q];
+              const unsigned long long* src =
+                  k == 3 ? rowj + col[q] * NV
+                         : slots + (size_t)cs[q] * xw + (k == 0 ? 0 : (k == 1 ? NV : NV + 1 + col[q] * NV));
+              const uint64_t t0 = gtimer();
+              while ((wa[q] >> 32) != want || (wb[q] >> 32) != want) {
+                if (gtimer() - t0 > GB_SPIN_LIMIT_NS) {
+                  atomicOr(P.status, ST_TIMEOUT);
+                  ok = 0;
+                  break;
+                }
+                wa[q] = get_word(src);
+                if (NV == 2 && k != 1) wb[q] = get_word(src + 1);
+              }
+              if (!ok) continue;
             }
-            if (!poll_batch(uq, wa, wb, -1)) {
-              ok = 0;
-              break;
+            const uint32_t pa = (uint32_t)wa[q], pb = (uint32_t)wb[q];
+            T v;
+            if constexpr (sizeof(T) == 4) {
+              v = __uint_as_float(pa);
+            } else {
+              v = __longlong_as_double((long long)(((unsigned long long)pa << 32) | pb));
             }
-#pragma unroll
-            for (int q = 0; q < QB; ++q)
-              if (uq[q] >= 0) store_unit(uq[q], wa[q], wb[q], -1);
-          }
-        } else {
-          // headers: thread c < G takes slot c (|a| and row index)
-          {
-            int uq[QB];
-            unsigned long long wa[QB], wb[QB];
-#pragma unroll
-            for (int q = 0; q < QB; ++q) uq[q] = -1;
-            if (tid < G) {
-              uq[0] = tid * upslot;
-              uq[1] = tid * upslot + 1;
-            }
-            if (!poll_batch(uq, wa, wb, -1)) ok = 0;
-            if (ok && tid < G) {
-              store_unit(uq[0], wa[0], wb[0], -1);
-              store_unit(uq[1], wa[1], wb[1], -1);
-            }
-          }
-          if (!ok) misc[3] = 0;
-          __syncthreads();
-          if (misc[3] == 0) return;
-          bv = tid < G ? xv[tid] : T(-1);
-          bi = tid < G ? xi[tid] : INT_MAX;
-          warp_argmax(bv, bi);
-          if (lane == 0) {
-            redv[warp] = bv;
-            redi[warp] = bi;
-          }
-          __syncthreads();
-          T v0 = lane < PNL_WARPS ? redv[lane] : T(-1);
-          int i0 = lane < PNL_WARPS ? redi[lane] : INT_MAX;
-          warp_argmax(v0, i0);
-          // the pivot's row (slot of the CTA that owns row i0) and row jg
-          {
-            int uq[QB];
-            unsigned long long wa[QB], wb[QB];
-#pragma unroll
-            for (int q = 0; q < QB; ++q) uq[q] = -1;
-            if (tid < ibs) {
-              uq[0] = 2 + tid;           // a value unit of slot 0, redirected to the pivot's slot
-              uq[1] = nslotu + tid;      // row jg
-            }
-            const int pc = i0 != INT_MAX ? i0 / R : 0;
-            if (!poll_batch(uq, wa, wb, pc)) ok = 0;
-            if (ok && tid < ibs) {
-              store_unit(uq[0], wa[0], wb[0], pc);
-              store_unit(uq[1], wa[1], wb[1], pc);
+            switch (kind[q]) {
+              case 0: xv[cs[q]] = v; break;
+              case 1: xi[cs[q]] = (int)pa; break;
+              case 2: xall[cs[q] * ib + col[q]] = v; break;
+              default: xrj[col[q]] = v; break;
             }
           }
         }
