@@ -25,8 +25,10 @@ cudaError_t allow_max_smem(const void* func);
 // Scratch of the cooperative panel kernel (global memory, owned by the caller).
 struct PanelScratch {
   unsigned* bar;   // 2 words: grid barrier (zeroed by the launcher)
-  unsigned long long* xs;  // stamped candidate exchange: [2][Gmax][slot words] + [2][row words]
-  size_t xs_bytes;         // (zeroed by the launcher)
+  void* xval;      // [2][Gmax] T
+  int* xidx;       // [2][Gmax]
+  void* xrow;      // [2][Gmax][ib] T
+  void* xrowj;     // [2][ib] T
   int* perm;       // 1 + 4*wmax ints: count, dst positions, src positions
   int gmax;        // capacity in CTAs
   int ibmax;

@@ -52,21 +52,14 @@ __device__ __forceinline__ T tabs(T v) {
 // One cooperative launch factors the whole panel.  CTA c owns the contiguous
 // rows [c*R, c*R + R) of the panel.  The panel is processed in sub-panels of
 // ib (<= 32) columns; a sub-panel's rows are held in shared memory, so each
-// column step costs one exchange of candidates across the grid:
+// column step costs one grid barrier:
 //   1. every CTA finds the first row of largest |a| among its rows >= j and
 //      publishes (|a|, row) and that row's sub-panel values;
-//   2. every CTA reads all G candidates;
-//   3. every CTA reduces them (largest |a|, then lowest row) to the pivot p,
-//      swaps rows j and p inside its tile where it owns them, scales its
-//      column entries below j by 1/pivot (a division, as in the definition)
-//      and applies the rank-1 update to the sub-panel columns.
-// The exchange needs no barrier: every published 64-bit word carries the
-// column's stamp (j + 1) in its high half and 32 payload bits in its low
-// half, so a reader polls the words themselves until each shows the stamp
-// (one L2 round trip after the last writer, no release fence).  A buffer
-// (two, alternating by column parity) is rewritten only after its readers are
-// done: a CTA publishes column j + 2 only after it has read every CTA's
-// column j + 1, which each CTA publishes only after it has read column j.
+//   2. grid barrier;
+//   3. every CTA reduces the G candidates (largest |a|, then lowest row) to
+//      the pivot p, swaps rows j and p inside its tile where it owns them,
+//      scales its column entries below j by 1/pivot (a division, as in the
+//      definition) and applies the rank-1 update to the sub-panel columns.
 // After a sub-panel, its interchanges are applied to the other panel columns,
 // the sub-panel's L block solves the top rows of the panel columns to its
 // right, and every CTA updates its own rows of those columns (a rank-ib GEMM).
@@ -74,9 +67,10 @@ __device__ __forceinline__ T tabs(T v) {
 constexpr int PNL_THREADS = 256;
 constexpr int PNL_WARPS = PNL_THREADS / 32;
 constexpr int PNL_IB = 32;
-// Every CTA reads all candidate rows at once (one L2 round trip); up to
-// PNL_XG CTAs.
+// After each column's barrier every CTA reads all candidate rows at once
+// (one L2 round trip); up to PNL_XG CTAs.
 constexpr int PNL_XG = 160;
+constexpr int PNL_XQ = PNL_XG * PNL_IB / PNL_THREADS;  // candidate values per thread
 constexpr int PNL_HF = 2048;  // hash buckets: rows outside the panel's top w rows
 constexpr int PNL_HS = 128;   // hash buckets: rows outside a sub-panel's top rows
 
@@ -90,44 +84,18 @@ struct PanelParams {
   int* info;
   int* status;
   unsigned* bar;
-  unsigned long long* xs;  // [2][G][xw] candidate slots, then [2][ib * NV] row j
-  int xw;                  // words per slot
+  T* xval;
+  int* xidx;
+  T* xrow;
+  T* xrowj;
   int* perm;
 };
-
-// Stamped exchange words: high 32 bits = column stamp, low 32 = payload.  A
-// float is one word, a double two (high then low half of its pattern).
-template <typename T>
-struct XWords {
-  static constexpr int n = sizeof(T) / 4;
-};
-__host__ __device__ constexpr int panel_slot_words(int ib, int nv) { return 1 + nv * (ib + 1); }
-
-__device__ __forceinline__ void put_word(unsigned long long* p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long get_word(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-template <typename T>
-__device__ __forceinline__ void put_value(unsigned long long* p, unsigned s, T v) {
-  const unsigned long long hs = (unsigned long long)s << 32;
-  if constexpr (sizeof(T) == 4) {
-    put_word(p, hs | __float_as_uint(v));
-  } else {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    put_word(p, hs | (b >> 32));
-    put_word(p + 1, hs | (b & 0xffffffffull));
-  }
-}
 
 __host__ __device__ inline size_t panel_smem_bytes(int R, int ib, int w, int tsize) {
   const int Rs = R | 1;
   size_t tcount = (size_t)ib * Rs + (size_t)ib * ib + (size_t)ib * 32 + 2 * (size_t)ib * 32 + PNL_WARPS +
-                  (size_t)PNL_XG * ib + PNL_XG + ib;
-  size_t icount = PNL_WARPS + 4 * (size_t)w + 4 * (size_t)ib + 2 * PNL_HF + 2 * PNL_HS + 8 + PNL_XG + 8;
+                  (size_t)PNL_XG * ib;
+  size_t icount = PNL_WARPS + 4 * (size_t)w + 4 * (size_t)ib + 2 * PNL_HF + 2 * PNL_HS + 8;
   return tcount * tsize + icount * sizeof(int) + 16;
 }
 
@@ -208,9 +176,7 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
   T* stage = Ust + ib * 32;               // [2*ib][32] interchange staging
   T* xall = stage + 2 * ib * 32;          // [PNL_XG][ib] all candidate rows
   T* redv = xall + PNL_XG * ib;           // [PNL_WARPS]
-  T* xv = redv + PNL_WARPS;               // [PNL_XG] candidate |a|
-  T* xrj = xv + PNL_XG;                   // [ib] row j of the sub-panel
-  int* redi = reinterpret_cast<int*>(xrj + ib);
+  int* redi = reinterpret_cast<int*>(redv + PNL_WARPS);
   int* fpos = redi + PNL_WARPS;  // [2w] whole-panel permutation record
   int* fcur = fpos + 2 * w;
   int* spos = fcur + 2 * w;      // [2ib] sub-panel permutation record
@@ -219,21 +185,15 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
   int* hfv = hfk + PNL_HF;
   int* hsk = hfv + PNL_HF;       // [PNL_HS]
   int* hsv = hsk + PNL_HS;
-  int* misc = hsv + PNL_HS;      // 0: fcnt 1: scnt 2: barrier flag 3: exchange flag
-  int* xi = misc + 8;            // [PNL_XG] candidate rows
+  int* misc = hsv + PNL_HS;      // 0: fcnt 1: scnt 2: barrier flag
   unsigned nbar = 0;
-  constexpr int NV = XWords<T>::n;
-  const int xw = P.xw;
 
   for (int s = tid; s < w; s += PNL_THREADS) {
     fpos[s] = s;
     fcur[s] = s;
   }
   for (int s = tid; s < PNL_HF; s += PNL_THREADS) hfk[s] = -1;
-  if (tid == 0) {
-    misc[0] = w;
-    misc[3] = 1;
-  }
+  if (tid == 0) misc[0] = w;
   const PermRec fperm{fpos, fcur, hfk, hfv, PNL_HF - 1, 0, w, &misc[0]};
   __syncthreads();
 
@@ -262,9 +222,6 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
       const int par = jg & 1;
       // ---- 1. this CTA's candidate: first row of largest |a| in column j
       //      among its rows >= jg; publish it with its sub-panel values
-      const unsigned stamp = (unsigned)jg + 1u;
-      unsigned long long* slots = P.xs + (size_t)par * G * xw;
-      unsigned long long* rowj = P.xs + (size_t)2 * G * xw + (size_t)par * ib * NV;
       if (bv != bv) atomicOr(P.status, ST_RANGE);
       warp_argmax(bv, bi);
       if (lane == 0) {
@@ -276,95 +233,34 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
         T v = lane < PNL_WARPS ? redv[lane] : T(-1);
         int i = lane < PNL_WARPS ? redi[lane] : INT_MAX;
         warp_argmax(v, i);
-        unsigned long long* my = slots + (size_t)cta * xw;
         if (lane == 0) {
-          put_value<T>(my, stamp, v);
-          put_word(my + NV, ((unsigned long long)stamp << 32) | (unsigned)i);
+          P.xval[par * G + cta] = v;
+          P.xidx[par * G + cta] = i;
         }
-        if (lane < ibs) put_value<T>(my + NV + 1 + lane * NV, stamp, i != INT_MAX ? S[lane * Rs + (i - row0)] : T(0));
+        if (i != INT_MAX && lane < ibs) P.xrow[((int64_t)par * G + cta) * ib + lane] = S[lane * Rs + (i - row0)];
       } else if (warp == 1) {
-        if (jg >= row0 && jg < row0 + rloc && lane < ibs) put_value<T>(rowj + lane * NV, stamp, S[lane * Rs + (jg - row0)]);
+        if (jg >= row0 && jg < row0 + rloc && lane < ibs) P.xrowj[par * ib + lane] = S[lane * Rs + (jg - row0)];
       }
-      // ---- 2. read every candidate slot and row jg: poll the words until
-      //      each carries this column's stamp (bounded).  Units: per slot
-      //      |a|, row index, ibs values; then the ibs values of row jg; a
-      //      double's two words are read by the same thread.
-      {
-        const int upslot = 2 + ibs;
-        const int nslotu = G * upslot;
-        const int total = nslotu + ibs;
-        const unsigned long long want = (unsigned long long)stamp;
-        constexpr int QB = 8;
-        int ok = 1;
-        for (int base = tid; base < total && ok; base += PNL_THREADS * QB) {
-          unsigned long long wa[QB], wb[QB];
-          int kind[QB], cs[QB], col[QB];
+      // ---- 2. exchange
+      if (!grid_sync_mono(P.bar, (++nbar) * (unsigned)G, P.status, &misc[2])) return;
+      // ---- 3. every candidate row, (|a|, row) pair and row jg in one round
+      T xq[PNL_XQ];
 #pragma unroll
-          for (int q = 0; q < QB; ++q) {
-            const int u = base + q * PNL_THREADS;
-            kind[q] = -1;
-            cs[q] = 0;
-            col[q] = 0;
-            const unsigned long long* src = nullptr;
-            if (u < nslotu) {
-              cs[q] = u / upslot;
-              const int k = u % upslot;
-              kind[q] = k < 2 ? k : 2;
-              col[q] = k - 2;
-              src = slots + (size_t)cs[q] * xw + (k == 0 ? 0 : (k == 1 ? NV : NV + 1 + (k - 2) * NV));
-            } else if (u < total) {
-              kind[q] = 3;
-              col[q] = u - nslotu;
-              src = rowj + col[q] * NV;
-            }
-            wa[q] = src ? get_word(src) : (want << 32);
-            wb[q] = (src && NV == 2 && kind[q] != 1) ? get_word(src + 1) : (want << 32);
-          }
-#pragma unroll
-          for (int q = 0; q < QB; ++q) {
-            if (kind[q] < 0 || !ok) continue;
-            if ((wa[q] >> 32) != want || (wb[q] >> 32) != want) {
-              const int k = kind[q];
-              const unsigned long long* src =
-                  k == 3 ? rowj + col[q] * NV
-                         : slots + (size_t)cs[q] * xw + (k == 0 ? 0 : (k == 1 ? NV : NV + 1 + col[q] * NV));
-              const uint64_t t0 = gtimer();
-              while ((wa[q] >> 32) != want || (wb[q] >> 32) != want) {
-                if (gtimer() - t0 > GB_SPIN_LIMIT_NS) {
-                  atomicOr(P.status, ST_TIMEOUT);
-                  ok = 0;
-                  break;
-                }
-                wa[q] = get_word(src);
-                if (NV == 2 && k != 1) wb[q] = get_word(src + 1);
-              }
-              if (!ok) continue;
-            }
-            const uint32_t pa = (uint32_t)wa[q], pb = (uint32_t)wb[q];
-            T v;
-            if constexpr (sizeof(T) == 4) {
-              v = __uint_as_float(pa);
-            } else {
-              v = __longlong_as_double((long long)(((unsigned long long)pa << 32) | pb));
-            }
-            switch (kind[q]) {
-              case 0: xv[cs[q]] = v; break;
-              case 1: xi[cs[q]] = (int)pa; break;
-              case 2: xall[cs[q] * ib + col[q]] = v; break;
-              default: xrj[col[q]] = v; break;
-            }
-          }
-        }
-        if (!ok) misc[3] = 0;
+      for (int q = 0; q < PNL_XQ; ++q) {
+        const int e = tid + q * PNL_THREADS;
+        xq[q] = e < G * ib ? __ldcg(P.xrow + (int64_t)par * G * ib + e) : T(0);
       }
-      __syncthreads();
-      if (misc[3] == 0) return;
-      const T rjq = tid < ibs ? xrj[tid] : T(0);
+      const T rjq = tid < ibs ? __ldcg(P.xrowj + par * ib + tid) : T(0);
       bv = T(-1);
       bi = INT_MAX;
       if (tid < G) {
-        bv = xv[tid];
-        bi = xi[tid];
+        bv = __ldcg(P.xval + par * G + tid);
+        bi = __ldcg(P.xidx + par * G + tid);
+      }
+#pragma unroll
+      for (int q = 0; q < PNL_XQ; ++q) {
+        const int e = tid + q * PNL_THREADS;
+        if (e < G * ib) xall[e] = xq[q];
       }
       warp_argmax(bv, bi);
       if (lane == 0) {
@@ -488,23 +384,29 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
 }
 
 size_t panel_scratch_bytes(int gmax, int ibmax, int wmax, int tsize) {
-  const int nv = tsize / 4;
-  size_t b = 64;                                                                   // barrier
-  b += ((size_t)2 * gmax * panel_slot_words(ibmax, nv) + 2 * (size_t)ibmax * nv) * 8 + 256;  // exchange
-  b += (1 + 4 * (size_t)wmax) * sizeof(int) + 256;                                  // perm
+  size_t b = 64;                                   // barrier
+  b += 2 * (size_t)gmax * tsize + 256;             // xval
+  b += 2 * (size_t)gmax * sizeof(int) + 256;       // xidx
+  b += 2 * (size_t)gmax * ibmax * tsize + 256;     // xrow
+  b += 2 * (size_t)ibmax * tsize + 256;            // xrowj
+  b += (1 + 4 * (size_t)wmax) * sizeof(int) + 256; // perm
   return b;
 }
 
 static inline char* align_up(char* p, size_t a) { return (char*)(((uintptr_t)p + a - 1) / a * a); }
 
 void panel_scratch_carve(PanelScratch* s, void* base, int gmax, int ibmax, int wmax, int tsize) {
-  const int nv = tsize / 4;
   char* p = (char*)base;
   s->bar = (unsigned*)p;
   p += 64;
-  s->xs = (unsigned long long*)p;
-  s->xs_bytes = ((size_t)2 * gmax * panel_slot_words(ibmax, nv) + 2 * (size_t)ibmax * nv) * 8;
-  p = align_up(p + s->xs_bytes, 256);
+  s->xval = p;
+  p = align_up(p + 2 * (size_t)gmax * tsize, 256);
+  s->xidx = (int*)p;
+  p = align_up(p + 2 * (size_t)gmax * sizeof(int), 256);
+  s->xrow = p;
+  p = align_up(p + 2 * (size_t)gmax * ibmax * tsize, 256);
+  s->xrowj = p;
+  p = align_up(p + 2 * (size_t)ibmax * tsize, 256);
   s->perm = (int*)p;
   s->gmax = gmax;
   s->ibmax = ibmax;
@@ -552,12 +454,7 @@ cudaError_t launch_panel(T* Wkk, int64_t ldw, int m, int w, int kabs, int* ipiv,
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PNL_THREADS, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1 || G > per_sm * dev.sm_count || G > s.gmax) return cudaErrorCooperativeLaunchTooLarge;
-  // the barrier counter and the exchange words (stamps start from zero); the
-  // exchange follows the barrier in the scratch, so one memset covers both
-  const int xw = panel_slot_words(ib, XWords<T>::n);
-  const size_t xbytes = ((size_t)2 * G * xw + 2 * (size_t)ib * XWords<T>::n) * 8;
-  if (xbytes > s.xs_bytes) return cudaErrorInvalidValue;
-  e = cudaMemsetAsync(s.bar, 0, (size_t)((char*)s.xs - (char*)s.bar) + xbytes, st);
+  e = cudaMemsetAsync(s.bar, 0, 2 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   PanelParams<T> P;
   P.A = Wkk;
@@ -572,8 +469,10 @@ cudaError_t launch_panel(T* Wkk, int64_t ldw, int m, int w, int kabs, int* ipiv,
   P.info = info;
   P.status = status;
   P.bar = s.bar;
-  P.xs = s.xs;
-  P.xw = xw;
+  P.xval = (T*)s.xval;
+  P.xidx = s.xidx;
+  P.xrow = (T*)s.xrow;
+  P.xrowj = (T*)s.xrowj;
   P.perm = s.perm;
   void* args[] = {&P};
   // A cooperative launch is refused (without side effects) while other
