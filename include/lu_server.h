@@ -20,14 +20,24 @@
  * that finds no room retries (bounded).  The environment variable
  * GB300LU_SERVER_SERIAL_FACTOR runs factorizations one at a time instead.
  *
+ * Small requests (n <= 512 and nrhs <= 8) go to a batch slot instead: it
+ * takes every queued small request at once (up to 4096), solves them in one
+ * persistent launch of the batched solver (lu_batched.h: FP32 factor + FP64
+ * refinement to scaled residual < 16, whatever the server's factor precision)
+ * and reports them with slot = max_slots.  Its working memory is counted in
+ * the budget while it runs.  Small requests never leave a factor resident and
+ * never use one (refactoring them in the batch costs less than any reuse).
+ *
  * Resident factors: a request with keep_factor != 0 leaves its factor resident
  * under factor_key (counted in the budget).  A later request with the same
  * key and use_resident != 0 skips the factorization; if the factor was evicted
  * it is factored again and the result says so.
  *
- * Determinism: a request's kernels and launch shapes depend only on the
- * request (n, nrhs, precision), so its result has the same bits whether it
- * runs alone or among others.
+ * Determinism: a request's route (worker slot or batch slot), kernels and
+ * launch shapes depend only on the request (n, nrhs, precision), and the
+ * batched solver computes each system in one CTA independently of the rest of
+ * its batch, so a result has the same bits whether it runs alone or among
+ * others.
  *
  * Thread safety: every lu_server_* call may come from any host thread.
  * Buffers: the caller owns A, B and X (device, column-major FP64) and keeps
@@ -67,7 +77,7 @@ typedef struct {
   double scaled_resid;    /* largest final HPL scaled residual */
   int reused_factor;      /* 1 if a resident factor was used */
   int refactored;         /* 1 if a requested resident factor had been evicted */
-  int slot;               /* slot that ran it */
+  int slot;               /* worker slot that ran it (max_slots: the batch slot) */
   uint64_t t_submit_ns, t_start_ns, t_done_ns; /* CLOCK_MONOTONIC */
 } lu_result;
 

@@ -632,6 +632,17 @@ extern "C" int lu_batch_run(lu_batch b, int* dInfo, int* dIters, double* dResid)
   return LU_OK;
 }
 
+// Device bytes a plan of `count` systems (largest n = nmax) allocates, for a
+// caller that budgets memory (the solve server): descriptors, order, queue
+// counter and the per-CTA working copies at the largest launch shape.
+size_t gb_batch_bytes(int count, int nmax, int sm_count) {
+  const int ldmax = (nmax + 3) & ~3;
+  const int64_t slot_floats = ((int64_t)nmax * ldmax + 63) / 64 * 64;
+  const size_t desc_bytes = ((sizeof(BatchDesc) * std::max(count, 1) + 255) / 256) * 256;
+  const size_t order_bytes = ((sizeof(int) * std::max(count, 1) + 255) / 256) * 256;
+  return desc_bytes + order_bytes + 256 + sizeof(float) * (size_t)slot_floats * (size_t)sm_count * 2;
+}
+
 extern "C" int lu_solve_batched(lu_ctx ctx, int count, const int* n, const int* nrhs, const double* const* dA,
                                 const int* lda, double* const* dB, const int* ldb, lu_prec prec, int* dInfo) {
   lu_batch b = nullptr;

@@ -1,7 +1,9 @@
 // Serving loop for dense solves: worker slots with their own contexts and
 // streams (continuous batching), admission by an HBM budget, resident
-// factors with LRU eviction.  Host C++ only; every GPU step goes through the
-// library's own entry points (lu_factor, lu_refine).
+// factors with LRU eviction, and a batch slot that solves the small requests
+// of the queue together in one persistent launch.  Host C++ only; every GPU
+// step goes through the library's own entry points (lu_factor, lu_refine,
+// lu_batch_*).
 #include <time.h>
 
 #include <algorithm>
@@ -19,10 +21,12 @@
 
 #include "kernels.h"
 #include "lu.h"
+#include "lu_batched.h"
 #include "lu_server.h"
 
 size_t gb_fact_bytes(int n, int nrhs, lu_prec prec, int nb, int sm_count);
 void gb_fact_rebind(lu_fact f, lu_ctx c);
+size_t gb_batch_bytes(int count, int nmax, int sm_count);
 
 namespace {
 
@@ -46,6 +50,12 @@ struct Resident {
   std::list<uint64_t>::iterator lru;
 };
 
+// Requests the batch slot takes: the batched kernel's limits.  The route
+// depends on the request's shape only, so a request takes the same path (and
+// gives the same bits) alone and in any mix.
+constexpr int SMALL_NMAX = 512, SMALL_RHSMAX = 8, BATCH_MAX = 4096;
+bool is_small(const lu_request& r) { return r.n <= SMALL_NMAX && r.nrhs <= SMALL_RHSMAX; }
+
 }  // namespace
 
 struct lu_server_s {
@@ -57,6 +67,7 @@ struct lu_server_s {
   std::condition_variable cv_work;  // slots wait for work / memory
   std::condition_variable cv_done;  // waiters wait for results
   std::deque<Job> queue;
+  std::deque<Job> small;  // requests for the batch slot
   std::unordered_map<uint64_t, lu_result> results;
   std::unordered_map<uint64_t, Resident> resident;  // key -> factor
   std::list<uint64_t> lru;                          // front = least recently used
@@ -66,6 +77,11 @@ struct lu_server_s {
   uint64_t evictions = 0;
   bool stopping = false;
   std::vector<std::thread> slots;
+  std::thread batch_slot;
+  int batch_state = 0;  // 0 starting, 1 running, -1 unavailable (small requests use the worker slots)
+  lu_ctx batch_ctx = nullptr;
+  cudaStream_t batch_stream = nullptr;
+  int max_slots = 0;
   std::vector<lu_ctx> ctxs;            // per slot; destroyed after the resident factors
   std::vector<cudaStream_t> streams;
   // Optionally one factorization at a time (GB300LU_SERVER_SERIAL_FACTOR):
@@ -217,6 +233,135 @@ static void slot_main(lu_server s, int slot) {
   lk.unlock();
 }
 
+// The batch slot: takes every queued small request at once (up to
+// BATCH_MAX), plans them as one batch (FP32 factor + FP64 refinement to scaled
+// residual < 16, one persistent launch), runs it and publishes the results.
+static void batch_main(lu_server s) {
+  cudaSetDevice(s->device);
+  cudaStream_t st = nullptr;
+  lu_ctx ctx = nullptr;
+  int* h_info = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || lu_create(&ctx, st) != LU_OK ||
+      cudaMallocHost(&h_info, (size_t)BATCH_MAX * 16) != cudaSuccess) {
+    // without a batch slot the small requests go to the worker slots
+    if (ctx) lu_destroy(ctx);
+    if (st) cudaStreamDestroy(st);
+    if (h_info) cudaFreeHost(h_info);
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->batch_state = -1;
+    s->cv_done.notify_all();
+    return;
+  }
+  int* h_iters = h_info + BATCH_MAX;
+  double* h_resid = reinterpret_cast<double*>(h_info + 2 * BATCH_MAX);
+  std::unique_lock<std::mutex> lk(s->mu);
+  s->batch_ctx = ctx;
+  s->batch_stream = st;
+  s->batch_state = 1;
+  s->cv_done.notify_all();
+  while (true) {
+    if (s->small.empty()) {
+      if (s->stopping) break;
+      s->cv_work.wait(lk);
+      continue;
+    }
+    // the oldest small requests whose batch fits the budget alone (halved
+    // until it does; a single request that cannot fit was refused at submit)
+    int count = (int)std::min<size_t>(s->small.size(), BATCH_MAX);
+    int nmax = 1;
+    size_t need = 0;
+    while (true) {
+      nmax = 1;
+      for (int i = 0; i < count; ++i) nmax = std::max(nmax, s->small[i].req.n);
+      need = gb_batch_bytes(count, nmax, s->sm_count) + (size_t)count * 16 + 1024;
+      if (need <= s->budget || count == 1) break;
+      count = (count + 1) / 2;
+    }
+    std::vector<lu_fact> freed;
+    if (!make_room(s, need, freed)) {
+      if (!freed.empty()) {
+        lk.unlock();
+        for (lu_fact f : freed) lu_fact_free(f);
+        lk.lock();
+      }
+      s->cv_work.wait(lk);  // memory comes back as other requests finish
+      continue;
+    }
+    std::vector<Job> jobs(s->small.begin(), s->small.begin() + count);
+    s->small.erase(s->small.begin(), s->small.begin() + count);
+    s->in_use += need;
+    lk.unlock();
+    for (lu_fact f : freed) lu_fact_free(f);
+
+    const uint64_t t0 = now_ns();
+    std::vector<int> n(count), k(count), lda(count), ldb(count), ldx(count);
+    std::vector<const double*> A(count), B(count);
+    std::vector<double*> X(count);
+    for (int i = 0; i < count; ++i) {
+      const lu_request& r = jobs[i].req;
+      n[i] = r.n;
+      k[i] = r.nrhs;
+      A[i] = r.dA;
+      lda[i] = r.lda;
+      B[i] = r.dB;
+      ldb[i] = r.ldb;
+      X[i] = r.dX;
+      ldx[i] = r.ldx;
+    }
+    int rc = LU_OK;
+    int* d_out = nullptr;
+    if (cudaMallocAsync((void**)&d_out, (size_t)count * 16, st) != cudaSuccess) {
+      cudaGetLastError();
+      rc = LU_ENOMEM;
+    }
+    int* d_info = d_out;
+    int* d_iters = d_out ? d_out + count : nullptr;
+    double* d_resid = d_out ? reinterpret_cast<double*>(d_out + 2 * count) : nullptr;
+    lu_batch b = nullptr;
+    if (rc == LU_OK)
+      rc = lu_batch_create(ctx, count, n.data(), k.data(), A.data(), lda.data(), B.data(), ldb.data(), X.data(),
+                           ldx.data(), LU_F32, 16.0, 50, 0, &b);
+    if (rc == LU_OK) rc = lu_batch_run(b, d_info, d_iters, d_resid);
+    if (rc == LU_OK &&
+        (cudaMemcpyAsync(h_info, d_info, (size_t)count * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+         cudaMemcpyAsync(h_iters, d_iters, (size_t)count * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+         cudaMemcpyAsync(h_resid, d_resid, (size_t)count * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess))
+      rc = LU_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == LU_OK) rc = LU_ECUDA;
+    if (b) lu_batch_free(b);
+    if (d_out) cudaFreeAsync(d_out, st);
+    cudaStreamSynchronize(st);
+    const uint64_t t1 = now_ns();
+
+    lk.lock();
+    s->in_use -= need;
+    for (int i = 0; i < count; ++i) {
+      lu_result res;
+      memset(&res, 0, sizeof(res));
+      res.slot = s->max_slots;  // the batch slot
+      res.t_submit_ns = jobs[i].t_submit;
+      res.t_start_ns = t0;
+      res.t_done_ns = t1;
+      if (rc != LU_OK) {
+        res.status = rc;
+      } else {
+        const int info = h_info[i];
+        res.status = info == 0 ? LU_OK : info > 0 ? LU_ESINGULAR : info == -1 ? LU_ENOTCONV : LU_ETIMEOUT;
+        res.iters = h_iters[i];
+        res.scaled_resid = h_resid[i];
+      }
+      s->results[jobs[i].ticket] = res;
+    }
+    s->done += count;
+    lk.unlock();
+    s->cv_done.notify_all();
+    s->cv_work.notify_all();
+    lk.lock();
+  }
+  lk.unlock();
+  cudaFreeHost(h_info);
+}
+
 extern "C" int lu_server_create(lu_server* out, size_t hbm_budget_bytes, lu_prec prec, int max_slots) {
   if (!out) return -1;
   *out = nullptr;
@@ -233,9 +378,16 @@ extern "C" int lu_server_create(lu_server* out, size_t hbm_budget_bytes, lu_prec
   s->prec = prec;
   s->budget = hbm_budget_bytes;
   s->serialize_factor = getenv("GB300LU_SERVER_SERIAL_FACTOR") != nullptr;
+  s->max_slots = max_slots;
   s->ctxs.assign(max_slots, nullptr);
   s->streams.assign(max_slots, nullptr);
   for (int i = 0; i < max_slots; ++i) s->slots.emplace_back(slot_main, s, i);
+  s->batch_slot = std::thread(batch_main, s);
+  {
+    // routing must not depend on timing: wait until the batch slot is up (or known unavailable)
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->cv_done.wait(lk, [&] { return s->batch_state != 0; });
+  }
   *out = s;
   return LU_OK;
 }
@@ -250,17 +402,21 @@ extern "C" int lu_server_submit(lu_server s, const lu_request* req, uint64_t* ti
     return -2;
   Job j;
   j.req = r;
-  j.bytes = request_bytes(s, r);
   j.t_submit = now_ns();
-  if (j.bytes > s->budget) return LU_ENOMEM;
   {
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->stopping) return LU_EINTERNAL;
+    const bool small = is_small(r) && s->batch_state == 1;
+    j.bytes = small ? gb_batch_bytes(1, r.n, s->sm_count) + 1024 + 16 : request_bytes(s, r);
+    if (j.bytes > s->budget) return LU_ENOMEM;
     j.ticket = s->next_ticket++;
     *ticket = j.ticket;
-    s->queue.push_back(j);
+    if (small)
+      s->small.push_back(j);
+    else
+      s->queue.push_back(j);
   }
-  s->cv_work.notify_one();
+  s->cv_work.notify_all();
   return LU_OK;
 }
 
@@ -303,7 +459,10 @@ extern "C" int lu_server_destroy(lu_server s) {
   }
   s->cv_work.notify_all();
   for (auto& t : s->slots) t.join();
+  if (s->batch_slot.joinable()) s->batch_slot.join();
   for (auto& kv : s->resident) lu_fact_free(kv.second.f);
+  if (s->batch_ctx) lu_destroy(s->batch_ctx);
+  if (s->batch_stream) cudaStreamDestroy(s->batch_stream);
   for (size_t i = 0; i < s->ctxs.size(); ++i) {
     if (s->ctxs[i]) lu_destroy(s->ctxs[i]);
     if (s->streams[i]) cudaStreamDestroy(s->streams[i]);

@@ -108,3 +108,30 @@ def test_budget_rejects_oversized_request():
         srv.submit(_dev(A), _dev(B), lu.colmajor_empty(n, 1))
     assert e.value.code == lu.LU_ENOMEM
     srv.close()
+
+
+def test_small_requests_take_the_batch_slot():
+    """n <= 512 and nrhs <= 8: solved together by the batched solver (slot =
+    max_slots), correct against the oracle, same bits alone and in a mix, and
+    never resident."""
+    from paper_2202_13995_gb300 import lu
+    sizes = [(32, 1), (100, 8), (257, 3), (512, 2), (513, 1), (64, 9), (400, 5)]
+    reqs = [_req(n, k, 900 + i) for i, (n, k) in enumerate(sizes)]
+    alone = lu.Server(8 * GB, "fp16", max_slots=2)
+    r0, x0 = _solve_one(alone, *reqs[2])
+    assert r0.status == 0 and r0.slot == 2
+    alone.close()
+    srv = lu.Server(8 * GB, "fp16", max_slots=2)
+    dev = [(_dev(A), _dev(B), lu.colmajor_empty(B.shape[0], B.shape[1])) for A, B in reqs]
+    tickets = [srv.submit(Ad, Bd, X, factor_key=10 + i, keep_factor=True) for i, (Ad, Bd, X) in enumerate(dev)]
+    res = [srv.wait(t) for t in tickets]
+    for (n, k), (A, B), (Ad, Bd, X), r in zip(sizes, reqs, dev, res):
+        assert r.status == 0 and r.scaled_resid < 16.0
+        small = n <= 512 and k <= 8
+        assert (r.slot == 2) == small, (n, k, r.slot)
+        xo, _, _, _ = O.solve(A, B)
+        assert np.abs(X.cpu().numpy() - xo).max() / np.abs(xo).max() <= 1e-10
+    assert np.array_equal(dev[2][2].cpu().numpy(), x0)
+    # only the two large requests left factors resident
+    assert srv.stats()["resident"] == 2
+    srv.close()
