@@ -50,6 +50,16 @@ template <typename T>
 cudaError_t launch_panel(T* Wkk, int64_t ldw, int m, int w, int kabs, int* ipiv, int* info, int* status,
                          const PanelScratch& s, const DevInfo& dev, cudaStream_t st);
 
+// The FP32 panel on one thread-block cluster (panel_cluster.cu): same
+// arguments and outputs as launch_panel; used by launch_panel<float> when
+// panel_cluster_available(m, w).  panel_cluster_size gives its CTA count.
+int panel_cluster_size(int m, int w);
+bool panel_cluster_available(int m, int w);
+cudaError_t launch_panel_cluster(float* Wkk, int64_t ldw, int m, int w, int kabs, int* ipiv, int* info, int* status,
+                                 int* perm, cudaStream_t st);
+// SMs one panel launch occupies (for the lookahead's trailing-update cap).
+int panel_sm_use(int m, int w, int tsize, const DevInfo& dev, const PanelScratch& s);
+
 // Apply the panel permutation in scratch.perm (positions relative to row k) to
 // columns [0, k) and [k + w, n) of W, and to the row-index vector rowid.
 template <typename T>

@@ -350,7 +350,7 @@ static int factor_loop(lu_fact f) {
     panel_ready = true;
     // the rest of the trailing matrix on the SMs the panel leaves free (the
     // latency-bound panel runs slower on SMs it shares with the update)
-    const int gp = panel_grid_size(rest, w2, sizeof(T), c->dev, f->ps.gmax);
+    const int gp = panel_sm_use(rest, w2, sizeof(T), c->dev, f->ps);
     const int cap = c->dev.sm_count - (gp > 0 ? gp : 0);
     const void* bop2 = (const char*)f->bop + (size_t)w2 * f->kpad * 2;
     CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)(A22 + w2), ld, f->aop, bop2, rest, rest - w2, f->kpad,

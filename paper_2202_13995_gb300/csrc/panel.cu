@@ -20,6 +20,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "permrec.cuh"
 
 namespace gb {
 
@@ -98,43 +99,6 @@ __host__ __device__ inline size_t panel_smem_bytes(int R, int ib, int w, int tsi
   size_t icount = PNL_WARPS + 4 * (size_t)w + 4 * (size_t)ib + 2 * PNL_HF + 2 * PNL_HS + 8;
   return tcount * tsize + icount * sizeof(int) + 16;
 }
-
-// Row-permutation record: slot s holds position pos[s] and the original
-// position cur[s] of the row that now sits there.  Positions [base, lim) use
-// slots [0, lim - base) directly; other positions are found through an
-// open-addressing hash (key = position, value = slot).  One thread only.
-struct PermRec {
-  int* pos;
-  int* cur;
-  int* hkey;
-  int* hval;
-  int mask;
-  int base, lim;
-  int* cnt;
-  __device__ __forceinline__ int slot(int p) const {
-    if (p < lim) return p - base;
-    unsigned b = ((unsigned)p * 2654435761u) & (unsigned)mask;
-    while (true) {
-      const int k = hkey[b];
-      if (k == p) return hval[b];
-      if (k < 0) {
-        const int s = (*cnt)++;
-        hkey[b] = p;
-        hval[b] = s;
-        pos[s] = p;
-        cur[s] = p;
-        return s;
-      }
-      b = (b + 1) & (unsigned)mask;
-    }
-  }
-  __device__ __forceinline__ void swap_rows(int a, int p) const {  // positions a (direct) and p
-    const int sa = slot(a), sb = slot(p);
-    const int t = cur[sa];
-    cur[sa] = cur[sb];
-    cur[sb] = t;
-  }
-};
 
 // Grid barrier on a monotonic arrival counter (zeroed by the launcher): the
 // k-th barrier waits until the counter reaches k * G.  Arrival is a release
@@ -436,10 +400,25 @@ int panel_grid_size(int m, int w, int tsize, const DevInfo& dev, int gmax, int g
   return (int)cdiv(m, R);
 }
 
+// FP32 panels use the cluster kernel when it fits (and GB300LU_PANEL_COOP is
+// not set); everything else uses the cooperative grid kernel.
+static bool use_cluster_panel(int m, int w, int tsize) {
+  static const bool coop = getenv("GB300LU_PANEL_COOP") != nullptr;
+  return tsize == 4 && !coop && panel_cluster_available(m, w);
+}
+
+int panel_sm_use(int m, int w, int tsize, const DevInfo& dev, const PanelScratch& s) {
+  if (use_cluster_panel(m, w, tsize)) return panel_cluster_size(m, w);
+  return panel_grid_size(m, w, tsize, dev, s.gmax, s.gtarget);
+}
+
 template <typename T>
 cudaError_t launch_panel(T* Wkk, int64_t ldw, int m, int w, int kabs, int* ipiv, int* info, int* status,
                          const PanelScratch& s, const DevInfo& dev, cudaStream_t st) {
   if (w <= 0 || m < w || w > s.wmax) return cudaErrorInvalidValue;
+  if constexpr (sizeof(T) == 4) {
+    if (use_cluster_panel(m, w, 4)) return launch_panel_cluster(Wkk, ldw, m, w, kabs, ipiv, info, status, s.perm, st);
+  }
   if (s.gmax > PNL_XG) return cudaErrorInvalidValue;  // every candidate row fits the exchange buffer
   const int ib = PNL_IB < s.ibmax ? PNL_IB : s.ibmax;
   const int G0 = panel_grid_size(m, w, sizeof(T), dev, s.gmax, s.gtarget);
