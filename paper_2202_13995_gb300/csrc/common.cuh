@@ -114,6 +114,15 @@ __device__ __forceinline__ void argmax_merge(T& v, int& i, T v2, int i2) {
   }
 }
 
+// Pivot-search magnitude |x|, with NaN as +infinity: a NaN entry is then
+// chosen as a pivot (and the non-finite pivot reported) instead of never
+// comparing and leaving a column without a candidate row.
+template <typename T>
+__device__ __forceinline__ T pivot_mag(T x) {
+  const T a = x < T(0) ? -x : x;
+  return a == a ? a : T(INFINITY);
+}
+
 template <typename T>
 __device__ __forceinline__ void warp_argmax(T& v, int& i) {
 #pragma unroll

@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
     int bi = INT_MAX;
     for (int r = tid; r < rloc; r += PNL_THREADS) {
       const int gi = row0 + r;
-      if (gi >= j0) argmax_merge(bv, bi, tabs(S[r]), gi);
+      if (gi >= j0) argmax_merge(bv, bi, pivot_mag(S[r]), gi);
     }
 
     for (int j = 0; j < ibs; ++j) {
@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
       const int par = jg & 1;
       // ---- 1. this CTA's candidate: first row of largest |a| in column j
       //      among its rows >= jg; publish it with its sub-panel values
-      if (bv != bv) atomicOr(P.status, ST_RANGE);
+      if (!(bv < T(INFINITY))) atomicOr(P.status, ST_RANGE);  // a non-finite candidate
       warp_argmax(bv, bi);
       if (lane == 0) {
         redv[warp] = bv;
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
           if (piv != T(0)) l = l / piv;
           S[j * Rs + r] = l;
           for (int c = j + 1; c < ibs; ++c) S[c * Rs + r] -= l * prow[c];
-          if (j + 1 < ibs) argmax_merge(bv, bi, tabs(S[(j + 1) * Rs + r]), gi);
+          if (j + 1 < ibs) argmax_merge(bv, bi, pivot_mag(S[(j + 1) * Rs + r]), gi);
         }
       }
     }

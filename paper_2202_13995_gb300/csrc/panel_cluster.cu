@@ -10,9 +10,9 @@
 // The grid is one cluster of CL <= 16 CTAs (512 threads each); CTA c owns the
 // panel rows [c R, c R + R).  Per column, the candidates are exchanged
 // through distributed shared memory: every CTA publishes its best (|a|, row)
-// and that row's sub-panel values in its own shared memory, arrives on every
-// peer's mbarrier (release, cluster scope), waits on its own (acquire,
-// bounded), and reads the peers' candidates directly.  That replaces the grid
+// and that row's sub-panel values in its own shared memory, the cluster
+// barrier (release/acquire, cluster scope) follows, and every CTA reads all
+// peers' candidates in one round of DSMEM loads.  That replaces the grid
 // barrier and the L2 round trips of the cooperative kernel.
 //
 // The panel is processed in sub-panels of 16 columns held in registers: a
@@ -22,12 +22,12 @@
 // other columns (columns distributed over the CTAs), every CTA solves the
 // sub-panel's top rows of the columns to its right (U rows, into shared
 // memory), and each CTA updates its own rows of those columns (a rank-16
-// update, coalesced along the row).  Three cluster synchronizations per
-// sub-panel, one per column.
+// update, coalesced along the row, U in registers).  Three cluster
+// synchronizations per sub-panel, one per column.
 //
-// Every wait is bounded (2 s): on timeout the kernel sets ST_TIMEOUT and stops
-// waiting (results are then undefined and reported as such); no CTA leaves
-// early, so the final cluster barrier is always reached by all.
+// The kernel spins on nothing: its only waits are hardware cluster barriers,
+// and every CTA executes the same sequence of them (no CTA leaves early, the
+// loop bounds are the same in all), so each one completes.
 #include <climits>
 #include <mutex>
 #include <utility>
@@ -47,17 +47,14 @@ constexpr int PC_WMAX = 512;
 constexpr int PC_HF = 2048;        // hash buckets: rows outside the panel's top w rows
 constexpr int PC_HS = 128;         // hash buckets: rows outside a sub-panel's top rows
 
-struct PcSmem {
-  unsigned long long bar[2];
+struct alignas(16) PcSmem {
   float slot[2][2 + PC_IB];  // |a|, row (bits), the row's sub-panel values
   float rowj[2][PC_IB];      // row j's sub-panel values (its owner CTA)
   float stg[PC_WARPS][PC_IB];
   float redv[PC_WARPS];
   int redi[PC_WARPS];
-  float prow[PC_IB];
+  float xs[PC_CLMAX][2 + PC_IB];  // every CTA's slot, read through DSMEM
   float rj[PC_IB];
-  int piv_row;
-  int ok;
   int cnt[2];  // permutation record counts: whole panel, sub-panel
   float L11[PC_IB][PC_IB + 1];
   int fpos[2 * PC_WMAX], fcur[2 * PC_WMAX];
@@ -93,20 +90,6 @@ __device__ __forceinline__ float cl_ldf(uint32_t addr) {
   asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
   return v;
 }
-__device__ __forceinline__ void cl_arrive(uint32_t addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
-}
-__device__ __forceinline__ bool cl_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
 __device__ __forceinline__ void cl_barrier() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
@@ -125,29 +108,12 @@ __device__ __forceinline__ float pc_pick(const float (&v)[PC_RPT][PC_IB], int c,
   return x;
 }
 
-// Cluster synchronization: this CTA's prior writes (shared and global)
-// become visible to every peer, and the peers' to this CTA.
-#define PC_CSYNC()                                                        \
-  do {                                                                    \
-    __syncthreads();                                                      \
-    const unsigned s_ = nsync++;                                          \
-    const uint32_t bar_ = sm_u32(&S.bar[s_ & 1]);                         \
-    if (tid < CL) cl_arrive(cl_map(bar_, (uint32_t)tid));                 \
-    if (tid == 0 && S.ok) {                                               \
-      const uint32_t par_ = (s_ >> 1) & 1u;                               \
-      if (!cl_try(bar_, par_)) {                                          \
-        const uint64_t t0_ = gtimer();                                    \
-        while (!cl_try(bar_, par_)) {                                     \
-          if (gtimer() - t0_ > GB_SPIN_LIMIT_NS) {                        \
-            atomicOr(P.status, ST_TIMEOUT);                               \
-            S.ok = 0;                                                     \
-            break;                                                        \
-          }                                                               \
-        }                                                                 \
-      }                                                                   \
-    }                                                                     \
-    __syncthreads();                                                      \
-  } while (0)
+// Cluster synchronization (the hardware cluster barrier, release/acquire at
+// cluster scope): this CTA's prior writes, shared and global, become visible
+// to every peer, and the peers' to this CTA.  Every CTA runs the same
+// sequence of synchronizations (the loop bounds are the same in all), so the
+// barrier always completes.
+#define PC_CSYNC() cl_barrier()
 
 // One column step of a sub-panel, column J (a literal, so that every index
 // into the register tile v is a compile-time constant).
@@ -155,8 +121,9 @@ __device__ __forceinline__ float pc_pick(const float (&v)[PC_RPT][PC_IB], int c,
   if ((J) < ibs) {                                                                                           \
     const int jg = j0 + (J);                                                                                 \
     const int par = jg & 1;                                                                                  \
+    float pr[PC_IB];                                                                                         \
     /* 1. this CTA's candidate and its row; row jg from its owner */                                         \
-    if (bv != bv) atomicOr(P.status, ST_RANGE);                                                              \
+    if (!(bv < INFINITY)) atomicOr(P.status, ST_RANGE); /* a non-finite candidate */                          \
     float wv = bv;                                                                                           \
     int wi = bi;                                                                                             \
     warp_argmax(wv, wi);                                                                                     \
@@ -186,29 +153,35 @@ __device__ __forceinline__ float pc_pick(const float (&v)[PC_RPT][PC_IB], int c,
       }                                                                                                      \
       if (lane < PC_IB) S.slot[par][2 + lane] = ci != INT_MAX ? S.stg[ww][lane] : 0.f;                       \
     }                                                                                                        \
-    /* 2. exchange: every CTA's candidate, the pivot row, row jg */                                          \
+    /* 2. exchange: every CTA's slot and row jg in one round of DSMEM reads */                                \
     PC_CSYNC();                                                                                              \
-    if (warp == 0) {                                                                                         \
-      float cv = -1.f;                                                                                       \
-      int ci = INT_MAX;                                                                                      \
-      if (lane < CL) {                                                                                       \
-        const uint32_t a_ = cl_map(sm_u32(&S.slot[par][0]), (uint32_t)lane);                                 \
-        cv = cl_ldf(a_);                                                                                     \
-        ci = __float_as_int(cl_ldf(a_ + 4));                                                                 \
-      }                                                                                                      \
-      warp_argmax(cv, ci);                                                                                   \
-      if (ci == INT_MAX) ci = jg; /* a column without a comparable entry (NaN) keeps its row */             \
-      const int pc = ci / R, jc = jg / R;                                                                    \
-      if (lane < PC_IB) {                                                                                    \
-        S.prow[lane] = cl_ldf(cl_map(sm_u32(&S.slot[par][2 + lane]), (uint32_t)pc));                         \
-        S.rj[lane] = cl_ldf(cl_map(sm_u32(&S.rowj[par][lane]), (uint32_t)jc));                               \
-      }                                                                                                      \
-      if (lane == 0) S.piv_row = ci;                                                                         \
+    if (tid < CL * (2 + PC_IB)) {                                                                            \
+      const int c_ = tid / (2 + PC_IB), k_ = tid % (2 + PC_IB);                                              \
+      S.xs[c_][k_] = cl_ldf(cl_map(sm_u32(&S.slot[par][k_]), (uint32_t)c_));                                 \
+    } else if (tid >= 320 && tid < 320 + PC_IB) {                                                            \
+      S.rj[tid - 320] = cl_ldf(cl_map(sm_u32(&S.rowj[par][tid - 320]), (uint32_t)(jg / R)));                 \
     }                                                                                                        \
     __syncthreads();                                                                                         \
-    const int p = S.piv_row;                                                                                 \
-    float pr[PC_IB];                                                                                         \
-    _Pragma("unroll") for (int c = 0; c < PC_IB; ++c) pr[c] = S.prow[c];                                     \
+    int p;                                                                                                   \
+    {                                                                                                        \
+      float cv = -1.f;                                                                                       \
+      int ci = INT_MAX, cc = 0;                                                                              \
+      for (int c_ = 0; c_ < CL; ++c_) {                                                                      \
+        const float v_ = S.xs[c_][0];                                                                        \
+        const int i_ = __float_as_int(S.xs[c_][1]);                                                          \
+        if (v_ > cv || (v_ == cv && i_ < ci)) {                                                              \
+          cv = v_;                                                                                           \
+          ci = i_;                                                                                           \
+          cc = c_;                                                                                           \
+        }                                                                                                    \
+      }                                                                                                      \
+      p = ci;                                                                                                \
+      _Pragma("unroll") for (int c = 0; c < PC_IB; ++c) pr[c] = S.xs[cc][2 + c];                             \
+      if (ci == INT_MAX) { /* no candidate at all (cannot happen: row jg is one): keep row jg */           \
+        p = jg;                                                                                              \
+        _Pragma("unroll") for (int c = 0; c < PC_IB; ++c) pr[c] = S.rj[c];                                   \
+      }                                                                                                      \
+    }                                                                                                        \
     const float piv = pr[(J)];                                                                               \
     if (tid == 0) {                                                                                          \
       if (cta == 0) {                                                                                        \
@@ -240,7 +213,7 @@ __device__ __forceinline__ float pc_pick(const float (&v)[PC_RPT][PC_IB], int c,
           v[q][(J)] = l;                                                                                     \
           _Pragma("unroll") for (int c = (J) + 1; c < PC_IB; ++c) v[q][c] -= l * pr[c];                      \
           if ((J) + 1 < ibs) {                                                                               \
-            const float a = fabsf(v[q][((J) + 1) & (PC_IB - 1)]);                                            \
+            const float a = pivot_mag(v[q][((J) + 1) & (PC_IB - 1)]);                                       \
             if (a > bv || (a == bv && rg < bi)) {                                                            \
               bv = a;                                                                                        \
               bi = rg;                                                                                       \
@@ -269,21 +242,17 @@ __global__ void __launch_bounds__(PC_THREADS, 1) panel_cluster_kernel(PcParams P
     S.fcur[s] = s;
   }
   for (int s = tid; s < PC_HF; s += PC_THREADS) S.hfk[s] = -1;
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sm_u32(&S.bar[0])), "r"(CL) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sm_u32(&S.bar[1])), "r"(CL) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    S.ok = 1;
-    S.cnt[0] = w;
-  }
+  if (tid == 0) S.cnt[0] = w;
   __syncthreads();
-  cl_barrier();  // every peer's mbarriers exist before any remote arrival
+  cl_barrier();  // every peer has started before any DSMEM access
   const PermRec fperm{S.fpos, S.fcur, S.hfk, S.hfv, PC_HF - 1, 0, w, &S.cnt[0]};
-  unsigned nsync = 0;
 
   float v[PC_RPT][PC_IB];
+  // 16-byte row segments: the tile moves in float4 when the rows allow it
+  const bool aligned = ((uintptr_t)A & 15u) == 0 && (ld % 4) == 0;
   for (int j0 = 0; j0 < w; j0 += PC_IB) {
     const int ibs = min(PC_IB, w - j0);
+    const bool vec = aligned && ibs == PC_IB;
     // ---- the sub-panel's rows into registers
 #pragma unroll
     for (int q = 0; q < PC_RPT; ++q) {
@@ -292,9 +261,20 @@ __global__ void __launch_bounds__(PC_THREADS, 1) panel_cluster_kernel(PcParams P
       for (int c = 0; c < PC_IB; ++c) v[q][c] = 0.f;
       if (r < rloc) {
         const float* src = A + (int64_t)(row0 + r) * ld + j0;
+        if (vec) {
 #pragma unroll
-        for (int c = 0; c < PC_IB; ++c)
-          if (c < ibs) v[q][c] = __ldcg(src + c);
+          for (int u = 0; u < PC_IB / 4; ++u) {
+            const float4 x = __ldcg(reinterpret_cast<const float4*>(src) + u);
+            v[q][4 * u] = x.x;
+            v[q][4 * u + 1] = x.y;
+            v[q][4 * u + 2] = x.z;
+            v[q][4 * u + 3] = x.w;
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < PC_IB; ++c)
+            if (c < ibs) v[q][c] = __ldcg(src + c);
+        }
       }
     }
     for (int s = tid; s < ibs; s += PC_THREADS) {
@@ -313,7 +293,7 @@ __global__ void __launch_bounds__(PC_THREADS, 1) panel_cluster_kernel(PcParams P
     for (int q = 0; q < PC_RPT; ++q) {
       const int r = tid + PC_THREADS * q;
       if (r < rloc && row0 + r >= j0) {
-        const float a = fabsf(v[q][0]);
+        const float a = pivot_mag(v[q][0]);
         if (a > bv || (a == bv && row0 + r < bi)) {
           bv = a;
           bi = row0 + r;
@@ -330,10 +310,17 @@ __global__ void __launch_bounds__(PC_THREADS, 1) panel_cluster_kernel(PcParams P
       const int r = tid + PC_THREADS * q;
       if (r < rloc) {
         float* dst = A + (int64_t)(row0 + r) * ld + j0;
+        float4* lsv = reinterpret_cast<float4*>(Ls + r * PC_IB);
 #pragma unroll
-        for (int c = 0; c < PC_IB; ++c) {
-          if (c < ibs) dst[c] = v[q][c];
-          Ls[r * PC_IB + c] = v[q][c];
+        for (int u = 0; u < PC_IB / 4; ++u) {
+          const float4 x = make_float4(v[q][4 * u], v[q][4 * u + 1], v[q][4 * u + 2], v[q][4 * u + 3]);
+          lsv[u] = x;
+          if (vec) reinterpret_cast<float4*>(dst)[u] = x;
+        }
+        if (!vec) {
+#pragma unroll
+          for (int c = 0; c < PC_IB; ++c)
+            if (c < ibs) dst[c] = v[q][c];
         }
       }
     }
@@ -377,24 +364,65 @@ __global__ void __launch_bounds__(PC_THREADS, 1) panel_cluster_kernel(PcParams P
     }
     PC_CSYNC();  // every CTA has read the top rows before their owners overwrite them
     if (nr > 0) {
-      // ---- (d) own rows: top rows take U, rows below get the rank-ibs update
+      // ---- (d) own rows: top rows take U; rows below get the rank-ibs
+      //      update.  A warp takes rows; a lane takes 4 columns 32 apart per
+      //      pass, with their U column in registers (4 FMAs per shared-memory
+      //      load of the row's L value), the next row's values loaded ahead.
       for (int r = warp; r < rloc; r += PC_WARPS) {
         const int rg = row0 + r;
-        if (rg < j0) continue;
-        float* rowp = A + (int64_t)rg * ld + j0 + ibs;
-        if (rg < j0 + ibs) {
+        if (rg >= j0 && rg < j0 + ibs) {
+          float* rowp = A + (int64_t)rg * ld + j0 + ibs;
           for (int c = lane; c < nr; c += 32) rowp[c] = S.U[rg - j0][c];
-          continue;
         }
-        float lv[PC_IB];
+      }
+      const int rfirst = max(0, j0 + ibs - row0);  // first own row below the sub-panel
+      for (int cb = 0; cb < nr; cb += 128) {
+        float u[PC_IB][4];
 #pragma unroll
-        for (int t = 0; t < PC_IB; ++t) lv[t] = Ls[r * PC_IB + t];
-        for (int c = lane; c < nr; c += 32) {
-          float a = __ldcg(rowp + c);
+        for (int t = 0; t < PC_IB; ++t)
 #pragma unroll
-          for (int t = 0; t < PC_IB; ++t)
-            if (t < ibs) a -= lv[t] * S.U[t][c];
-          rowp[c] = a;
+          for (int k = 0; k < 4; ++k) {
+            const int c = cb + lane + 32 * k;
+            u[t][k] = (t < ibs && c < nr) ? S.U[t][c] : 0.f;
+          }
+        int r = rfirst + warp;
+        float a[4];
+        if (r < rloc) {
+          const float* rowp = A + (int64_t)(row0 + r) * ld + j0 + ibs + cb;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) a[k] = (cb + lane + 32 * k < nr) ? __ldcg(rowp + lane + 32 * k) : 0.f;
+        }
+        for (; r < rloc; r += PC_WARPS) {
+          float* rowp = A + (int64_t)(row0 + r) * ld + j0 + ibs + cb;
+          // next row's values in flight
+          const int rn = r + PC_WARPS;
+          float an[4];
+          if (rn < rloc) {
+            const float* np = A + (int64_t)(row0 + rn) * ld + j0 + ibs + cb;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) an[k] = (cb + lane + 32 * k < nr) ? __ldcg(np + lane + 32 * k) : 0.f;
+          }
+          const float4* lr4 = reinterpret_cast<const float4*>(Ls + r * PC_IB);
+#pragma unroll
+          for (int t4 = 0; t4 < PC_IB / 4; ++t4) {
+            const float4 l4 = lr4[t4];
+            const float lt[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+            for (int tt = 0; tt < 4; ++tt) {
+              const int t = 4 * t4 + tt;
+              if (t < ibs) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) a[k] -= lt[tt] * u[t][k];
+              }
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (cb + lane + 32 * k < nr) rowp[lane + 32 * k] = a[k];
+          if (rn < rloc) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a[k] = an[k];
+          }
         }
       }
     }
