@@ -177,7 +177,11 @@ extern "C" int lu_create(lu_ctx* out, void* cuda_stream) {
   }
   cudaMemset(c->d_status, 0, 64 * sizeof(int));
   cudaMemset(c->d_small, 0, 128 * sizeof(double));
-  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+  // the side stream (lookahead panels) has the highest priority, so that a
+  // panel waiting for SMs is placed before the concurrent update's CTAs
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_next, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_panel, cudaEventDisableTiming) != cudaSuccess) {
     lu_destroy(c);

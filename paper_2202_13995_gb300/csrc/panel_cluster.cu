@@ -15,9 +15,12 @@
 // peers' candidates in one round of DSMEM loads.  That replaces the grid
 // barrier and the L2 round trips of the cooperative kernel.
 //
-// The panel is processed in sub-panels of 16 columns held in registers: a
-// thread owns up to 4 rows (tid + 512 q) of the sub-panel, so the per-column
-// scaling and rank-1 update touch registers only.  After a sub-panel: its
+// The panel is processed in sub-panels of 16 columns.  A thread owns up to 4
+// rows (tid + 512 q) of the sub-panel; the part of a row still being updated
+// sits in registers, rotated so that the current column is always register 0
+// (every register index is a compile-time constant and one copy of the column
+// code serves all columns), and the finished part of every row goes to shared
+// memory (Ls), where the sub-panel is whole when its last column is done.  After a sub-panel: its
 // values are written back, its row interchanges are applied to the panel's
 // other columns (columns distributed over the CTAs), every CTA solves the
 // sub-panel's top rows of the columns to its right (U rows, into shared
@@ -115,116 +118,6 @@ __device__ __forceinline__ float pc_pick(const float (&v)[PC_RPT][PC_IB], int c,
 // barrier always completes.
 #define PC_CSYNC() cl_barrier()
 
-// One column step of a sub-panel, column J (a literal, so that every index
-// into the register tile v is a compile-time constant).
-#define PC_COLUMN(J)                                                                                         \
-  if ((J) < ibs) {                                                                                           \
-    const int jg = j0 + (J);                                                                                 \
-    const int par = jg & 1;                                                                                  \
-    float pr[PC_IB];                                                                                         \
-    /* 1. this CTA's candidate and its row; row jg from its owner */                                         \
-    if (!(bv < INFINITY)) atomicOr(P.status, ST_RANGE); /* a non-finite candidate */                          \
-    float wv = bv;                                                                                           \
-    int wi = bi;                                                                                             \
-    warp_argmax(wv, wi);                                                                                     \
-    if (wi != INT_MAX && bi == wi) {                                                                         \
-      _Pragma("unroll") for (int c = 0; c < PC_IB; ++c) S.stg[warp][c] = pc_pick(v, c, bq);                 \
-    }                                                                                                        \
-    if (lane == 0) {                                                                                         \
-      S.redv[warp] = wv;                                                                                     \
-      S.redi[warp] = wi;                                                                                     \
-    }                                                                                                        \
-    {                                                                                                        \
-      const int lr = jg - row0;                                                                              \
-      if (lr >= 0 && lr < rloc && (lr % PC_THREADS) == tid) {                                                \
-        _Pragma("unroll") for (int c = 0; c < PC_IB; ++c) S.rowj[par][c] = pc_pick(v, c, lr / PC_THREADS);   \
-      }                                                                                                      \
-    }                                                                                                        \
-    __syncthreads();                                                                                         \
-    if (warp == 0) {                                                                                         \
-      float cv = lane < PC_WARPS ? S.redv[lane] : -1.f;                                                      \
-      int ci = lane < PC_WARPS ? S.redi[lane] : INT_MAX;                                                     \
-      warp_argmax(cv, ci);                                                                                   \
-      const unsigned mk = __ballot_sync(0xffffffffu, lane < PC_WARPS && ci != INT_MAX && S.redi[lane] == ci); \
-      const int ww = mk ? __ffs(mk) - 1 : 0;                                                                 \
-      if (lane == 0) {                                                                                       \
-        S.slot[par][0] = cv;                                                                                 \
-        S.slot[par][1] = __int_as_float(ci);                                                                 \
-      }                                                                                                      \
-      if (lane < PC_IB) S.slot[par][2 + lane] = ci != INT_MAX ? S.stg[ww][lane] : 0.f;                       \
-    }                                                                                                        \
-    /* 2. exchange: every CTA's slot and row jg in one round of DSMEM reads */                                \
-    PC_CSYNC();                                                                                              \
-    if (tid < CL * (2 + PC_IB)) {                                                                            \
-      const int c_ = tid / (2 + PC_IB), k_ = tid % (2 + PC_IB);                                              \
-      S.xs[c_][k_] = cl_ldf(cl_map(sm_u32(&S.slot[par][k_]), (uint32_t)c_));                                 \
-    } else if (tid >= 320 && tid < 320 + PC_IB) {                                                            \
-      S.rj[tid - 320] = cl_ldf(cl_map(sm_u32(&S.rowj[par][tid - 320]), (uint32_t)(jg / R)));                 \
-    }                                                                                                        \
-    __syncthreads();                                                                                         \
-    int p;                                                                                                   \
-    {                                                                                                        \
-      float cv = -1.f;                                                                                       \
-      int ci = INT_MAX, cc = 0;                                                                              \
-      for (int c_ = 0; c_ < CL; ++c_) {                                                                      \
-        const float v_ = S.xs[c_][0];                                                                        \
-        const int i_ = __float_as_int(S.xs[c_][1]);                                                          \
-        if (v_ > cv || (v_ == cv && i_ < ci)) {                                                              \
-          cv = v_;                                                                                           \
-          ci = i_;                                                                                           \
-          cc = c_;                                                                                           \
-        }                                                                                                    \
-      }                                                                                                      \
-      p = ci;                                                                                                \
-      _Pragma("unroll") for (int c = 0; c < PC_IB; ++c) pr[c] = S.xs[cc][2 + c];                             \
-      if (ci == INT_MAX) { /* no candidate at all (cannot happen: row jg is one): keep row jg */           \
-        p = jg;                                                                                              \
-        _Pragma("unroll") for (int c = 0; c < PC_IB; ++c) pr[c] = S.rj[c];                                   \
-      }                                                                                                      \
-    }                                                                                                        \
-    const float piv = pr[(J)];                                                                               \
-    if (tid == 0) {                                                                                          \
-      if (cta == 0) {                                                                                        \
-        P.ipiv[P.kabs + jg] = P.kabs + p + 1;                                                                \
-        if (piv == 0.f) atomicMin(P.info, P.kabs + jg + 1);                                                  \
-      }                                                                                                      \
-      if (p != jg) {                                                                                         \
-        if (cta == 0) fperm.swap_rows(jg, p);                                                                \
-        sperm.swap_rows(jg, p);                                                                              \
-      }                                                                                                      \
-    }                                                                                                        \
-    /* 3. swap, scale (a division, as in the definition), rank-1 update, next candidate */                   \
-    bv = -1.f;                                                                                               \
-    bi = INT_MAX;                                                                                            \
-    bq = 0;                                                                                                  \
-    _Pragma("unroll") for (int q = 0; q < PC_RPT; ++q) {                                                     \
-      const int r = tid + PC_THREADS * q;                                                                    \
-      const int rg = row0 + r;                                                                               \
-      if (r < rloc) {                                                                                        \
-        if (p != jg && rg == p) {                                                                            \
-          _Pragma("unroll") for (int c = 0; c < PC_IB; ++c) v[q][c] = S.rj[c];                               \
-        }                                                                                                    \
-        if (rg == jg) {                                                                                      \
-          _Pragma("unroll") for (int c = 0; c < PC_IB; ++c) v[q][c] = pr[c];                                 \
-        }                                                                                                    \
-        if (rg > jg) {                                                                                       \
-          float l = v[q][(J)];                                                                               \
-          if (piv != 0.f) l = l / piv;                                                                       \
-          v[q][(J)] = l;                                                                                     \
-          _Pragma("unroll") for (int c = (J) + 1; c < PC_IB; ++c) v[q][c] -= l * pr[c];                      \
-          if ((J) + 1 < ibs) {                                                                               \
-            const float a = pivot_mag(v[q][((J) + 1) & (PC_IB - 1)]);                                       \
-            if (a > bv || (a == bv && rg < bi)) {                                                            \
-              bv = a;                                                                                        \
-              bi = rg;                                                                                       \
-              bq = q;                                                                                        \
-            }                                                                                                \
-          }                                                                                                  \
-        }                                                                                                    \
-      }                                                                                                      \
-    }                                                                                                        \
-  }
-
 __global__ void __launch_bounds__(PC_THREADS, 1) panel_cluster_kernel(PcParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   PcSmem& S = *reinterpret_cast<PcSmem*>(smem_raw);
@@ -277,6 +170,17 @@ __global__ void __launch_bounds__(PC_THREADS, 1) panel_cluster_kernel(PcParams P
         }
       }
     }
+    // every row's sub-panel values also start in Ls (rows above the
+    // sub-panel keep them; the others are overwritten as they finish)
+#pragma unroll
+    for (int q = 0; q < PC_RPT; ++q) {
+      const int r = tid + PC_THREADS * q;
+      if (r < rloc) {
+        float4* lsv = reinterpret_cast<float4*>(Ls + r * PC_IB);
+#pragma unroll
+        for (int u = 0; u < PC_IB / 4; ++u) lsv[u] = make_float4(v[q][4 * u], v[q][4 * u + 1], v[q][4 * u + 2], v[q][4 * u + 3]);
+      }
+    }
     for (int s = tid; s < ibs; s += PC_THREADS) {
       S.spos[s] = j0 + s;
       S.scur[s] = j0 + s;
@@ -301,26 +205,145 @@ __global__ void __launch_bounds__(PC_THREADS, 1) panel_cluster_kernel(PcParams P
         }
       }
     }
-    PC_COLUMN(0) PC_COLUMN(1) PC_COLUMN(2) PC_COLUMN(3) PC_COLUMN(4) PC_COLUMN(5) PC_COLUMN(6) PC_COLUMN(7)
-    PC_COLUMN(8) PC_COLUMN(9) PC_COLUMN(10) PC_COLUMN(11) PC_COLUMN(12) PC_COLUMN(13) PC_COLUMN(14) PC_COLUMN(15)
+#pragma unroll 1
+    for (int J = 0; J < ibs; ++J) {
+      const int jg = j0 + J;
+      const int par = jg & 1;
+      // ---- 1. this CTA's candidate and its row; row jg from its owner.  A
+      //      published row is whole: its finished part from Ls, the rest
+      //      from the (rotated) registers.
+      if (!(bv < INFINITY)) atomicOr(P.status, ST_RANGE);  // a non-finite candidate
+      float wv = bv;
+      int wi = bi;
+      warp_argmax(wv, wi);
+      if (wi != INT_MAX && bi == wi) {
+        const int r = wi - row0;
+        for (int c = 0; c < J; ++c) S.stg[warp][c] = Ls[r * PC_IB + c];
+#pragma unroll
+        for (int k = 0; k < PC_IB; ++k)
+          if (J + k < PC_IB) S.stg[warp][J + k] = pc_pick(v, k, bq);
+      }
+      if (lane == 0) {
+        S.redv[warp] = wv;
+        S.redi[warp] = wi;
+      }
+      {
+        const int lr = jg - row0;
+        if (lr >= 0 && lr < rloc && (lr % PC_THREADS) == tid) {
+          for (int c = 0; c < J; ++c) S.rowj[par][c] = Ls[lr * PC_IB + c];
+#pragma unroll
+          for (int k = 0; k < PC_IB; ++k)
+            if (J + k < PC_IB) S.rowj[par][J + k] = pc_pick(v, k, lr / PC_THREADS);
+        }
+      }
+      __syncthreads();
+      if (warp == 0) {
+        float cv = lane < PC_WARPS ? S.redv[lane] : -1.f;
+        int ci = lane < PC_WARPS ? S.redi[lane] : INT_MAX;
+        warp_argmax(cv, ci);
+        const unsigned mk = __ballot_sync(0xffffffffu, lane < PC_WARPS && ci != INT_MAX && S.redi[lane] == ci);
+        const int ww = mk ? __ffs(mk) - 1 : 0;
+        if (lane == 0) {
+          S.slot[par][0] = cv;
+          S.slot[par][1] = __int_as_float(ci);
+        }
+        if (lane < PC_IB) S.slot[par][2 + lane] = ci != INT_MAX ? S.stg[ww][lane] : 0.f;
+      }
+      // ---- 2. exchange: every CTA's slot and row jg in one round of DSMEM reads
+      PC_CSYNC();
+      if (tid < CL * (2 + PC_IB)) {
+        const int c_ = tid / (2 + PC_IB), k_ = tid % (2 + PC_IB);
+        S.xs[c_][k_] = cl_ldf(cl_map(sm_u32(&S.slot[par][k_]), (uint32_t)c_));
+      } else if (tid >= 320 && tid < 320 + PC_IB) {
+        S.rj[tid - 320] = cl_ldf(cl_map(sm_u32(&S.rowj[par][tid - 320]), (uint32_t)(jg / R)));
+      }
+      __syncthreads();
+      int p, cc = 0;
+      {
+        float cv = -1.f;
+        int ci = INT_MAX;
+        for (int c_ = 0; c_ < CL; ++c_) {
+          const float v_ = S.xs[c_][0];
+          const int i_ = __float_as_int(S.xs[c_][1]);
+          if (v_ > cv || (v_ == cv && i_ < ci)) {
+            cv = v_;
+            ci = i_;
+            cc = c_;
+          }
+        }
+        p = ci;
+      }
+      const float* prow = p != INT_MAX ? &S.xs[cc][2] : S.rj;  // the whole pivot row
+      if (p == INT_MAX) p = jg;  // no candidate at all (cannot happen: row jg is one)
+      float pr[PC_IB];  // its part from column J on, rotated like the registers
+#pragma unroll
+      for (int k = 0; k < PC_IB; ++k) pr[k] = J + k < PC_IB ? prow[J + k] : 0.f;
+      const float piv = pr[0];
+      if (tid == 0) {
+        if (cta == 0) {
+          P.ipiv[P.kabs + jg] = P.kabs + p + 1;
+          if (piv == 0.f) atomicMin(P.info, P.kabs + jg + 1);
+        }
+        if (p != jg) {
+          if (cta == 0) fperm.swap_rows(jg, p);
+          sperm.swap_rows(jg, p);
+        }
+      }
+      // ---- 3. swap, scale (a division, as in the definition), rank-1
+      //      update, rotation, and the next column's local candidate
+      bv = -1.f;
+      bi = INT_MAX;
+      bq = 0;
+#pragma unroll
+      for (int q = 0; q < PC_RPT; ++q) {
+        const int r = tid + PC_THREADS * q;
+        const int rg = row0 + r;
+        if (r < rloc) {
+          if (p != jg && rg == p) {
+            // row p takes row jg: its finished part and its current part
+            for (int c = 0; c < J; ++c) Ls[r * PC_IB + c] = S.rj[c];
+#pragma unroll
+            for (int k = 0; k < PC_IB; ++k) v[q][k] = J + k < PC_IB ? S.rj[J + k] : 0.f;
+          }
+          if (rg == jg) {
+            // the pivot row is final from here on
+            for (int c = 0; c < PC_IB; ++c) Ls[r * PC_IB + c] = prow[c];
+          }
+          if (rg > jg) {
+            float l = v[q][0];
+            if (piv != 0.f) l = l / piv;
+            Ls[r * PC_IB + J] = l;
+#pragma unroll
+            for (int k = 1; k < PC_IB; ++k) v[q][k] -= l * pr[k];
+#pragma unroll
+            for (int k = 0; k + 1 < PC_IB; ++k) v[q][k] = v[q][k + 1];
+            v[q][PC_IB - 1] = 0.f;
+            if (J + 1 < ibs) {
+              const float a = pivot_mag(v[q][0]);
+              if (a > bv || (a == bv && rg < bi)) {
+                bv = a;
+                bi = rg;
+                bq = q;
+              }
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
 
-    // ---- (a) sub-panel back to memory; its L rows into shared memory
+    // ---- (a) the sub-panel (whole in Ls) back to memory
 #pragma unroll
     for (int q = 0; q < PC_RPT; ++q) {
       const int r = tid + PC_THREADS * q;
       if (r < rloc) {
         float* dst = A + (int64_t)(row0 + r) * ld + j0;
-        float4* lsv = reinterpret_cast<float4*>(Ls + r * PC_IB);
+        const float4* lsv = reinterpret_cast<const float4*>(Ls + r * PC_IB);
+        if (vec) {
 #pragma unroll
-        for (int u = 0; u < PC_IB / 4; ++u) {
-          const float4 x = make_float4(v[q][4 * u], v[q][4 * u + 1], v[q][4 * u + 2], v[q][4 * u + 3]);
-          lsv[u] = x;
-          if (vec) reinterpret_cast<float4*>(dst)[u] = x;
-        }
-        if (!vec) {
-#pragma unroll
-          for (int c = 0; c < PC_IB; ++c)
-            if (c < ibs) dst[c] = v[q][c];
+          for (int u = 0; u < PC_IB / 4; ++u) reinterpret_cast<float4*>(dst)[u] = lsv[u];
+        } else {
+          for (int c = 0; c < ibs; ++c) dst[c] = Ls[r * PC_IB + c];
         }
       }
     }
@@ -376,6 +399,7 @@ __global__ void __launch_bounds__(PC_THREADS, 1) panel_cluster_kernel(PcParams P
         }
       }
       const int rfirst = max(0, j0 + ibs - row0);  // first own row below the sub-panel
+      constexpr int D = 2;                         // rows per step (and rows of loads in flight)
       for (int cb = 0; cb < nr; cb += 128) {
         float u[PC_IB][4];
 #pragma unroll
@@ -385,44 +409,50 @@ __global__ void __launch_bounds__(PC_THREADS, 1) panel_cluster_kernel(PcParams P
             const int c = cb + lane + 32 * k;
             u[t][k] = (t < ibs && c < nr) ? S.U[t][c] : 0.f;
           }
-        int r = rfirst + warp;
-        float a[4];
-        if (r < rloc) {
-          const float* rowp = A + (int64_t)(row0 + r) * ld + j0 + ibs + cb;
+        bool cok[4];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) a[k] = (cb + lane + 32 * k < nr) ? __ldcg(rowp + lane + 32 * k) : 0.f;
-        }
-        for (; r < rloc; r += PC_WARPS) {
-          float* rowp = A + (int64_t)(row0 + r) * ld + j0 + ibs + cb;
-          // next row's values in flight
-          const int rn = r + PC_WARPS;
-          float an[4];
-          if (rn < rloc) {
-            const float* np = A + (int64_t)(row0 + rn) * ld + j0 + ibs + cb;
+        for (int k = 0; k < 4; ++k) cok[k] = cb + lane + 32 * k < nr;
+        auto load_rows = [&](int rb, float (&x)[D][4]) {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) an[k] = (cb + lane + 32 * k < nr) ? __ldcg(np + lane + 32 * k) : 0.f;
+          for (int d = 0; d < D; ++d) {
+            const int r = rb + PC_WARPS * d;
+            const float* rp = A + (int64_t)(row0 + r) * ld + j0 + ibs + cb + lane;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) x[d][k] = (r < rloc && cok[k]) ? __ldcg(rp + 32 * k) : 0.f;
           }
-          const float4* lr4 = reinterpret_cast<const float4*>(Ls + r * PC_IB);
+        };
+        float a[D][4], an[D][4];
+        int rb = rfirst + warp;
+        load_rows(rb, a);
+        for (; rb < rloc; rb += PC_WARPS * D) {
+          load_rows(rb + PC_WARPS * D, an);  // the next rows' values in flight
 #pragma unroll
-          for (int t4 = 0; t4 < PC_IB / 4; ++t4) {
-            const float4 l4 = lr4[t4];
-            const float lt[4] = {l4.x, l4.y, l4.z, l4.w};
+          for (int d = 0; d < D; ++d) {
+            const int r = rb + PC_WARPS * d;
+            if (r < rloc) {
+              const float4* lr4 = reinterpret_cast<const float4*>(Ls + r * PC_IB);
 #pragma unroll
-            for (int tt = 0; tt < 4; ++tt) {
-              const int t = 4 * t4 + tt;
-              if (t < ibs) {
+              for (int t4 = 0; t4 < PC_IB / 4; ++t4) {
+                const float4 l4 = lr4[t4];
+                const float lt[4] = {l4.x, l4.y, l4.z, l4.w};
 #pragma unroll
-                for (int k = 0; k < 4; ++k) a[k] -= lt[tt] * u[t][k];
+                for (int tt = 0; tt < 4; ++tt) {
+                  if (4 * t4 + tt < ibs) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) a[d][k] -= lt[tt] * u[4 * t4 + tt][k];
+                  }
+                }
               }
+              float* rowp = A + (int64_t)(row0 + r) * ld + j0 + ibs + cb + lane;
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                if (cok[k]) rowp[32 * k] = a[d][k];
             }
           }
 #pragma unroll
-          for (int k = 0; k < 4; ++k)
-            if (cb + lane + 32 * k < nr) rowp[lane + 32 * k] = a[k];
-          if (rn < rloc) {
+          for (int d = 0; d < D; ++d)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) a[k] = an[k];
-          }
+            for (int k = 0; k < 4; ++k) a[d][k] = an[d][k];
         }
       }
     }
