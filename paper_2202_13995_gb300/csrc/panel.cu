@@ -400,11 +400,14 @@ int panel_grid_size(int m, int w, int tsize, const DevInfo& dev, int gmax, int g
   return (int)cdiv(m, R);
 }
 
-// FP32 panels use the cluster kernel when it fits (and GB300LU_PANEL_COOP is
-// not set); everything else uses the cooperative grid kernel.
+// Panels use the cooperative grid kernel.  The cluster kernel (FP32 only;
+// GB300LU_PANEL_CLUSTER set) computes the same factorization on at most 16
+// SMs: about 4 us per column like the cooperative kernel, but its in-panel
+// update on 16 SMs makes it slower alone (210 vs 185 ms of panels at
+// n = 32768), and beside the lookahead update it waits for a free GPC.
 static bool use_cluster_panel(int m, int w, int tsize) {
-  static const bool coop = getenv("GB300LU_PANEL_COOP") != nullptr;
-  return tsize == 4 && !coop && panel_cluster_available(m, w);
+  static const bool cluster = getenv("GB300LU_PANEL_CLUSTER") != nullptr;
+  return tsize == 4 && cluster && panel_cluster_available(m, w);
 }
 
 int panel_sm_use(int m, int w, int tsize, const DevInfo& dev, const PanelScratch& s) {
