@@ -619,6 +619,7 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision companion measurement")
     ap.add_argument("--rate", type=float, default=None, help="served: offered requests per second")
     ap.add_argument("--seconds", type=float, default=None, help="served: seconds of arrivals")
+    ap.add_argument("--slots", type=int, default=None, help="served: worker slots of the server")
     args = ap.parse_args()
     cfg = WORKLOADS[args.workload]
     if args.workload.startswith("served"):
@@ -627,7 +628,7 @@ def main():
             return 0
         import torch
         torch.cuda.set_device(0)
-        r = served_measure(cfg, args.rate, args.seconds)
+        r = served_measure(dict(cfg, slots=args.slots) if args.slots else cfg, args.rate, args.seconds)
         line = {"metric": "served solves/s, p50/p99 latency ms", "value": r["solves_per_s"], "unit": "solves/s",
                 "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": r["wall_s"] * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "fp16+f32acc+f64refine", "data": "synthetic",

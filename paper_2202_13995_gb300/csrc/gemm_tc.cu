@@ -6,13 +6,18 @@
 // 2202.13995, section "Base Implementation"; the paper's own design unrolls a
 // register-blocked GEMM in FPGA DSPs), here on the 5th-generation tensor cores:
 //   - warp 0 (one thread) streams K-chunks of 64 elements of both operands
-//     into a 3-stage shared-memory ring with TMA (128-byte swizzle), small
-//     enough that a concurrent FP32 panel CTA fits on the same SM;
+//     into a 3-stage shared-memory ring with TMA (128-byte swizzle);
 //   - warp 1 (one thread) issues tcgen05.mma (M=128, N=256, K=16) into one of
 //     two TMEM accumulators (2 x 256 columns), committing each stage back to
 //     the producer and each finished tile to the epilogue;
 //   - warps 2..9 drain a finished accumulator with tcgen05.ld while the next
 //     tile accumulates in the other one, and subtract it from C in place.
+//     C moves through shared memory in 32 x 32 chunks: each epilogue warp
+//     keeps TC_CBUF chunk buffers and loads C (cp.async, row-contiguous
+//     16-byte pieces, four full 128-byte lines per warp instruction) three
+//     chunks ahead of the one it drains.  TMEM hands each thread one row: the
+//     thread subtracts its row in shared memory, and the warp writes the chunk
+//     back row-contiguously.  The CTA's next tile is also prefetched into L2.
 // Persistent CTAs (one per SM) walk the output tiles.  Every mbarrier wait is
 // bounded; on timeout the kernel raises ST_TIMEOUT, lets its TMA loads and
 // MMAs land, frees its TMEM and returns.
@@ -31,13 +36,17 @@ namespace gb {
 constexpr int TC_BM = 128;
 constexpr int TC_BN = 256;
 constexpr int TC_BK = 64;  // one 128-byte swizzle row of 16-bit elements
-constexpr int TC_STAGES = 3;  // 144 KB ring: leaves room for one panel CTA on the same SM
+constexpr int TC_STAGES = 2;  // 96 KB ring: the MMAs of a tile take a fraction of its epilogue
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;  // 16 KB
 constexpr int TC_B_BYTES = TC_BN * TC_BK * 2;  // 32 KB
 constexpr int TC_EPI_WARPS = 8;
 constexpr int TC_THREADS = 32 * (2 + TC_EPI_WARPS);
 constexpr int TC_TMEM_COLS = 512;
-constexpr size_t TC_SMEM = 1024 + (size_t)TC_STAGES * (TC_A_BYTES + TC_B_BYTES) + 256;
+constexpr int TC_CHUNK_BYTES = 32 * 32 * 4;  // 32 rows x 32 columns of FP32 C
+constexpr int TC_CBUF = 4;                    // chunk buffers per epilogue warp (3 loads ahead)
+constexpr int TC_STG_BYTES = TC_CBUF * TC_CHUNK_BYTES;
+constexpr size_t TC_SMEM = 1024 + (size_t)TC_STAGES * (TC_A_BYTES + TC_B_BYTES) + TC_EPI_WARPS * TC_STG_BYTES + 256;
+static_assert(TC_SMEM <= 232448, "tc_gemm_kernel shared memory");
 
 // ------------------------------------------------------------ kernel
 struct TcParams {
@@ -58,7 +67,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   unsigned char* gbase = smem_raw + (base - raw);
   const uint32_t sA = base;
   const uint32_t sB = base + TC_STAGES * TC_A_BYTES;
-  unsigned char* ctl = gbase + TC_STAGES * (TC_A_BYTES + TC_B_BYTES);
+  float4* stg_all = reinterpret_cast<float4*>(gbase + TC_STAGES * (TC_A_BYTES + TC_B_BYTES));
+  unsigned char* ctl = gbase + TC_STAGES * (TC_A_BYTES + TC_B_BYTES) + TC_EPI_WARPS * TC_STG_BYTES;
   const uint32_t bar_full = smem_u32(ctl);
   const uint32_t bar_empty = bar_full + 8 * TC_STAGES;
   const uint32_t bar_tfull = bar_empty + 8 * TC_STAGES;
@@ -183,47 +193,135 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ---------------- epilogue: C -= accumulator
     const int q = warp & 3;              // TMEM lane quarter this warp may access
     const int half = (warp - 2) >> 2;    // which 128 columns of the tile
+    const uint32_t cbuf = smem_u32(stg_all) + (uint32_t)((warp - 2) * TC_STG_BYTES);
+    float4* const cbuf_p = stg_all + (warp - 2) * (TC_STG_BYTES / 16);
+    // Coalesced view of a chunk: lane -> rows 4i + lane/8 (i < 8), 16-byte
+    // unit lane%8.  In a buffer, (row r, unit u) sits at float4 r*8 +
+    // (u ^ (r & 7)), so that the row-per-lane accesses and the coalesced ones
+    // are both free of bank conflicts; (4i + lane/8) & 7 depends on i only
+    // through its parity.
+    const int rsub = lane >> 3, unit = lane & 7;
+    const uint32_t coff0 = (uint32_t)(rsub * 8 + (unit ^ rsub)) * 16u;        // even i
+    const uint32_t coff1 = (uint32_t)(rsub * 8 + (unit ^ (rsub + 4))) * 16u;  // odd i, less 512 B
+    const int64_t ldc4 = 4 * P.ldc;
+    // A lane's view of one tile: its first row and column, rows and columns left.
+    struct View {
+      float* p;
+      int rows, cols;  // rows and columns of C from the lane's first ones on
+      bool vec;        // C rows 16-byte aligned (else the element-wise path only)
+    };
+    auto view_of = [&](int t) -> View {
+      View v;
+      const int tm = t % P.tiles_m, tn = t / P.tiles_m;
+      const int r0 = tm * TC_BM + q * 32 + rsub, c0 = tn * TC_BN + half * 128 + 4 * unit;
+      v.p = P.C + (int64_t)r0 * P.ldc + c0;
+      v.rows = P.m - r0;
+      v.cols = P.n - c0;
+      v.vec = P.vec_ok != 0;
+      return v;
+    };
+    // cp.async of chunk cc of a tile (zero-filled where C is ragged: those
+    // pieces are updated in global memory directly)
+    auto load_chunk = [&](const View& v, int cc, int slot) {
+      const bool full = v.vec && cc * 32 + 4 <= v.cols;
+      const uint32_t b = cbuf + (uint32_t)(slot * TC_CHUNK_BYTES);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const bool ok = full && 4 * i < v.rows;
+        const float* src = v.p + i * ldc4 + cc * 32;
+        cpa16_zfill(b + (uint32_t)(i >> 1) * 1024u + ((i & 1) ? coff1 + 512u : coff0), ok ? (const void*)src
+                                                                                         : (const void*)P.C,
+                    ok ? 16u : 0u);
+      }
+    };
+    // L2 prefetch of this thread's 128-column row segment of tile t
+    auto prefetch_c = [&](int t) {
+      if (t >= ntiles || !P.vec_ok) return;
+      const int r = (t % P.tiles_m) * TC_BM + q * 32 + lane;
+      const int c0 = (t / P.tiles_m) * TC_BN + half * 128;
+      const int nc = min(128, P.n - c0);
+      if (r >= P.m || nc < 4) return;
+      l2_prefetch_bulk(P.C + (int64_t)r * P.ldc + c0, (uint32_t)(nc & ~3) * 4u);
+    };
+    // the load side runs TC_CBUF - 1 chunks ahead of the drain side
+    int lt = blockIdx.x, lcc = 0, lslot = 0;
+    View lv = view_of(lt < ntiles ? lt : 0);
+    auto load_next = [&]() {
+      if (lt < ntiles) load_chunk(lv, lcc, lslot);
+      cpa_commit();  // one group per chunk, empty past the last one
+      if (++lslot == TC_CBUF) lslot = 0;
+      if (++lcc == 4) {
+        lcc = 0;
+        lt += gridDim.x;
+        if (lt < ntiles) lv = view_of(lt);
+      }
+    };
+    prefetch_c(blockIdx.x);
+#pragma unroll 1
+    for (int g = 0; g < TC_CBUF - 1; ++g) load_next();
     int acc = 0;
     uint32_t aph = 0;
+    int slot = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-      const int tm = t % P.tiles_m, tn = t / P.tiles_m;
+      prefetch_c(t + gridDim.x);
+      const View dv = view_of(t);
       int okw = 1;
       if (lane == 0) okw = mbar_wait(bar_tfull + 8 * acc, aph, P.status, abort_flag) ? 1 : 0;
       okw = __shfl_sync(0xffffffffu, okw, 0);
       if (!okw) break;
       tc_fence_after();
-      const int row = tm * TC_BM + q * 32 + lane;
-      float* crow = P.C + (int64_t)row * P.ldc;
-      const bool rok = row < P.m;
 #pragma unroll 1
-      for (int cc = 0; cc < 128; cc += 32) {
-        const int col0 = half * 128 + cc;
+      for (int cc = 0; cc < 4; ++cc) {
+        load_next();
         uint32_t v[32];
-        const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * TC_BN + col0);
+        const uint32_t taddr =
+            tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * TC_BN + half * 128 + cc * 32);
         TMEM_LD_X32(taddr, v);
+        cpa_wait<TC_CBUF - 1>();  // this thread's pieces of the chunk have landed
         tmem_wait_ld();
-        const int gc0 = tn * TC_BN + col0;
-        if (rok) {
-          if (P.vec_ok && gc0 + 32 <= P.n) {
-            float4* cp = reinterpret_cast<float4*>(crow + gc0);
-            float4 cv[8];
+        __syncwarp();  // ... and every other lane's
+        float4* buf = cbuf_p + slot * (TC_CHUNK_BYTES / 16);
+        // row `lane`: C -= accumulator in shared memory
 #pragma unroll
-            for (int j = 0; j < 8; ++j) cv[j] = cp[j];
+        for (int u = 0; u < 8; ++u) {
+          float4* p = buf + lane * 8 + (u ^ (lane & 7));
+          float4 c = *p;
+          c.x -= __uint_as_float(v[4 * u + 0]);
+          c.y -= __uint_as_float(v[4 * u + 1]);
+          c.z -= __uint_as_float(v[4 * u + 2]);
+          c.w -= __uint_as_float(v[4 * u + 3]);
+          *p = c;
+        }
+        __syncwarp();
+        const unsigned char* bb = reinterpret_cast<const unsigned char*>(buf);
+        const bool full = dv.vec && cc * 32 + 4 <= dv.cols;
+        if (full && dv.rows >= 29) {
+          // whole chunk in range for this lane
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              cv[j].x -= __uint_as_float(v[4 * j + 0]);
-              cv[j].y -= __uint_as_float(v[4 * j + 1]);
-              cv[j].z -= __uint_as_float(v[4 * j + 2]);
-              cv[j].w -= __uint_as_float(v[4 * j + 3]);
+          for (int i = 0; i < 8; ++i) {
+            const float4 a = *reinterpret_cast<const float4*>(bb + (i >> 1) * 1024 + ((i & 1) ? coff1 + 512 : coff0));
+            *reinterpret_cast<float4*>(dv.p + i * ldc4 + cc * 32) = a;
+          }
+        } else {
+          const int gcols = dv.cols - cc * 32;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            if (4 * i >= dv.rows) break;
+            const float4 a = *reinterpret_cast<const float4*>(bb + (i >> 1) * 1024 + ((i & 1) ? coff1 + 512 : coff0));
+            float* cp = dv.p + i * ldc4 + cc * 32;
+            if (full) {
+              *reinterpret_cast<float4*>(cp) = a;
+            } else {
+              // the buffer held zeros here: a = -accumulator, and C + a == C - accumulator
+              if (0 < gcols) cp[0] += a.x;
+              if (1 < gcols) cp[1] += a.y;
+              if (2 < gcols) cp[2] += a.z;
+              if (3 < gcols) cp[3] += a.w;
             }
-#pragma unroll
-            for (int j = 0; j < 8; ++j) cp[j] = cv[j];
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-              if (gc0 + j < P.n) crow[gc0 + j] -= __uint_as_float(v[j]);
           }
         }
+        __syncwarp();  // the buffer is refilled by a later load
+        if (++slot == TC_CBUF) slot = 0;
       }
       tc_fence_before();
       __syncwarp();
@@ -233,6 +331,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         aph ^= 1u;
       }
     }
+    cpa_wait<0>();  // no copy may land after the CTA exits
   }
   tc_fence_before();
   __syncthreads();
@@ -305,7 +404,8 @@ __global__ void cast_b_kernel(const float* __restrict__ U12, int64_t ld, int n, 
 cudaError_t launch_cast_operands(int kind, const float* L21, const float* U12, int64_t ldw, int m, int n, int k,
                                  void* Aop, void* Bop, int kpad, int* status, cudaStream_t st) {
   if (m <= 0 || n <= 0) return cudaSuccess;
-  if (m > 65535 * 64 || (kpad % 64) != 0 || k > kpad) return cudaErrorInvalidValue;
+  // the A cast runs one grid row per operand row
+  if (m > 65535 || (kpad % 64) != 0 || k > kpad) return cudaErrorInvalidValue;
   dim3 ga((unsigned)cdiv(kpad, 256), (unsigned)m);
   dim3 gb_((unsigned)cdiv(n, 32), (unsigned)cdiv(kpad, 32));
   if (kind == 1) {

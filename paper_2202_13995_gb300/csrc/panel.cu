@@ -557,11 +557,27 @@ __global__ void __launch_bounds__(256) trsm_lower_kernel(const T* L, T* X, int64
         if (t < bw) Xs[(b0 + t) * 32 + lane] = x[t];
     }
     __syncthreads();
-    for (int r = b0 + bw + warp; r < w; r += 8) {
-      const T lv = lane < bw ? L[(int64_t)r * ldw + b0 + lane] : T(0);
-      T acc = Xs[r * 32 + lane];
-      for (int t = 0; t < bw; ++t) acc -= __shfl_sync(0xffffffffu, lv, t) * Xs[(b0 + t) * 32 + lane];
-      Xs[r * 32 + lane] = acc;
+    // rows below the block: each warp takes every 8th row, eight rows per
+    // batch so that their L loads are in flight together
+    T xb[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) xb[t] = (t < bw) ? Xs[(b0 + t) * 32 + lane] : T(0);
+    for (int r0 = b0 + bw + warp; r0 < w; r0 += 64) {
+      T lv[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = r0 + 8 * i;
+        lv[i] = (r < w && lane < bw) ? L[(int64_t)r * ldw + b0 + lane] : T(0);
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int r = r0 + 8 * i;
+        if (r >= w) break;
+        T acc = Xs[r * 32 + lane];
+#pragma unroll
+        for (int t = 0; t < 32; ++t) acc -= __shfl_sync(0xffffffffu, lv[i], t) * xb[t];
+        Xs[r * 32 + lane] = acc;
+      }
     }
     __syncthreads();
   }

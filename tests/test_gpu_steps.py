@@ -155,6 +155,31 @@ def test_gemm_tensor_core(ctx, prec, m, n, k):
     assert ctx.status() == 0
 
 
+@pytest.mark.parametrize("m,n,k,ldc", [(257, 301, 64, 304), (130, 515, 48, 520), (600, 1027, 256, 1032)])
+def test_gemm_tensor_core_strided_ragged(ctx, m, n, k, ldc):
+    """C a view with 16-byte aligned rows and a width that is not a multiple
+    of 4 (the last columns take the element-wise path); the columns past n
+    are untouched."""
+    import torch
+    rng = np.random.default_rng(m + n + k)
+    Cfull = rng.uniform(-1, 1, (m, ldc)).astype(np.float32)
+    Am = rng.uniform(-1, 1, (m, k)).astype(np.float32)
+    Bm = rng.uniform(-1, 1, (k, n)).astype(np.float32)
+    ld = max(k, n)
+    Ab = np.zeros((m, ld), np.float32); Ab[:, :k] = Am
+    Bb = np.zeros((k, ld), np.float32); Bb[:, :n] = Bm
+    Cd = _rm(Cfull, torch.float32)
+    Ad, Bd = _rm(Ab, torch.float32), _rm(Bb, torch.float32)
+    ctx.step_gemm(Cd[:, :n], Ad[:, :k], Bd[:, :n], "bf16")
+    Ar, Br = O.round_bf16(Am), O.round_bf16(Bm)
+    want = O.gemm_update(Cfull[:, :n].astype(np.float64), Ar, Br)
+    got = Cd.cpu().numpy()
+    bound = (k + 4) * EPS32 * (np.abs(Cfull[:, :n]) + np.abs(Ar) @ np.abs(Br))
+    assert np.all(np.abs(got[:, :n].astype(np.float64) - want) <= bound)
+    assert np.array_equal(got[:, n:], Cfull[:, n:])
+    assert ctx.status() == 0
+
+
 def test_gemm_fp16_overflow_is_reported(ctx):
     import torch
     from paper_2202_13995_gb300 import lu
