@@ -56,6 +56,8 @@ WORKLOADS = {
     # the batched configuration: 4096 systems, n ~ U{32..512}, 1-8 right-hand
     # sides, A + n I, FP32 factor + FP64 refinement, one persistent launch
     "batched_4096": dict(count=4096, nmin=32, nmax=512, kmax=8, seed=5, prec="f32"),
+    # a small case of the same kernel for profiling captures
+    "batched_512": dict(count=512, nmin=32, nmax=512, kmax=8, seed=5, prec="f32"),
     # the served configuration: Poisson arrivals, n log-uniform 64..8192, 1-16
     # right-hand sides, 30% repeat-RHS on resident factors, FP16 factor + FP64
     # refinement, admission by a 120 GB HBM budget
@@ -379,7 +381,7 @@ def batched_measure(ctx, stream, cfg: dict, steps: int, warmup: int, tune: bool 
     ms = e0.elapsed_time(e1) / steps
     flops = float(sum(2.0 / 3.0 * float(n) ** 3 + 2.0 * float(n) ** 2 * float(k) for n, k in zip(ns, ks)))
     shape = bt.shape()
-    out = {"workload": "batched_4096", "systems": cnt, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+    out = {"workload": f"batched_{cnt}", "systems": cnt, "value": flops / (ms * 1e-3) / 1e12, "unit": "TFLOP/s",
            "ms_per_step": ms, "solves_per_s": cnt / (ms * 1e-3), "all_converged": bool((info == 0).all().item()),
            "max_scaled_residual": float(resid.max().item()), "max_refine_iters": int(iters.max().item()),
            "launch_shape": {"threads": shape[0], "ctas_per_sm": shape[1]}, "launches": ctx.launch_count() - l0,
@@ -635,7 +637,7 @@ def main():
                 "config": {"workload": args.workload}, "served": r}
         print(json.dumps(line), flush=True)
         return 0
-    if args.workload == "batched_4096":
+    if args.workload.startswith("batched_"):
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the batched workload has no CPU reference arm; "
                               "the oracle solves each system in tests/test_gpu_batched.py"}))
@@ -650,7 +652,7 @@ def main():
         line = {"metric": METRIC, "value": r["value"], "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64refine", "data": "synthetic",
-                "config": {"workload": "batched_4096", "systems": cfg["count"]}, "batched": r,
+                "config": {"workload": args.workload, "systems": cfg["count"]}, "batched": r,
                 "gpu_launches": r["launches"]}
         print(json.dumps(line), flush=True)
         return 0

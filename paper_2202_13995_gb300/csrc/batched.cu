@@ -48,13 +48,14 @@ struct BatchSmem {
   float Ld[BT_NB][BT_NB + 1];
   float redf[32];
   int redi[32];
-  double redd[3 * BT_RHSMAX * 32];
+  double redd[3 * BT_RHSMAX * 32];  // >= 16 warps x 32 + 32
   int misc[8];
 };
 // refinement phase views (alias P/Us): x (FP64), r (FP64), y (FP32), 8 x 512 each
 static_assert(sizeof(float) * BT_NB * (BT_NMAX + BT_CW) >=
                   2 * sizeof(double) * BT_RHSMAX * BT_NMAX + sizeof(float) * BT_RHSMAX * BT_NMAX,
               "refinement vectors must fit in the factor-phase buffers");
+static_assert(3 * BT_RHSMAX * 32 >= 16 * 32 + 32, "block_max_many needs 16 warps x 32 + 32 slots");
 
 __device__ __forceinline__ void block_argmax_f(float& v, int& i, BatchSmem& sm, int nt) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -80,9 +81,21 @@ __device__ int bt_factor(float* W, int ld, int n, BatchSmem& sm, int* status) {
   for (int k0 = 0; k0 < n; k0 += BT_NB) {
     const int kb = min(BT_NB, n - k0);
     const int m = n - k0;
-    for (int e = tid; e < m * BT_NB; e += NT) {
-      const int r = e / BT_NB, c = e % BT_NB;
-      if (c < kb) sm.P[c][r] = W[(int64_t)sm.perm[k0 + r] * ld + k0 + c];
+    // thread = row, four columns per load (rows and k0 are 16-byte aligned):
+    // the column-major panel is then written without bank conflicts
+    for (int e = tid; e < m * (BT_NB / 4); e += NT) {
+      const int r = e % m, c = (e / m) * 4;
+      if (c >= kb) continue;
+      const float* src = W + (int64_t)sm.perm[k0 + r] * ld + k0 + c;
+      if (c + 4 <= kb) {
+        const float4 v = *reinterpret_cast<const float4*>(src);
+        sm.P[c][r] = v.x;
+        sm.P[c + 1][r] = v.y;
+        sm.P[c + 2][r] = v.z;
+        sm.P[c + 3][r] = v.w;
+      } else {
+        for (int x = 0; c + x < kb; ++x) sm.P[c + x][r] = src[x];
+      }
     }
     __syncthreads();
     for (int j = 0; j < kb; ++j) {
@@ -116,20 +129,35 @@ __device__ int bt_factor(float* W, int ld, int n, BatchSmem& sm, int* status) {
       }
       __syncthreads();
     }
-    for (int e = tid; e < m * BT_NB; e += NT) {
-      const int r = e / BT_NB, c = e % BT_NB;
-      if (c < kb) W[(int64_t)sm.perm[k0 + r] * ld + k0 + c] = sm.P[c][r];
+    for (int e = tid; e < m * (BT_NB / 4); e += NT) {
+      const int r = e % m, c = (e / m) * 4;
+      if (c >= kb) continue;
+      float* dst = W + (int64_t)sm.perm[k0 + r] * ld + k0 + c;
+      if (c + 4 <= kb) {
+        *reinterpret_cast<float4*>(dst) = make_float4(sm.P[c][r], sm.P[c + 1][r], sm.P[c + 2][r], sm.P[c + 3][r]);
+      } else {
+        for (int x = 0; c + x < kb; ++x) dst[x] = sm.P[c + x][r];
+      }
     }
     __syncthreads();
     // U12 (top blocks) and the inner update, in column chunks
     for (int c0 = k0 + kb; c0 < n; c0 += BT_CW) {
       const int cw = min(BT_CW, n - c0);
       for (int c = tid; c < cw; c += NT) {
-        for (int j = 0; j < kb; ++j) {
-          float v = W[(int64_t)sm.perm[k0 + j] * ld + c0 + c];
-          for (int i = 0; i < j; ++i) v -= sm.P[i][j] * sm.Us[i][c];
-          sm.Us[j][c] = v;
-          W[(int64_t)sm.perm[k0 + j] * ld + c0 + c] = v;
+        // the column's kb entries are loaded together, then solved in registers
+        float v[BT_NB];
+#pragma unroll
+        for (int j = 0; j < BT_NB; ++j) v[j] = j < kb ? W[(int64_t)sm.perm[k0 + j] * ld + c0 + c] : 0.0f;
+#pragma unroll
+        for (int j = 1; j < BT_NB; ++j)
+#pragma unroll
+          for (int i = 0; i < j; ++i) v[j] -= sm.P[i][j] * v[i];
+#pragma unroll
+        for (int j = 0; j < BT_NB; ++j) {
+          if (j < kb) {
+            sm.Us[j][c] = v[j];
+            W[(int64_t)sm.perm[k0 + j] * ld + c0 + c] = v[j];
+          }
         }
       }
       __syncthreads();
@@ -139,13 +167,24 @@ __device__ int bt_factor(float* W, int ld, int n, BatchSmem& sm, int* status) {
       const int rt = (rows + 3) / 4, ct = (cw + 3) / 4;
       for (int t = tid; t < rt * ct; t += NT) {
         const int r0 = kb + (t / ct) * 4, cc = (t % ct) * 4;
+        // the tile's entries of W first: their latency runs under the products
+        float cw4[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float* wr = W + (int64_t)sm.perm[k0 + min(r0 + i, m - 1)] * ld + c0 + cc;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) cw4[i][q] = (r0 + i < m && cc + q < cw) ? wr[q] : 0.0f;
+        }
         float acc[4][4] = {};
+        // kb = 32 here (the last block has no rows below it), so r0 and cc
+        // are multiples of 4: one 16-byte shared load per operand and k.
+        // Lanes past m or cw read stale entries into rows / columns of acc
+        // that are never stored.
         for (int k = 0; k < kb; ++k) {
-          float a[4], b[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) a[i] = (r0 + i < m) ? sm.P[k][r0 + i] : 0.0f;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) b[q] = (cc + q < cw) ? sm.Us[k][cc + q] : 0.0f;
+          const float4 a4 = *reinterpret_cast<const float4*>(&sm.P[k][r0]);
+          const float4 b4 = *reinterpret_cast<const float4*>(&sm.Us[k][cc]);
+          const float a[4] = {a4.x, a4.y, a4.z, a4.w};
+          const float b[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -157,7 +196,7 @@ __device__ int bt_factor(float* W, int ld, int n, BatchSmem& sm, int* status) {
           float* wr = W + (int64_t)sm.perm[k0 + r0 + i] * ld + c0 + cc;
 #pragma unroll
           for (int q = 0; q < 4; ++q)
-            if (cc + q < cw) wr[q] -= acc[i][q];
+            if (cc + q < cw) wr[q] = cw4[i][q] - acc[i][q];
         }
       }
       __syncthreads();
@@ -241,16 +280,58 @@ __device__ void bt_solve(const float* W, int ld, int n, int nr, float* y, BatchS
   }
 }
 
-__device__ __forceinline__ double block_max_d(double v, double* red, int nt) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// r = b - A x in FP64 for the rows of this thread (A FP64 column-major), with
+// the column maxima of |r|, |x|, |b| and, on the first pass, the row sums of |A|.
+template <int NR, bool FIRST>
+__device__ __forceinline__ void bt_resid_rows(const BatchDesc& d, int n, const double* xs, double* rs, double& amax,
+                                              double* rmax, double* xmax, double* bmax, int tid, int nt) {
+  for (int i = tid; i < n; i += nt) {
+    double acc[NR];
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    for (int q = 0; q < NR; ++q) {
+      acc[q] = d.B[(int64_t)q * d.ldb + i];
+      bmax[q] = fmax(bmax[q], fabs(acc[q]));
+    }
+    double asum = 0.0;
+    for (int j = 0; j < n; ++j) {
+      const double a = d.A[(int64_t)j * d.lda + i];
+      if (FIRST) asum += fabs(a);
+#pragma unroll
+      for (int q = 0; q < NR; ++q) acc[q] = fma(-a, xs[q * BT_NMAX + j], acc[q]);
+    }
+    amax = fmax(amax, asum);
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      rs[q * BT_NMAX + i] = acc[q];
+      rmax[q] = fmax(rmax[q], fabs(acc[q]));
+      xmax[q] = fmax(xmax[q], fabs(xs[q * BT_NMAX + i]));
+    }
+  }
+}
+
+// Block-wide maxima of 3 nr (+1) per-thread values in one shared-memory round:
+// returns a shared array (valid until the next call) with rmax[0..nr),
+// xmax[0..nr), bmax[0..nr) and, if with_a, amax.  Maxima do not depend on the
+// order of reduction.
+__device__ __forceinline__ const double* block_max_many(const double* rmax, const double* xmax, const double* bmax,
+                                                        double amax, int nr, bool with_a, double* red, int nt) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int K = 3 * nr + (with_a ? 1 : 0);  // <= 25
+  __syncthreads();  // the previous results have been read
+  for (int k = 0; k < K; ++k) {
+    double v = k < nr ? rmax[k] : k < 2 * nr ? xmax[k - nr] : k < 3 * nr ? bmax[k - 2 * nr] : amax;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if (lane == 0) red[warp * 32 + k] = v;
+  }
   __syncthreads();
-  if (lane == 0) red[warp] = v;
+  if ((int)threadIdx.x < K) {
+    double m = 0.0;
+    for (int w = 0; w < nt / 32; ++w) m = fmax(m, red[w * 32 + threadIdx.x]);
+    red[16 * 32 + threadIdx.x] = m;
+  }
   __syncthreads();
-  double r = 0.0;
-  for (int w = 0; w < nt / 32; ++w) r = fmax(r, red[w]);
-  return r;
+  return red + 16 * 32;
 }
 
 template <int NT>
@@ -324,37 +405,38 @@ __global__ void __launch_bounds__(NT) batched_kernel(const BatchDesc* __restrict
 #pragma unroll
       for (int q = 0; q < BT_RHSMAX; ++q) rmax[q] = xmax[q] = bmax[q] = 0.0;
       double amax = 0.0;
-      for (int i = tid; i < n; i += NT) {
-        double acc[BT_RHSMAX];
-#pragma unroll
-        for (int q = 0; q < BT_RHSMAX; ++q) acc[q] = q < nr ? d.B[(int64_t)q * d.ldb + i] : 0.0;
-#pragma unroll
-        for (int q = 0; q < BT_RHSMAX; ++q) bmax[q] = fmax(bmax[q], fabs(acc[q]));
-        double asum = 0.0;
-        for (int j = 0; j < n; ++j) {
-          const double a = d.A[(int64_t)j * d.lda + i];
-          if (it == 0) asum += fabs(a);
-#pragma unroll
-          for (int q = 0; q < BT_RHSMAX; ++q)
-            if (q < nr) acc[q] = fma(-a, xs[q * BT_NMAX + j], acc[q]);
-        }
-        amax = fmax(amax, asum);
-#pragma unroll
-        for (int q = 0; q < BT_RHSMAX; ++q) {
-          if (q < nr) {
-            rs[q * BT_NMAX + i] = acc[q];
-            rmax[q] = fmax(rmax[q], fabs(acc[q]));
-            xmax[q] = fmax(xmax[q], fabs(xs[q * BT_NMAX + i]));
-          }
-        }
+      // one instantiation per right-hand-side count, so that no FP64
+      // operation is issued for absent columns
+#define GB_RESID_CASE(NRC)                                                              \
+  case NRC:                                                                             \
+    if (it == 0)                                                                        \
+      bt_resid_rows<NRC, true>(d, n, xs, rs, amax, rmax, xmax, bmax, tid, NT);          \
+    else                                                                                \
+      bt_resid_rows<NRC, false>(d, n, xs, rs, amax, rmax, xmax, bmax, tid, NT);         \
+    break;
+      switch (nr) {
+        GB_RESID_CASE(1)
+        GB_RESID_CASE(2)
+        GB_RESID_CASE(3)
+        GB_RESID_CASE(4)
+        GB_RESID_CASE(5)
+        GB_RESID_CASE(6)
+        GB_RESID_CASE(7)
+        GB_RESID_CASE(8)
+        default:
+          break;
       }
-      if (it == 0) anorm = block_max_d(amax, sm.redd, NT);
+#undef GB_RESID_CASE
+      // all column maxima (and max_i sum_j |a_ij| on the first pass) in one
+      // block reduction: value k < nr is |r_k|, then |x_k|, |b_k|, ||A||
+      const double* cm = block_max_many(rmax, xmax, bmax, amax, nr, it == 0, sm.redd, NT);
+      if (it == 0) anorm = cm[3 * nr];
       worst = 0.0;
       unsigned still = 0u;
       for (int q = 0; q < nr; ++q) {
-        const double rn = block_max_d(rmax[q], sm.redd, NT);
-        const double xn = block_max_d(xmax[q], sm.redd, NT);
-        const double bn = block_max_d(bmax[q], sm.redd, NT);
+        const double rn = cm[q];
+        const double xn = cm[nr + q];
+        const double bn = cm[2 * nr + q];
         const double den = eps * (anorm * xn + bn) * (double)n;
         const double sc = den > 0.0 ? rn / den : (rn > 0.0 ? INFINITY : 0.0);
         worst = fmax(worst, sc);
