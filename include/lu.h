@@ -138,6 +138,16 @@ int lu_refine(lu_fact f, const double *dA, int lda, const double *dB, int ldb, d
 int lu_scaled_residual(lu_ctx ctx, int n, int nrhs, const double *dA, int lda, const double *dX, int ldx,
                        const double *dB, int ldb, double *out);
 
+/* The infinity norms behind the scaled residual, per column q of dX:
+ * out[4q] = ||b - A x||, out[4q+1] = ||A||, out[4q+2] = ||x||, out[4q+3] =
+ * ||b|| (r computed in FP64 on the device; out is host memory, 4*nrhs
+ * doubles).  They give the HPL form above and the paper's own shape of the
+ * check, ||r|| / (n ||b|| eps) (arxiv 2202.13995, section "High Performance
+ * Linpack", where its printed formula has no residual in it and is read this
+ * way).  Synchronizes.  Errors as lu_scaled_residual. */
+int lu_residual_norms(lu_ctx ctx, int n, int nrhs, const double *dA, int lda, const double *dX, int ldx,
+                      const double *dB, int ldb, double *out);
+
 /* Device bytes that lu_factor (block width nb, 0 = default) plus lu_refine
  * with nrhs right-hand sides allocate for an n x n system on the current
  * device (0 on an invalid argument).  For memory budgeting. */

@@ -699,13 +699,10 @@ extern "C" int lu_refine(lu_fact f, const double* dA, int lda, const double* dB,
   return result;
 }
 
-extern "C" int lu_scaled_residual(lu_ctx c, int n, int nrhs, const double* dA, int lda, const double* dX, int ldx,
-                                  const double* dB, int ldb, double* out) {
-  if (!c) return -1;
-  if (n < 0) return -2;
-  if (nrhs < 0) return -3;
-  if (!out) return -10;
-  if (n == 0 || nrhs == 0) return LU_OK;
+// ||r||, ||A||, ||x||, ||b|| (infinity norms, r = b - A x in FP64) per column
+// into norms[4 q .. 4 q + 3].
+static int residual_norms(lu_ctx c, int n, int nrhs, const double* dA, int lda, const double* dX, int ldx,
+                          const double* dB, int ldb, double* norms) {
   const size_t need = residual_partial_bytes(n, nrhs > 32 ? 32 : nrhs) + 256;
   void* ws = nullptr;
   int rc = dalloc(c, &ws, need);
@@ -722,11 +719,43 @@ extern "C" int lu_scaled_residual(lu_ctx c, int n, int nrhs, const double* dA, i
     if (rc) break;
     rc = read_status(c);
     if (rc) break;
-    for (int q = 0; q < nr; ++q)
-      out[q0 + q] = hpl_scaled(n, c->h_norms[4 + q], c->h_norms[0], c->h_norms[4 + nr + q], c->h_norms[4 + 2 * nr + q]);
+    for (int q = 0; q < nr; ++q) {
+      double* o = norms + 4 * (size_t)(q0 + q);
+      o[0] = c->h_norms[4 + q];
+      o[1] = c->h_norms[0];
+      o[2] = c->h_norms[4 + nr + q];
+      o[3] = c->h_norms[4 + 2 * nr + q];
+    }
   }
   dfree(c, ws);
   return rc;
+}
+
+extern "C" int lu_scaled_residual(lu_ctx c, int n, int nrhs, const double* dA, int lda, const double* dX, int ldx,
+                                  const double* dB, int ldb, double* out) {
+  if (!c) return -1;
+  if (n < 0) return -2;
+  if (nrhs < 0) return -3;
+  if (!out) return -10;
+  if (n == 0 || nrhs == 0) return LU_OK;
+  double* norms = new (std::nothrow) double[4 * (size_t)nrhs];
+  if (!norms) return LU_ENOMEM;
+  const int rc = residual_norms(c, n, nrhs, dA, lda, dX, ldx, dB, ldb, norms);
+  if (rc == LU_OK)
+    for (int q = 0; q < nrhs; ++q)
+      out[q] = hpl_scaled(n, norms[4 * q], norms[4 * q + 1], norms[4 * q + 2], norms[4 * q + 3]);
+  delete[] norms;
+  return rc;
+}
+
+extern "C" int lu_residual_norms(lu_ctx c, int n, int nrhs, const double* dA, int lda, const double* dX, int ldx,
+                                 const double* dB, int ldb, double* out) {
+  if (!c) return -1;
+  if (n < 0) return -2;
+  if (nrhs < 0) return -3;
+  if (!out) return -10;
+  if (n == 0 || nrhs == 0) return LU_OK;
+  return residual_norms(c, n, nrhs, dA, lda, dX, ldx, dB, ldb, out);
 }
 
 // ------------------------------------------------------------------ step-level entry points

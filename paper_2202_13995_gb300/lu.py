@@ -27,7 +27,7 @@ LU_FACTOR_NOPIV, LU_FACTOR_OZAKI = 1, 2
 
 EXPORTED = [
     "lu_create", "lu_destroy", "lu_strerror", "lu_factor", "lu_fact_info", "lu_fact_ipiv", "lu_fact_lu",
-    "lu_solve", "lu_refine", "lu_scaled_residual", "lu_fact_free",
+    "lu_solve", "lu_refine", "lu_scaled_residual", "lu_residual_norms", "lu_fact_free",
     "lu_step_panel", "lu_step_trsm", "lu_step_gemm", "lu_ctx_status", "lu_device_sm_count", "lu_build_tag",
     "lu_profile_enable", "lu_profile_read", "lu_launch_count", "lu_step_panel_static",
     "lu_batch_create", "lu_batch_run", "lu_batch_shape", "lu_batch_free", "lu_solve_batched",
@@ -84,6 +84,7 @@ def load():
             "lu_solve": (I, [P, I, P, I]),
             "lu_refine": (I, [P, P, I, P, I, P, I, I, D, I, IP, DP]),
             "lu_scaled_residual": (I, [P, I, I, P, I, P, I, P, I, DP]),
+            "lu_residual_norms": (I, [P, I, I, P, I, P, I, P, I, DP]),
             "lu_fact_free": (None, [P]),
             "lu_step_panel": (I, [P, I, I, I, P, I, P, P]),
             "lu_step_trsm": (I, [P, I, I, I, P, I, P, I]),
@@ -252,6 +253,16 @@ class Context:
         _check(load().lu_scaled_residual(self._h, A.shape[0], nrhs, C.c_void_p(pa), lda, C.c_void_p(px), ldx,
                                          C.c_void_p(pb), ldb, out), "lu_scaled_residual")
         return np.array(out[:nrhs])
+
+    def residual_norms(self, A, X, B) -> np.ndarray:
+        """(nrhs, 4) array: ||b - A x||, ||A||, ||x||, ||b|| (infinity norms) per column."""
+        pa, lda, _ = _colmajor(A, "A")
+        px, ldx, nrhs = _colmajor(X, "X")
+        pb, ldb, _ = _colmajor(B, "B")
+        out = (C.c_double * max(1, 4 * nrhs))()
+        _check(load().lu_residual_norms(self._h, A.shape[0], nrhs, C.c_void_p(pa), lda, C.c_void_p(px), ldx,
+                                        C.c_void_p(pb), ldb, out), "lu_residual_norms")
+        return np.array(out[:4 * nrhs]).reshape(nrhs, 4)
 
     # ---- step-level entry points (row-major operands)
     def step_panel(self, P, ipiv, info, prec="f64"):

@@ -98,6 +98,36 @@ def test_multi_rhs_f64(ctx, nrhs):
     assert np.all(O.scaled_residual(A, Xg, B) < 16.0)
 
 
+def test_residual_norms_against_oracle(ctx):
+    """lu_residual_norms: the four infinity norms per column against the
+    oracle's, and both checks (HPL's and the paper's shape) built from them."""
+    n, nrhs = 900, 3
+    A = I.hpl_matrix(n, 31)
+    B = I.hpl_rhs(n, nrhs, 32)
+    f = ctx.factor(_dev(A), "f64", 64)
+    X = _dev(B)
+    f.solve_(X)
+    Xg = X.cpu().numpy()
+    got = ctx.residual_norms(_dev(A), X, _dev(B))
+    assert got.shape == (nrhs, 4)
+    R = O.residual(A, Xg, B)
+    for q in range(nrhs):
+        rn, an, xn, bn = got[q]
+        ano = O.norm_inf(A)  # row sums: another summation order on the device
+        assert abs(an - ano) <= n * 2.0 ** -53 * ano
+        assert xn == O.norm_inf(Xg[:, q])  # maxima are exact
+        assert bn == O.norm_inf(B[:, q])
+        # r is summed in another order on the device: same magnitude, FP64 rounding apart
+        ro = O.norm_inf(R[:, q])
+        assert abs(rn - ro) <= 4 * n * 2.0 ** -53 * an * xn
+        hpl = O.scaled_residual_from_norms(n, rn, an, xn, bn)
+        assert abs(hpl - O.scaled_residual_from_norms(n, ro, an, xn, bn)) <= 4.0
+        assert hpl < 16.0
+        assert O.paper_residual(n, rn, bn) >= 0.0
+    assert np.allclose(ctx.scaled_residual(_dev(A), X, _dev(B)),
+                       [O.scaled_residual_from_norms(n, *got[q]) for q in range(nrhs)], rtol=1e-12, atol=0)
+
+
 def test_all_ones_closed_form(ctx):
     """The paper's validation idea: b = A * ones gives x = ones."""
     n = 1200
