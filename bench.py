@@ -488,7 +488,7 @@ def run_ours(args, cfg, wname):
     r = timed_solves(ctx, stream, cfg, nb, args.steps, args.warmup, rank, ws, ClockSampler(local))
     A, B = r["A"], r["B"]
     ms, prof, launches = r["ms"], r["prof"], r["launches"]
-    res, ck = r["res"], r["clocks"]
+    res, ck, res_paper = r["res"], r["clocks"], r["res_paper"]
     ozaki = bool(cfg.get("ozaki", False))
     roofline = gemm_roofline(prof, n, nb, prec, args.steps, peaks, wname, ozaki)
 
@@ -600,10 +600,11 @@ def run_ours(args, cfg, wname):
             "vs_baseline": None, "dtype": ("f64 (bf16-split products)" if ozaki else "f64") if not mixed else f"{prec}+f32acc+f64refine", "data": "synthetic",
             "config": {"workload": wname, "n": n, "nb": nb or "auto", "nrhs": nrhs, "precision": prec,
                        "matrix": "uniform[-0.5,0.5]" + (f" + {cfg['shift']}*n*I" if shift else ""),
-                       "l2": f"inputs larger than L2 (A = {n * n * 8 / 2 ** 30:.1f} GiB FP64)",
+                       "l2": (f"inputs larger than L2 (A = {n * n * 8 / 2 ** 30:.1f} GiB FP64)" if n * n * 8 > 129e6
+                              else f"inputs smaller than L2 (A = {n * n * 8 / 2 ** 20:.0f} MiB FP64), not flushed"),
                        "parallelism": "replicas" if ws > 1 else "1 gpu"},
             "scaled_residual": res,
-            "paper_residual": r["res_paper"],
+            "paper_residual": res_paper,
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,

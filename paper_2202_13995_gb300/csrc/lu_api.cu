@@ -464,6 +464,11 @@ extern "C" int lu_factor_ex(lu_ctx c, int n, const double* dA, int lda, lu_prec 
   f->rowid = f->ipiv + nn;
   f->info_d = f->rowid + nn;
   panel_scratch_carve(&f->ps, f->panel_mem, gmax, 32, f->nb, f->tsize);
+  // With the lookahead, the FP32 panel shares the GPU with the update of the
+  // rest of the trailing matrix: 5/8 of the SMs for the panel (measured at
+  // n = 32768: 96 of 152 SMs, 238 ms per solve against 256 with 64 and 265
+  // with 112, where the update runs short of SMs).
+  if ((prec == LU_BF16 || prec == LU_FP16) && c->lookahead) f->ps.gtarget = (c->dev.sm_count * 5 + 7) / 8;
   solve_scratch_carve(&f->ss, f->solve_mem, nn, f->tsize);
   if (prec != LU_F64) {
     // FP32 factors: inverted diagonal blocks for the correction solves
