@@ -194,23 +194,40 @@ def gemm_roofline(prof: dict, n: int, nb: int, prec: str, steps: int, peaks: dic
     nbx = nb or default_nb(n, prec)
     kpad = -(-nbx // 64) * 64
     flops = bytes_ = 0.0
+    dram_alg = 0.0  # algorithmic DRAM bytes of the kernel's own data type, all launches of one step
+    nlaunch = 0
     for k in range(0, n, nbx):
         w = min(nbx, n - k)
         rest = n - k - w
         if rest > 0:
             flops += 2.0 * rest * rest * w
             bytes_ += 8.0 * rest * rest + 2.0 * (2 * rest) * kpad
+            if ozaki:  # FP64 C read + write, 8 BF16 slices of both operands
+                dram_alg += 16.0 * rest * rest + 16.0 * (2 * rest) * kpad
+            elif prec == "f64":  # FP64 C read + write, FP64 operands
+                dram_alg += 16.0 * rest * rest + 8.0 * (2 * rest) * w
+            else:
+                dram_alg += 8.0 * rest * rest + 2.0 * (2 * rest) * kpad
+            nlaunch += 1
     flops *= steps
     bytes_ *= steps
     sec = gemm_ms * 1e-3
-    traffic = None
+    kernel = "oz_gemm_kernel" if ozaki else ("gemm_simt_kernel<double>" if prec == "f64" else "tc_gemm_kernel")
+    # traffic per launch: the ratio of ncu DRAM bytes to algorithmic bytes of
+    # launches captured at full size (profiles/traffic.json, one entry per
+    # kernel), times this step's mean algorithmic bytes per update
+    traffic = traffic_ratio = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
+    if os.path.exists(tpath) and nlaunch:
         try:
-            traffic = json.load(open(tpath)).get(wname)
+            ent = json.load(open(tpath)).get(kernel)
+            if ent:
+                traffic_ratio = float(ent["ratio"])
+                traffic = traffic_ratio * dram_alg / nlaunch
         except Exception:
-            traffic = None
+            traffic = traffic_ratio = None
     base = {"launches": gemm_n, "kernel_ms_per_step": gemm_ms / steps, "traffic": traffic,
+            "traffic_over_algorithmic": traffic_ratio,
             "tflops": flops / sec / 1e12 if sec > 0 else None}
     if ozaki:
         tflops_bf16 = 36.0 * flops / nbx * kpad / sec / 1e12 if sec > 0 else None

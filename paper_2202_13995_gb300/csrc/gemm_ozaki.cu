@@ -241,6 +241,23 @@ struct OzParams {
   int* status;
 };
 
+// Output tile t -> (tm, tn), grouped by OZ_GROUP tile rows: within a group the
+// tiles run down the rows first, so the tiles that the persistent CTAs hold at
+// one time span about OZ_GROUP row blocks and gridDim / OZ_GROUP column
+// blocks.  Their A and B slices (512 KB per block) then stay in L2 while C
+// streams through it, instead of every row block's slices being evicted and
+// read again from HBM for each column block.
+constexpr int OZ_GROUP = 12;
+__device__ __forceinline__ void oz_tile(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
+  const int per_group = OZ_GROUP * tiles_n;
+  const int g = t / per_group;
+  const int first = g * OZ_GROUP;
+  const int gm = min(OZ_GROUP, tiles_m - first);
+  const int r = t - g * per_group;
+  tm = first + r % gm;
+  tn = r / gm;
+}
+
 // 64-bit add of (xh:xl) into (h:l) through the carry flag.
 __device__ __forceinline__ void oz_add64(uint32_t& l, uint32_t& h, uint32_t xl, uint32_t xh) {
   asm("add.cc.u32 %0, %0, %2;\n\taddc.u32 %1, %1, %3;" : "+r"(l), "+r"(h) : "r"(xl), "r"(xh));
@@ -367,7 +384,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       // slice (tile, p + 1) is issued once the B chunks of (p, q = 0) are.
       auto load_a = [&](int tile, int p) -> bool {
         if (!mbar_wait(bar_aempty + 8 * ab, abph ^ 1u, P.status, abort_flag)) return false;
-        const int tm = tile % P.tiles_m;
+        int tm, tn_unused;
+        oz_tile(tile, P.tiles_m, P.tiles_n, tm, tn_unused);
         mbar_expect_tx(bar_afull + 8 * ab, (uint32_t)(P.kchunks * OZ_CHUNK));
         for (int kc = 0; kc < P.kchunks; ++kc)
           tma_load_2d(sA + ab * OZ_ABUF + kc * OZ_CHUNK, &tmA, kc * OZ_BK, p * P.a_rows + tm * OZ_BM,
@@ -381,7 +399,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       };
       if ((int)blockIdx.x < ntiles) ok = load_a(blockIdx.x, 0);
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        const int tn = t / P.tiles_m;
+        int tm_unused, tn;
+        oz_tile(t, P.tiles_m, P.tiles_n, tm_unused, tn);
         for (int p = 0; p < OZ_S && ok; ++p) {
           for (int q = 0; q < OZ_S - p && ok; ++q) {
             for (int kc = 0; kc < P.kchunks; ++kc) {
@@ -540,7 +559,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     uint32_t tph = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-      const int tm = t % P.tiles_m, tn = t / P.tiles_m;
+      int tm, tn;
+      oz_tile(t, P.tiles_m, P.tiles_n, tm, tn);
       const int row = tm * OZ_BM + quarter * 32 + lane;
       const bool rok = row < P.m;
       const int col0 = tn * OZ_BN + half * 64;
