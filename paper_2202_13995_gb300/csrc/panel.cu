@@ -486,34 +486,51 @@ __global__ void __launch_bounds__(256) laswp_kernel(T* W, int64_t ldw, int n, in
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* stage = reinterpret_cast<T*>(smem_raw);
   const int cnt = perm[0];
+  if (cnt == 0) return;  // no row moved (every pivot on the diagonal)
   const int* dst = perm + 1;
   const int* src = perm + 1 + 2 * w;
   const int nout = n - w;
-  const int o = blockIdx.x * CW + (threadIdx.x % CW);
   const int rsub = threadIdx.x / CW;
-  const int c = o < k ? o : o + w;
-  for (int s = rsub; s < cnt; s += RPP)
-    if (o < nout) stage[s * CW + (threadIdx.x % CW)] = W[(int64_t)(k + src[s]) * ldw + c];
   if (blockIdx.x == 0 && rowid != nullptr) {
     int* istage = reinterpret_cast<int*>(stage + (size_t)2 * w * CW);
     for (int s = threadIdx.x; s < cnt; s += 256) istage[s] = rowid[k + src[s]];
     __syncthreads();
     for (int s = threadIdx.x; s < cnt; s += 256) rowid[k + dst[s]] = istage[s];
   }
-  __syncthreads();
-  for (int s = rsub; s < cnt; s += RPP)
-    if (o < nout) W[(int64_t)(k + dst[s]) * ldw + c] = stage[s * CW + (threadIdx.x % CW)];
+  // column chunks, grid-stride
+  for (int q = blockIdx.x; q * CW < nout; q += gridDim.x) {
+    const int o = q * CW + (threadIdx.x % CW);
+    const int c = o < k ? o : o + w;
+    for (int s = rsub; s < cnt; s += RPP)
+      if (o < nout) stage[s * CW + (threadIdx.x % CW)] = W[(int64_t)(k + src[s]) * ldw + c];
+    __syncthreads();
+    for (int s = rsub; s < cnt; s += RPP)
+      if (o < nout) W[(int64_t)(k + dst[s]) * ldw + c] = stage[s * CW + (threadIdx.x % CW)];
+    __syncthreads();  // the stage is refilled by the next chunk
+  }
 }
 
 template <typename T>
 cudaError_t launch_laswp(T* W, int64_t ldw, int n, int k, int w, const int* perm, int* rowid, cudaStream_t st) {
   constexpr int CW = 128 / sizeof(T);
   const int nout = n - w;
-  const int blocks = nout > 0 ? (int)cdiv(nout, CW) : 1;
+  const int chunks = nout > 0 ? (int)cdiv(nout, CW) : 1;
   const size_t smem = (size_t)2 * w * CW * sizeof(T) + 2 * (size_t)w * sizeof(int) + 16;
   auto kern = laswp_kernel<T>;
   cudaError_t e = allow_max_smem((const void*)kern);
   if (e != cudaSuccess) return e;
+  // one resident wave (the launch is short and mostly waits on its first loads)
+  static thread_local int per_sm = -1, sm_count = 0, per_sm_w = -1;
+  if (per_sm < 0 || per_sm_w != w) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    per_sm_w = w;
+  }
+  const int wave = per_sm * sm_count;
+  const int blocks = chunks < wave ? chunks : wave;
   laswp_kernel<T><<<blocks, 256, smem, st>>>(W, ldw, n, k, w, perm, rowid);
   return cudaGetLastError();
 }
