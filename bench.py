@@ -143,16 +143,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def dist_setup():
+def dist_setup(backend: str = "nccl"):
+    """One process per GPU (torchrun): rank, world size, local rank.  The
+    replicas share no data; the group only carries the barrier and the
+    max-over-ranks time (gloo serves the CPU tests of this logic)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
         import torch
         import torch.distributed as dist
         lr = int(os.environ.get("LOCAL_RANK", "0"))
-        torch.cuda.set_device(lr)
-        dist.init_process_group("nccl")
+        if backend == "nccl":
+            torch.cuda.set_device(lr)
+        dist.init_process_group(backend)
         return dist.get_rank(), ws, lr
     return 0, 1, 0
+
+
+def replica_seed(seed: int, rank: int) -> int:
+    """Seed of rank's own system: independent replicas, no data exchanged."""
+    return seed + 1000 * rank
 
 
 def barrier(ws):
@@ -166,7 +175,7 @@ def max_over_ranks(v: float, ws: int) -> float:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
@@ -333,8 +342,8 @@ def timed_solves(ctx, stream, cfg: dict, nb, steps: int, warmup: int, rank: int,
     n, prec, nrhs = cfg["n"], cfg["prec"], cfg["nrhs"]
     shift = cfg["shift"] * n
     mixed = prec != "f64"
-    A = I.hpl_matrix_torch(n, cfg["seed"] + 1000 * rank, diag_shift=shift, device="cuda")
-    B = I.hpl_rhs_torch(n, nrhs, cfg["seed"] + 1000 * rank, device="cuda")
+    A = I.hpl_matrix_torch(n, replica_seed(cfg["seed"], rank), diag_shift=shift, device="cuda")
+    B = I.hpl_rhs_torch(n, nrhs, replica_seed(cfg["seed"], rank), device="cuda")
     X = lu.colmajor_empty(n, nrhs)
     torch.cuda.synchronize()
     iters = []
