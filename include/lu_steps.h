@@ -77,6 +77,16 @@ int lu_step_gemm(lu_ctx ctx, lu_prec prec, int m, int n, int k, void *dC, int ld
 int lu_step_gemm_ozaki(lu_ctx ctx, int m, int n, int k, double *dC, int ldc, const double *dA, int lda,
                        const double *dB, int ldb);
 
+/* Failure-path probe: runs one of the library's bounded device waits on a
+ * condition that nothing ever satisfies -- kind 0: a triangular solve's wait
+ * for a solution block that is never published; 1: a panel's grid barrier
+ * that the other CTA never reaches; 2: a tensor-core kernel's mbarrier wait
+ * for a copy that never lands.  The wait gives up after the library's
+ * compiled-in limit (2 s), the kernel sets the timeout bit and returns, and
+ * the call returns LU_ETIMEOUT with the status cleared; the context stays
+ * usable.  Synchronizes.  Returns -1 (ctx NULL), -2 (kind not 0..2). */
+int lu_step_wait_probe(lu_ctx ctx, int kind);
+
 /* Read and clear the context's device status bits (synchronizes): returns
  * LU_OK, LU_ETIMEOUT or LU_ERANGE. */
 int lu_ctx_status(lu_ctx ctx);

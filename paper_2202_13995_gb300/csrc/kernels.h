@@ -157,4 +157,8 @@ cudaError_t launch_norm_inf(const double* A, int64_t lda, int n, double* partial
 cudaError_t launch_add_update(double* X, int64_t ldx, const double* D, int64_t ldd, int n, int nrhs,
                               const int* active, cudaStream_t st);
 
+// Bounded-wait probe (waitprobe.cu): kind 0 flag wait, 1 grid barrier, 2
+// mbarrier wait, each on a condition nothing satisfies; 8 bytes of scratch.
+cudaError_t launch_wait_probe(int kind, void* scratch, int* status, cudaStream_t st);
+
 }  // namespace gb

@@ -855,6 +855,16 @@ extern "C" int lu_step_gemm(lu_ctx c, lu_prec prec, int m, int n, int k, void* d
   return LU_OK;
 }
 
+extern "C" int lu_step_wait_probe(lu_ctx c, int kind) {
+  if (!c) return -1;
+  if (kind < 0 || kind > 2) return -2;
+  int rc = ensure_step_ws(c, 256);
+  if (rc) return rc;
+  CU_TRY(launch_wait_probe(kind, c->step_ws, c->d_status, c->stream));
+  c->launches += 1;
+  return read_status(c);
+}
+
 extern "C" int lu_step_gemm_ozaki(lu_ctx c, int m, int n, int k, double* dC, int ldc, const double* dA, int lda,
                                   const double* dB, int ldb) {
   if (!c) return -1;

@@ -100,30 +100,6 @@ __host__ __device__ inline size_t panel_smem_bytes(int R, int ib, int w, int tsi
   return tcount * tsize + icount * sizeof(int) + 16;
 }
 
-// Grid barrier on a monotonic arrival counter (zeroed by the launcher): the
-// k-th barrier waits until the counter reaches k * G.  Arrival is a release
-// reduction, so a CTA never waits on its own arrival round trip.
-__device__ __forceinline__ bool grid_sync_mono(unsigned* count, unsigned target, int* status, int* smem_flag) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
-    int ok = 1;
-    if (ld_acquire_u32(count) < target) {
-      const uint64_t t0 = gtimer();
-      while (ld_acquire_u32(count) < target) {
-        if (gtimer() - t0 > GB_SPIN_LIMIT_NS) {
-          atomicOr(status, ST_TIMEOUT);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    *smem_flag = ok;
-  }
-  __syncthreads();
-  return *smem_flag != 0;
-}
-
 template <typename T>
 __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

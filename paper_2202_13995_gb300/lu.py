@@ -32,7 +32,7 @@ EXPORTED = [
     "lu_profile_enable", "lu_profile_read", "lu_launch_count", "lu_step_panel_static",
     "lu_batch_create", "lu_batch_run", "lu_batch_shape", "lu_batch_free", "lu_solve_batched",
     "lu_server_create", "lu_server_submit", "lu_server_poll", "lu_server_wait", "lu_server_stats",
-    "lu_server_destroy", "lu_fact_bytes", "lu_factor_ex", "lu_step_gemm_ozaki",
+    "lu_server_destroy", "lu_fact_bytes", "lu_factor_ex", "lu_step_gemm_ozaki", "lu_step_wait_probe",
 ]
 PHASES = ["panel", "laswp", "trsm", "cast", "gemm", "solve", "residual", "other"]
 
@@ -90,6 +90,7 @@ def load():
             "lu_step_trsm": (I, [P, I, I, I, P, I, P, I]),
             "lu_step_gemm": (I, [P, I, I, I, I, P, I, P, I, P, I]),
             "lu_step_gemm_ozaki": (I, [P, I, I, I, P, I, P, I, P, I]),
+            "lu_step_wait_probe": (I, [P, I]),
             "lu_ctx_status": (I, [P]),
             "lu_device_sm_count": (I, [P]),
             "lu_build_tag": (C.c_char_p, []),
@@ -294,6 +295,14 @@ class Context:
         n = B.shape[1]
         _check(load().lu_step_gemm(self._h, _prec(prec), m, n, k, C.c_void_p(pc), ldc, C.c_void_p(pa), lda,
                                    C.c_void_p(pb), ldb), "lu_step_gemm")
+
+    def wait_probe(self, kind: int) -> int:
+        """Run one bounded device wait on a condition nothing satisfies (0 flag,
+        1 grid barrier, 2 mbarrier); returns the library's code (LU_ETIMEOUT)."""
+        rc = load().lu_step_wait_probe(self._h, int(kind))
+        if rc < 0:
+            _check(rc, "lu_step_wait_probe")
+        return rc
 
     def step_gemm_ozaki(self, Cm, A, B):
         """C -= A B in FP64 with the products on the BF16 tensor cores (row-major FP64, k <= 256)."""

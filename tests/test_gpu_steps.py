@@ -191,3 +191,27 @@ def test_gemm_fp16_overflow_is_reported(ctx):
     ctx.step_gemm(Cd, Ad[:, :64], Bd, "fp16")
     assert ctx.status() == lu.LU_ERANGE
     assert ctx.status() == 0  # cleared by the read
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+def test_bounded_wait_times_out_and_context_survives(ctx, kind):
+    """Failure detection without a fault: a solve's flag wait, a panel's grid
+    barrier and a tensor-core mbarrier wait, each on a condition nothing
+    satisfies, give up after the library's limit with LU_ETIMEOUT; the status
+    is cleared and the same context then factors and solves correctly."""
+    import time
+    from paper_2202_13995_gb300 import lu
+    t0 = time.time()
+    assert ctx.wait_probe(kind) == lu.LU_ETIMEOUT
+    assert 1.5 < time.time() - t0 < 60.0
+    assert ctx.status() == lu.LU_OK
+    n = 300
+    A = I.hpl_matrix(n, 3)
+    B = I.hpl_rhs(n, 1, 3)
+    import torch
+    At = torch.from_numpy(np.asfortranarray(A)).cuda()
+    f = ctx.factor(lu.colmajor_empty(n, n).copy_(At), "f64", 64)
+    x = lu.colmajor_empty(n, 1)
+    x.copy_(torch.from_numpy(np.asfortranarray(B)).cuda())
+    f.solve_(x)
+    assert O.scaled_residual(A, x.cpu().numpy(), B)[0] < 16.0
