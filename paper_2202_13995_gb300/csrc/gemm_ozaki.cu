@@ -761,34 +761,59 @@ namespace gb {
 
 // M = I - L^-1 for the unit-lower w x w block L (row-major, ld ldl): the top
 // block solve U12 = L^-1 A12 then becomes the update A12 - M A12, which the
-// split product runs on the tensor cores.  One warp per column j of L^-1:
-// forward substitution x_i = -sum_{k=j}^{i-1} L(i,k) x_k (x_j = 1), the sum
-// split over the lanes and reduced by shuffles; M(i,j) = -x_i below the
-// diagonal, 0 on and above it.
-__global__ void __launch_bounds__(256) unit_lower_inv_comp_kernel(const double* __restrict__ L, int64_t ldl, int w,
-                                                                  double* __restrict__ M, int64_t ldm) {
-  __shared__ double xs[8][OZ_KMAX];
-  const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-  const int j = blockIdx.x * 8 + wl;
-  if (j >= w) return;
-  double* x = xs[wl];
-  for (int i = lane; i < w; i += 32) x[i] = i == j ? 1.0 : 0.0;
-  __syncwarp();
-  for (int i = j + 1; i < w; ++i) {
-    double part = 0.0;
-    for (int k = j + lane; k < i; k += 32) part = fma(L[(int64_t)i * ldl + k], x[k], part);
+// split product runs on the tensor cores.  One warp per column j of L^-1,
+// forward substitution in its column (axpy) form: x = e_j, then for
+// k = j, j+1, ...: x_i -= L(i,k) x_k for every i > k, so each x_i receives its
+// terms in the order of k as in the definition.  Lane l holds x_i for
+// i = l + 32 r (r < 8); x_k is broadcast by a shuffle.  No reduction: GB300
+// runs FP64 at two operations per clock per SM, and a shuffle-add tree per
+// row cost more than the products.  M(i,j) = -x_i below the diagonal, 0 on
+// and above it.
+template <int KB>
+__device__ __forceinline__ void oz_inv_block(const double* __restrict__ L, int64_t ldl, int w, int j, int lane,
+                                             double (&x)[8]) {
+  if (j >= (KB + 1) * 32) return;  // this block of k lies left of column j
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
-    if (lane == 0) x[i] = -part;
-    __syncwarp();
+  for (int kk = 0; kk < 32; ++kk) {
+    const int k = KB * 32 + kk;
+    if (k < j) continue;
+    if (k >= w - 1) return;
+    const double xk = __shfl_sync(0xffffffffu, x[KB], kk);
+#pragma unroll
+    for (int r = KB; r < 8; ++r) {
+      const int i = lane + 32 * r;
+      if (i > k && i < w) x[r] = fma(-L[(int64_t)i * ldl + k], xk, x[r]);
+    }
   }
-  for (int i = lane; i < w; i += 32) M[(int64_t)i * ldm + j] = i > j ? -x[i] : 0.0;
+}
+
+__global__ void __launch_bounds__(32) unit_lower_inv_comp_kernel(const double* __restrict__ L, int64_t ldl, int w,
+                                                                 double* __restrict__ M, int64_t ldm) {
+  const int lane = threadIdx.x;
+  const int j = blockIdx.x;
+  double x[8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r) x[r] = (lane + 32 * r == j) ? 1.0 : 0.0;
+  oz_inv_block<0>(L, ldl, w, j, lane, x);
+  oz_inv_block<1>(L, ldl, w, j, lane, x);
+  oz_inv_block<2>(L, ldl, w, j, lane, x);
+  oz_inv_block<3>(L, ldl, w, j, lane, x);
+  oz_inv_block<4>(L, ldl, w, j, lane, x);
+  oz_inv_block<5>(L, ldl, w, j, lane, x);
+  oz_inv_block<6>(L, ldl, w, j, lane, x);
+  oz_inv_block<7>(L, ldl, w, j, lane, x);
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int i = lane + 32 * r;
+    if (i < w) M[(int64_t)i * ldm + j] = i > j ? -x[r] : 0.0;
+  }
 }
 
 cudaError_t launch_unit_lower_inv_comp(const double* L, int64_t ldl, int w, double* M, int64_t ldm, cudaStream_t st) {
   if (w <= 0) return cudaSuccess;
   if (w > OZ_KMAX) return cudaErrorInvalidValue;
-  unit_lower_inv_comp_kernel<<<(unsigned)cdiv(w, 8), 256, 0, st>>>(L, ldl, w, M, ldm);
+  static_assert(OZ_KMAX <= 8 * 32, "one warp holds a column of up to 256 entries");
+  unit_lower_inv_comp_kernel<<<(unsigned)w, 32, 0, st>>>(L, ldl, w, M, ldm);
   return cudaGetLastError();
 }
 
