@@ -123,6 +123,38 @@ __device__ __forceinline__ T pivot_mag(T x) {
   return a == a ? a : T(INFINITY);
 }
 
+// FP64 specialisations on the bit patterns: GB300 runs FP64 instructions,
+// comparisons included, at two per clock per SM, while a pivot search
+// compares magnitudes only.  A magnitude (non-negative, +inf for NaN) and the
+// "no candidate" value -1 order as their bit patterns read as signed 64-bit
+// integers, so the integer pipe gives the same answer.
+template <>
+__device__ __forceinline__ void argmax_merge<double>(double& v, int& i, double v2, int i2) {
+  const long long a = __double_as_longlong(v), b = __double_as_longlong(v2);
+  if (b > a || (b == a && i2 < i)) {
+    v = v2;
+    i = i2;
+  }
+}
+
+template <>
+__device__ __forceinline__ double pivot_mag<double>(double x) {
+  const unsigned long long m = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+  return __longlong_as_double((long long)(m > 0x7ff0000000000000ull ? 0x7ff0000000000000ull : m));
+}
+
+// x != 0 (either sign of zero); the FP64 form tests the bits on the integer pipe.
+__device__ __forceinline__ bool nonzero(float x) { return x != 0.0f; }
+__device__ __forceinline__ bool nonzero(double x) {
+  return ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) != 0ull;
+}
+
+// A pivot-search magnitude that is +inf (a non-finite entry).
+__device__ __forceinline__ bool is_inf_mag(float v) { return !(v < INFINITY); }
+__device__ __forceinline__ bool is_inf_mag(double v) {
+  return (unsigned long long)__double_as_longlong(v) == 0x7ff0000000000000ull;
+}
+
 template <typename T>
 __device__ __forceinline__ void warp_argmax(T& v, int& i) {
 #pragma unroll

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
       const int par = jg & 1;
       // ---- 1. this CTA's candidate: first row of largest |a| in column j
       //      among its rows >= jg; publish it with its sub-panel values
-      if (!(bv < T(INFINITY))) atomicOr(P.status, ST_RANGE);  // a non-finite candidate
+      if (is_inf_mag(bv)) atomicOr(P.status, ST_RANGE);  // a non-finite candidate
       warp_argmax(bv, bi);
       if (lane == 0) {
         redv[warp] = bv;
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
         const int gi = row0 + r;
         if (gi > jg) {
           T l = S[j * Rs + r];
-          if (piv != T(0)) l = l / piv;
+          if (nonzero(piv)) l = l / piv;
           S[j * Rs + r] = l;
           for (int c = j + 1; c < ibs; ++c) S[c * Rs + r] -= l * prow[c];
           if (j + 1 < ibs) argmax_merge(bv, bi, pivot_mag(S[(j + 1) * Rs + r]), gi);

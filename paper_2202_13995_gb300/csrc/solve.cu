@@ -43,14 +43,17 @@ struct TrsvSmem {
   T yb[STAGES][NR][TS_BS];
   T Ld[TS_BS][TS_BS + 1];  // diagonal block (or its inverse), padded rows
   T v[NR][TS_BS];
+  T rinv[TS_BS];  // 1 / U(t,t) of the diagonal block (upper substitution)
   int flag;
   int blk;
 };
 
 // With DINV, the diagonal block's inverse (precomputed by trinv_kernel) turns
 // the serial substitution into a parallel matrix-vector product; the FP32
-// correction solves of the refinement use it.  The FP64 solve substitutes
-// (with the division of the definition).
+// correction solves of the refinement use it.  The FP64 solve substitutes;
+// its upper triangle multiplies by the reciprocals of the diagonal, computed
+// when the block starts, off the chain of blocks (an FP64 division on GB300
+// takes longer than the rest of a substitution step).
 
 // LOWER: Y = L^-1 (P B) with unit-lower L; the right-hand side is gathered
 //        from B through rowid: (P b)[i] = b[rowid[i]].
@@ -101,6 +104,10 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
     for (int q = 0; q < PER; ++q) {
       const int e = tid + q * 256;
       sm.Ld[e >> 6][e & 63] = dv[q];
+    }
+    if (!DINV && !LOWER) {
+      __syncthreads();
+      if (tid < TS_BS) sm.rinv[tid] = tid < rows ? T(1) / sm.Ld[tid][tid] : T(0);
     }
   }
   // this block's right-hand side: thread (row tid & 63) holds columns
@@ -262,10 +269,10 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
       for (int t = rows - 1; t >= 0; --t) {
         T xt;
         if (t >= 32) {
-          if (lane == t - 32) x1 = x1 / sm.Ld[t][t];
+          if (lane == t - 32) x1 = x1 * sm.rinv[t];
           xt = __shfl_sync(0xffffffffu, x1, t - 32);
         } else {
-          if (lane == t) x0 = x0 / sm.Ld[t][t];
+          if (lane == t) x0 = x0 * sm.rinv[t];
           xt = __shfl_sync(0xffffffffu, x0, t);
         }
         if (lane < t) x0 -= sm.Ld[lane][t] * xt;
