@@ -529,25 +529,28 @@ def run_ours(args, cfg, wname):
     # ---- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        Ah = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
-        Ah.copy_(A)
-        Bh = torch.empty((nrhs, n), dtype=torch.float64).pin_memory().t()
-        Bh.copy_(B)
-        Xh = torch.empty((nrhs, n), dtype=torch.float64).pin_memory().t()
+        # column-major host and device buffers held as contiguous (k, n)
+        # storages, so that every transfer is one plain copy of the bytes
+        Ah = torch.empty((n, n), dtype=torch.float64, pin_memory=True)
+        Ah.copy_(A.t())
+        Bh = torch.empty((nrhs, n), dtype=torch.float64, pin_memory=True)
+        Bh.copy_(B.t())
+        Xh = torch.empty((nrhs, n), dtype=torch.float64, pin_memory=True)
         Ad = lu.colmajor_empty(n, n)
         Bd = lu.colmajor_empty(n, nrhs)
         Xd = lu.colmajor_empty(n, nrhs)
+        assert Ad.t().is_contiguous() and Bd.t().is_contiguous() and Xd.t().is_contiguous()
 
         def e2e_step():
-            Ad.copy_(Ah, non_blocking=True)
-            Bd.copy_(Bh, non_blocking=True)
+            Ad.t().copy_(Ah, non_blocking=True)
+            Bd.t().copy_(Bh, non_blocking=True)
             f = ctx.factor(Ad, prec, nb, sync=False, nopiv=bool(cfg.get("nopiv", False)), ozaki=ozaki)
             if mixed and not cfg.get("norefine", False):
                 f.refine(Ad, Bd, Xd, 16.0, 50)
             else:
                 Xd.copy_(Bd)
                 f.solve_(Xd)
-            Xh.copy_(Xd, non_blocking=True)
+            Xh.copy_(Xd.t(), non_blocking=True)
             f.free()
 
         e2e_step()
