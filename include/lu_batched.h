@@ -53,7 +53,7 @@ int lu_batch_shape(lu_batch b, int *threads, int *ctas_per_sm, float *ms);
 /* Release the plan (stream-ordered). */
 void lu_batch_free(lu_batch b);
 
-/* One-call form (SURVEY boundary): plan, run and free; dB holds b on entry and
+/* One-call form: plan, run and free; dB holds b on entry and
  * x on return; dInfo as in lu_batch_run.  Synchronizes the stream. */
 int lu_solve_batched(lu_ctx ctx, int count, const int *n, const int *nrhs, const double *const *dA, const int *lda,
                      double *const *dB, const int *ldb, lu_prec prec, int *dInfo);
