@@ -6,14 +6,14 @@
 // 2202.13995, section "Base Implementation"; the paper's own design unrolls a
 // register-blocked GEMM in FPGA DSPs), here on the 5th-generation tensor cores:
 //   - warp 0 (one thread) streams K-chunks of 64 elements of both operands
-//     into a 3-stage shared-memory ring with TMA (128-byte swizzle);
+//     into a 2-stage shared-memory ring with TMA (128-byte swizzle);
 //   - warp 1 (one thread) issues tcgen05.mma (M=128, N=256, K=16) into one of
 //     two TMEM accumulators (2 x 256 columns), committing each stage back to
 //     the producer and each finished tile to the epilogue;
 //   - warps 2..9 drain a finished accumulator with tcgen05.ld while the next
 //     tile accumulates in the other one, and subtract it from C in place.
 //     C moves through shared memory in 32 x 32 chunks: each epilogue warp
-//     keeps TC_CBUF chunk buffers and loads C (cp.async, row-contiguous
+//     keeps four chunk buffers and loads C (cp.async, row-contiguous
 //     16-byte pieces, four full 128-byte lines per warp instruction) three
 //     chunks ahead of the one it drains.  TMEM hands each thread one row: the
 //     thread subtracts its row in shared memory, and the warp writes the chunk
