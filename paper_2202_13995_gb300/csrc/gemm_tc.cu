@@ -480,6 +480,5 @@ cudaError_t tc_gemm_run(int kind, float* C, int64_t ldc, const void* Aop, const 
   return cudaGetLastError();
 }
 
-size_t tc_gemm_plan_bytes() { return 0; }
 
 }  // namespace gb
