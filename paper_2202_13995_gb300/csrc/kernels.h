@@ -100,7 +100,6 @@ cudaError_t launch_gemm_simt(T* C, int64_t ldc, const T* A, int64_t lda, const T
 cudaError_t launch_cast_operands(int kind, const float* L21, const float* U12, int64_t ldw, int m, int n, int k,
                                  void* Aop, void* Bop, int kpad, int* status, cudaStream_t st);
 // C (row-major FP32, m x n) -= Aop * Bop^T on tcgen05 (FP32 accumulate in TMEM).
-struct TcGemmPlan;
 // max_ctas > 0 caps the persistent grid (to leave SMs to a concurrent kernel).
 cudaError_t tc_gemm_run(int kind, float* C, int64_t ldc, const void* Aop, const void* Bop, int m, int n, int kpad,
                         int* status, const DevInfo& dev, cudaStream_t st, int max_ctas = 0);
