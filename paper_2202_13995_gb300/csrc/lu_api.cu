@@ -375,10 +375,20 @@ static int factor_loop_nopiv(lu_fact f) {
   const int64_t ld = f->ldw;
   const bool tc = f->prec == LU_BF16 || f->prec == LU_FP16;
   const int kind = f->prec == LU_BF16 ? 1 : 2;
+  // Lookahead (tensor-core form): the next diagonal block's columns are
+  // updated first, then its LU (one CTA) runs on the side stream while the
+  // rest of the trailing matrix is updated on the other SMs.
+  const bool lookahead = tc && !f->ozaki && c->lookahead && c->side != nullptr;
+  bool diag_ready = false;
   for (int k = 0; k < n; k += nb) {
     const int w = (n - k) < nb ? (n - k) : nb;
     T* Wkk = W + (int64_t)k * ld + k;
-    CU_TRY(PHASE(c, PH_PANEL, 1, launch_diag_lu<T>(Wkk, ld, w, k, f->info_d, st)));
+    if (diag_ready) {
+      CU_TRY(cudaStreamWaitEvent(st, c->ev_panel, 0));
+      diag_ready = false;
+    } else {
+      CU_TRY(PHASE(c, PH_PANEL, 1, launch_diag_lu<T>(Wkk, ld, w, k, f->info_d, st)));
+    }
     const int rest = n - k - w;
     if (rest <= 0) continue;
     T* U12 = Wkk + w;
@@ -398,12 +408,28 @@ static int factor_loop_nopiv(lu_fact f) {
     } else if (tc) {
       CU_TRY(PHASE(c, PH_CAST, 2, launch_cast_operands(kind, (const float*)L21, (const float*)U12, ld, rest, rest,
                                                         w, f->aop, f->bop, f->kpad, c->d_status, st)));
-      CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)A22, ld, f->aop, f->bop, rest, rest, f->kpad,
+      const int w2 = rest < nb ? rest : nb;
+      if (!lookahead || rest <= w2) {
+        CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)A22, ld, f->aop, f->bop, rest, rest, f->kpad,
+                                                 c->d_status, c->dev, st)));
+        continue;
+      }
+      // the next diagonal block's columns, then its LU beside the rest
+      CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)A22, ld, f->aop, f->bop, rest, w2, f->kpad,
                                                c->d_status, c->dev, st)));
+      CU_TRY(cudaEventRecord(c->ev_next, st));
+      CU_TRY(cudaStreamWaitEvent(c->side, c->ev_next, 0));
+      CU_TRY(PHASE_ON(c, c->side, PH_PANEL, 1, launch_diag_lu<T>(A22, ld, w2, k + w, f->info_d, c->side)));
+      CU_TRY(cudaEventRecord(c->ev_panel, c->side));
+      diag_ready = true;
+      const void* bop2 = (const char*)f->bop + (size_t)w2 * f->kpad * 2;
+      CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)(A22 + w2), ld, f->aop, bop2, rest, rest - w2, f->kpad,
+                                               c->d_status, c->dev, st, c->dev.sm_count - 1)));
     } else {
       CU_TRY(PHASE(c, PH_GEMM, 1, launch_gemm_simt<T>(A22, ld, L21, ld, U12, ld, rest, rest, w, st)));
     }
   }
+  if (diag_ready) CU_TRY(cudaStreamWaitEvent(st, c->ev_panel, 0));
   return LU_OK;
 }
 
