@@ -14,12 +14,48 @@
 namespace gb {
 
 constexpr int NP_NB = 32;
+
+// 16-byte global accesses of 16 / sizeof(T) elements, and a 4-element
+// shared-memory load (one or two 16-byte accesses); the addresses are aligned.
+template <typename T>
+__device__ __forceinline__ void load16(const T* p, T* v);
+template <>
+__device__ __forceinline__ void load16<float>(const float* p, float* v) {
+  const float4 x = *reinterpret_cast<const float4*>(p);
+  v[0] = x.x;
+  v[1] = x.y;
+  v[2] = x.z;
+  v[3] = x.w;
+}
+template <>
+__device__ __forceinline__ void load16<double>(const double* p, double* v) {
+  const double2 x = *reinterpret_cast<const double2*>(p);
+  v[0] = x.x;
+  v[1] = x.y;
+}
+template <typename T>
+__device__ __forceinline__ void store16(T* p, const T* v);
+template <>
+__device__ __forceinline__ void store16<float>(float* p, const float* v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void store16<double>(double* p, const double* v) {
+  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+}
+template <typename T>
+__device__ __forceinline__ void load4s(const T* p, T* v) {
+  load16<T>(p, v);
+  if (sizeof(T) == 8) load16<T>(p + 2, v + 2);
+}
 constexpr int NP_CW = 128;  // column chunk of the in-block update
-// threads of the diagonal-block CTA: many for FP32 (its global updates are
-// latency-bound), fewer for FP64 (a thread holds 32 doubles in registers)
+// threads of the diagonal-block CTA: 512 for FP32 (the update loads its C
+// tile ahead of the products, which needs more than the 64 registers a thread
+// of a 1024-thread CTA has), 256 for FP64 (a thread holds 32 doubles in
+// registers)
 template <typename T>
 constexpr int np_threads() {
-  return sizeof(T) == 8 ? 256 : 1024;
+  return sizeof(T) == 8 ? 256 : 512;
 }
 
 // In-place LU (no pivoting) of the w x w block at D (row-major, ld), blocked by
@@ -33,11 +69,24 @@ __global__ void __launch_bounds__(np_threads<T>()) diag_lu_kernel(T* D, int64_t 
   T* Us = P + (size_t)NP_NB * wp;         // [NP_NB][NP_CW]
   const int tid = threadIdx.x;
   constexpr int NP_NT = np_threads<T>();
+  constexpr int CH = 16 / sizeof(T);  // elements per 16-byte access
+  const bool vec = ((reinterpret_cast<uintptr_t>(D) & 15) == 0) && (ld % CH) == 0;
   for (int k0 = 0; k0 < w; k0 += NP_NB) {
     const int kb = min(NP_NB, w - k0), m = w - k0;
-    for (int e = tid; e < m * NP_NB; e += NP_NT) {
-      const int r = e / NP_NB, c = e % NP_NB;
-      if (c < kb) P[c * wp + r] = D[(int64_t)(k0 + r) * ld + k0 + c];
+    // thread = row (consecutive threads, consecutive rows: the column-major
+    // sub-panel is written without bank conflicts), CH columns per load
+    for (int e = tid; e < m * (NP_NB / CH); e += NP_NT) {
+      const int r = e % m, c = (e / m) * CH;
+      if (c >= kb) continue;
+      const T* src = D + (int64_t)(k0 + r) * ld + k0 + c;
+      if (vec && c + CH <= kb) {
+        T v[CH];
+        load16<T>(src, v);
+#pragma unroll
+        for (int x = 0; x < CH; ++x) P[(c + x) * wp + r] = v[x];
+      } else {
+        for (int x = 0; c + x < kb; ++x) P[(c + x) * wp + r] = src[x];
+      }
     }
     __syncthreads();
     for (int j = 0; j < kb; ++j) {
@@ -51,9 +100,18 @@ __global__ void __launch_bounds__(np_threads<T>()) diag_lu_kernel(T* D, int64_t 
       }
       __syncthreads();
     }
-    for (int e = tid; e < m * NP_NB; e += NP_NT) {
-      const int r = e / NP_NB, c = e % NP_NB;
-      if (c < kb) D[(int64_t)(k0 + r) * ld + k0 + c] = P[c * wp + r];
+    for (int e = tid; e < m * (NP_NB / CH); e += NP_NT) {
+      const int r = e % m, c = (e / m) * CH;
+      if (c >= kb) continue;
+      T* dst = D + (int64_t)(k0 + r) * ld + k0 + c;
+      if (vec && c + CH <= kb) {
+        T v[CH];
+#pragma unroll
+        for (int x = 0; x < CH; ++x) v[x] = P[(c + x) * wp + r];
+        store16<T>(dst, v);
+      } else {
+        for (int x = 0; c + x < kb; ++x) dst[x] = P[(c + x) * wp + r];
+      }
     }
     __syncthreads();
     for (int c0 = k0 + kb; c0 < w; c0 += NP_CW) {
@@ -83,17 +141,26 @@ __global__ void __launch_bounds__(np_threads<T>()) diag_lu_kernel(T* D, int64_t 
       const int rt = (rows + 3) / 4, ct = (cw + 3) / 4;
       for (int t = tid; t < rt * ct; t += NP_NT) {
         const int r0 = kb + (t / ct) * 4, cc = (t % ct) * 4;
+        // the tile's entries of D first: their latency runs under the products
+        T dv[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const T* dr = D + (int64_t)(k0 + min(r0 + i, m - 1)) * ld + c0 + cc;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) dv[i][q] = (r0 + i < m && cc + q < cw) ? dr[q] : T(0);
+        }
         T acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[i][q] = T(0);
+        // kb = NP_NB here (the last block has no rows below it), so r0 and cc
+        // are multiples of 4: 16-byte shared loads.  Lanes past m or cw read
+        // stale entries into rows / columns of acc that are never stored.
         for (int k = 0; k < kb; ++k) {
           T a[4], b[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) a[i] = (r0 + i < m) ? P[k * wp + r0 + i] : T(0);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) b[q] = (cc + q < cw) ? Us[k * NP_CW + cc + q] : T(0);
+          load4s<T>(&P[k * wp + r0], a);
+          load4s<T>(&Us[k * NP_CW + cc], b);
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -105,7 +172,7 @@ __global__ void __launch_bounds__(np_threads<T>()) diag_lu_kernel(T* D, int64_t 
           T* dr = D + (int64_t)(k0 + r0 + i) * ld + c0 + cc;
 #pragma unroll
           for (int q = 0; q < 4; ++q)
-            if (cc + q < cw) dr[q] -= acc[i][q];
+            if (cc + q < cw) dr[q] = dv[i][q] - acc[i][q];
         }
       }
       __syncthreads();
