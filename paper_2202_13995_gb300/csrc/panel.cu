@@ -299,12 +299,24 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
         for (int t = warp; t < ibs; t += PNL_WARPS)
           if (lane < cw) Ust[t * 32 + lane] = __ldcg(P.A + (int64_t)(j0 + t) * ld + cc + lane);
         __syncthreads();
-        for (int r = warp; r < rloc; r += PNL_WARPS) {
-          const int gi = row0 + r;
-          if (gi >= c0 && lane < cw) {
-            T a = __ldcg(P.A + (int64_t)gi * ld + cc + lane);
-            for (int t = 0; t < ibs; ++t) a -= S[t * Rs + r] * Ust[t * 32 + lane];
-            P.A[(int64_t)gi * ld + cc + lane] = a;
+        // eight of the warp's rows per batch, their loads in flight together
+        // (one L2 round trip per eight rows instead of one per row)
+        for (int rb = warp; rb < rloc; rb += PNL_WARPS * 8) {
+          T a[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int r = rb + i * PNL_WARPS;
+            const bool ok = r < rloc && row0 + r >= c0 && lane < cw;
+            a[i] = ok ? __ldcg(P.A + (int64_t)(row0 + r) * ld + cc + lane) : T(0);
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int r = rb + i * PNL_WARPS;
+            if (r < rloc && row0 + r >= c0 && lane < cw) {
+              T v = a[i];
+              for (int t = 0; t < ibs; ++t) v -= S[t * Rs + r] * Ust[t * 32 + lane];
+              P.A[(int64_t)(row0 + r) * ld + cc + lane] = v;
+            }
           }
         }
         __syncthreads();
