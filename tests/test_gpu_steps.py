@@ -76,6 +76,35 @@ def test_panel_f32_exact_on_dyadic(ctx, m, w):
     assert np.array_equal(Pd.cpu().numpy().astype(np.float64), LUo)
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_panel_nan_is_reported(ctx, prec):
+    """A NaN in the panel compares as +inf in the pivot search: it becomes the
+    pivot of its column (so every column has a candidate row), the non-finite
+    pivot raises LU_ERANGE, and every pivot index stays in range."""
+    import torch
+    from paper_2202_13995_gb300 import lu
+    m, w, row, col = 700, 64, 350, 5
+    P = _panel_input(m, w, 11)
+    P[row, col] = np.nan
+    Pd = _rm(P, torch.float64 if prec == "f64" else torch.float32)
+    ipiv = torch.zeros(w, dtype=torch.int32, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.step_panel(Pd, ipiv, info, prec)
+    assert ctx.status() == lu.LU_ERANGE
+    ip = ipiv.cpu().numpy()
+    assert ((ip >= np.arange(1, w + 1)) & (ip <= m)).all()
+    # where the NaN's row stands after the first `col` interchanges: its pivot
+    pos = row
+    for j in range(col):
+        p = ip[j] - 1
+        pos = p if pos == j else (j if pos == p else pos)
+    assert ip[col] - 1 == pos
+    if prec == "f64":
+        # the columns before it never see the NaN: the oracle's pivots
+        _, ipo, _ = O.getf2(P[:, :col].copy())
+        assert np.array_equal(ip[:col], ipo)
+
+
 def test_panel_zero_pivot(ctx):
     import torch
     P = _panel_input(200, 40, 7)
