@@ -107,7 +107,8 @@ __device__ int bt_factor(float* W, int ld, int n, BatchSmem& sm, int* status) {
         argmax_merge(bv, bi, v, r);
       }
       block_argmax_f(bv, bi, sm, NT);
-      const int p = bi;
+      int p = bi;
+      if (!GB_IN_BOUNDS(status, p >= j && p < m)) p = j;
       if (tid < kb && p != j) {
         const float t = sm.P[tid][j];
         sm.P[tid][j] = sm.P[tid][p];

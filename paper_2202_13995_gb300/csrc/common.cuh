@@ -15,7 +15,17 @@ enum StatusBits : int {
   ST_TIMEOUT = 1,   // a bounded device wait hit its limit
   ST_RANGE = 2,     // a cast to a 16-bit format overflowed, or a NaN was met
   ST_BADARG = 4,    // a kernel was given a size it cannot handle
+  ST_BOUNDS = 8,    // an index guard of the bounds-checking build fired
 };
+
+// Index guards.  The bounds-checking build (-DLU_BOUNDS_CHECK) tests `cond`,
+// records ST_BOUNDS and lets the caller take a safe path when it fails; the
+// normal build compiles the guard away.
+#ifdef LU_BOUNDS_CHECK
+#define GB_IN_BOUNDS(status, cond) ((cond) ? true : (atomicOr((status), ST_BOUNDS), false))
+#else
+#define GB_IN_BOUNDS(status, cond) true
+#endif
 
 // limit of every device spin (nanoseconds of %globaltimer)
 #ifndef GB_SPIN_LIMIT_NS

@@ -254,7 +254,7 @@ static int read_status(lu_ctx c) {
   }
   if (s & ST_TIMEOUT) return LU_ETIMEOUT;
   if (s & ST_RANGE) return LU_ERANGE;
-  if (s & ST_BADARG) return LU_EINTERNAL;
+  if (s & (ST_BADARG | ST_BOUNDS)) return LU_EINTERNAL;
   return LU_OK;
 }
 

@@ -214,7 +214,8 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
         warp_argmax(v, i);
         bi = i;  // the pivot row, in every thread
       }
-      const int p = bi;
+      int p = bi;
+      if (!GB_IN_BOUNDS(P.status, p >= jg && p < P.m)) p = jg;
       const T* prow = xall + (p / R) * ib;  // the pivot row's sub-panel values
       if (tid < ibs) {
         if (p != jg && p >= row0 && p < row0 + rloc) S[tid * Rs + (p - row0)] = rjq;

@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
   }
   __syncthreads();
   const int t_ = sm.blk;
+  if (!GB_IN_BOUNDS(status, t_ >= 0 && t_ < nblk)) return;  // uniform: sm.blk is the CTA's
   const int ib = LOWER ? t_ : nblk - 1 - t_;
   const int i0 = ib * TS_BS;
   const int rows = min(TS_BS, n - i0);

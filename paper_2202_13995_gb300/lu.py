@@ -18,7 +18,8 @@ import weakref
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgb300lu.so")
+# GB300LU_LIB names another build of the library (the bounds-checking one)
+LIB_PATH = os.environ.get("GB300LU_LIB") or os.path.join(_HERE, "libgb300lu.so")
 
 LU_F64, LU_BF16, LU_FP16, LU_F32 = 0, 1, 2, 3
 PRECS = {"f64": LU_F64, "bf16": LU_BF16, "fp16": LU_FP16, "f32": LU_F32}
