@@ -78,3 +78,24 @@ def test_traffic_scales_the_measured_ratio():
     assert r["traffic_over_algorithmic"] == ratios["gemm_simt_kernel<double>"]["ratio"]
     for k in ("gemm_simt_kernel<double>", "tc_gemm_kernel", "oz_gemm_kernel"):
         assert 0.5 < ratios[k]["ratio"] < 3.0 and "command" in ratios[k]
+
+
+def test_reference_arm_line_has_the_contract_keys():
+    """`bench.py --impl reference` (the oracle on the host cores) prints one
+    JSON line with the keys of the bench contract."""
+    import json
+    import subprocess
+    cmd = [sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+           "--ref-seconds", "0.5", "--workload", "hpl_f64_n1024_nb64"]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e", "gpu_launches"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert d["config"]["workload"] == "hpl_f64_n1024_nb64" and d["metric"] == bench.METRIC
