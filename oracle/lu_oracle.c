@@ -297,18 +297,25 @@ void orc_getrs(int n, int nrhs, const double *LU, int lda, const int *ipiv, doub
     }
 }
 
-/* R = B - A X (n x nrhs).  Each r_i sums its products in column order. */
+/* R = B - A X (n x nrhs).  Each r_i sums its products in column order
+ * (j = 0, 1, ..., n-1), whatever the number of threads: the threads split the
+ * rows, and a block of rows walks every column in order for each right-hand
+ * side. */
 void orc_residual(int n, int nrhs, const double *A, int lda, const double *X, int ldx,
                   const double *B, int ldb, double *R, int ldr) {
-    for (int r = 0; r < nrhs; ++r) {
-        double *rr = R + IDX(0, r, ldr);
-        const double *bb = B + IDX(0, r, ldb);
-        const double *xx = X + IDX(0, r, ldx);
-        for (int i = 0; i < n; ++i) rr[i] = bb[i];
+    const int RB = 256;
+#pragma omp parallel for schedule(static)
+    for (int i0 = 0; i0 < n; i0 += RB) {
+        const int i1 = (i0 + RB) < n ? (i0 + RB) : n;
+        for (int r = 0; r < nrhs; ++r)
+            for (int i = i0; i < i1; ++i) R[IDX(i, r, ldr)] = B[IDX(i, r, ldb)];
         for (int j = 0; j < n; ++j) {
-            double xj = xx[j];
             const double *a = A + IDX(0, j, lda);
-            for (int i = 0; i < n; ++i) rr[i] -= a[i] * xj;
+            for (int r = 0; r < nrhs; ++r) {
+                const double xj = X[IDX(j, r, ldx)];
+                double *rr = R + IDX(0, r, ldr);
+                for (int i = i0; i < i1; ++i) rr[i] -= a[i] * xj;
+            }
         }
     }
 }

@@ -236,6 +236,28 @@ def test_residual_and_norms_library_pin():
     assert O.norm_inf(X[:, 1]) == np.abs(X[:, 1]).max()
 
 
+def test_residual_sums_in_column_order_on_any_thread_count():
+    """r_i = b_i - a_i1 x_1 - a_i2 x_2 - ... in that order (one rounding per
+    product and per subtraction), bit for bit, whether the oracle's threads
+    split the rows or not: the definition, written here with numpy column by
+    column, over several row blocks and a ragged tail."""
+    rng = np.random.default_rng(17)
+    n, k = 600, 3
+    A = rng.standard_normal((n, n))
+    X = rng.standard_normal((n, k))
+    B = rng.standard_normal((n, k))
+    want = B.copy()
+    for j in range(n):
+        want = want - A[:, j:j + 1] * X[j:j + 1, :]
+    t0 = O.num_threads()
+    try:
+        for t in (1, max(2, t0)):
+            O.set_threads(t)
+            assert np.array_equal(O.residual(A, X, B), want)
+    finally:
+        O.set_threads(t0)
+
+
 def test_cond_estimate_against_exact():
     rng = np.random.default_rng(1)
     for n in (5, 20, 60):
