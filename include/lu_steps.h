@@ -37,12 +37,16 @@ int lu_step_panel(lu_ctx ctx, lu_prec prec, int m, int w, void *dP, int ld, int 
  * allows no allocation afterwards.  lu_step_panel allocates its scratch on
  * first use; this variant allocates nothing and creates no context object.
  *
- * Its scratch is one fixed 1 MiB array in device memory, held on every GPU
- * that loads the library until the process exits.  Limits: w <= 512, and
- * the device has at most 1024 SMs; larger requests return -4 (argument 4,
- * w, invalid) without running anything.  The first call on each device (with
- * that device current) looks up the array's device address and the SM count;
- * make that first call before any stream capture begins.
+ * Its scratch is one fixed array of about 96 KB in device memory, held on
+ * every GPU that loads the library until the process exits.  Limits: w <= 512
+ * (a wider panel returns -4, argument 4 invalid) and a panel whose rows fit
+ * the CTAs' shared memory (on GB300 about 78,000 rows in FP64 and 200,000 in
+ * FP32; a taller one returns -3); both are checked before anything is
+ * enqueued.  The panel runs
+ * on at most 160 CTAs (one per SM on GB300's 152 SMs; a larger device uses
+ * 160 of its SMs).  The first call on each device (with that device current)
+ * looks up the array's device address and the SM count; make that first call
+ * before any stream capture begins.
  *
  * Every call uses the same array and leaves its last contents there: calls
  * whose work overlaps on the GPU (on different streams, or from different
@@ -99,6 +103,10 @@ int lu_ctx_status(lu_ctx ctx);
  * 7 other; arrays of LU_NPHASE entries), then clears the record. */
 #define LU_NPHASE 8
 int lu_profile_enable(lu_ctx ctx, int enable);
+/* Phases recorded while profiling is enabled: bit p of phase_mask selects
+ * phase p (default: every phase).  Selecting one phase keeps the other
+ * launches free of events, e.g. to time one kernel inside a timed region. */
+int lu_profile_select(lu_ctx ctx, unsigned phase_mask);
 int lu_profile_read(lu_ctx ctx, double *ms, long long *launches);
 
 /* Kernels this context has launched so far (all phases, profiling or not). */

@@ -35,7 +35,19 @@ struct PanelScratch {
   int wmax;
   int gtarget = 0; // preferred CTA count (0: the default for the element size)
 };
-size_t panel_scratch_bytes(int gmax, int ibmax, int wmax, int tsize);
+// Most CTAs one cooperative panel launch may use: every CTA's candidate row
+// of a column must fit the exchange buffer each CTA reads after the barrier.
+constexpr int kPanelMaxCtas = 160;
+// Bytes of PanelScratch for up to gmax CTAs, sub-panels of ibmax columns,
+// panels up to wmax wide, elements of tsize bytes (each part 256-aligned).
+constexpr size_t panel_scratch_bytes(int gmax, int ibmax, int wmax, int tsize) {
+  return 64                                                  // barrier
+         + (2 * (size_t)gmax * tsize + 256)                  // xval
+         + (2 * (size_t)gmax * sizeof(int) + 256)            // xidx
+         + (2 * (size_t)gmax * ibmax * tsize + 256)          // xrow
+         + (2 * (size_t)ibmax * tsize + 256)                 // xrowj
+         + ((1 + 4 * (size_t)wmax) * sizeof(int) + 256);     // perm
+}
 void panel_scratch_carve(PanelScratch* s, void* base, int gmax, int ibmax, int wmax, int tsize);
 
 // CTAs that launch_panel uses for an m x w panel of element size tsize

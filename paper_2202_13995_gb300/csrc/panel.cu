@@ -70,7 +70,7 @@ constexpr int PNL_WARPS = PNL_THREADS / 32;
 constexpr int PNL_IB = 32;
 // After each column's barrier every CTA reads all candidate rows at once
 // (one L2 round trip); up to PNL_XG CTAs.
-constexpr int PNL_XG = 160;
+constexpr int PNL_XG = kPanelMaxCtas;
 constexpr int PNL_XQ = PNL_XG * PNL_IB / PNL_THREADS;  // candidate values per thread
 constexpr int PNL_HF = 2048;  // hash buckets: rows outside the panel's top w rows
 constexpr int PNL_HS = 128;   // hash buckets: rows outside a sub-panel's top rows
@@ -334,16 +334,6 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
       P.perm[1 + 2 * w + s2] = fcur[s2];
     }
   }
-}
-
-size_t panel_scratch_bytes(int gmax, int ibmax, int wmax, int tsize) {
-  size_t b = 64;                                   // barrier
-  b += 2 * (size_t)gmax * tsize + 256;             // xval
-  b += 2 * (size_t)gmax * sizeof(int) + 256;       // xidx
-  b += 2 * (size_t)gmax * ibmax * tsize + 256;     // xrow
-  b += 2 * (size_t)ibmax * tsize + 256;            // xrowj
-  b += (1 + 4 * (size_t)wmax) * sizeof(int) + 256; // perm
-  return b;
 }
 
 static inline char* align_up(char* p, size_t a) { return (char*)(((uintptr_t)p + a - 1) / a * a); }

@@ -18,10 +18,15 @@
 
 namespace {
 
-constexpr int kStaticGmax = 1024;  // CTAs of one cooperative panel launch
+// CTAs of one cooperative panel launch: the panel kernel's own limit (every
+// CTA's candidate row must fit the exchange buffer); a device with more SMs
+// runs the panel on this many of them.
+constexpr int kStaticGmax = gb::kPanelMaxCtas;
 constexpr int kStaticIb = 32;
 constexpr int kStaticWmax = 512;   // widest panel accepted
-constexpr size_t kStaticBytes = size_t(1) << 20;  // 1 MiB
+// the scratch of the largest launch (FP64, widest panel), with room for the
+// 256-byte alignment of its parts
+constexpr size_t kStaticBytes = gb::panel_scratch_bytes(kStaticGmax, kStaticIb, kStaticWmax, 8) + 1024;
 
 __device__ __align__(256) static unsigned char g_panel_scratch[kStaticBytes];
 
@@ -80,8 +85,10 @@ extern "C" int lu_step_panel_static(void* cuda_stream, lu_prec prec, int m, int 
   if (rc) return rc;
   const int tsize = prec == LU_F64 ? 8 : 4;
   const int gmax = info.sm_count < kStaticGmax ? info.sm_count : kStaticGmax;
-  if (info.sm_count > kStaticGmax) return LU_EINTERNAL;
-  if (gb::panel_scratch_bytes(gmax, kStaticIb, w, tsize) > kStaticBytes) return -4;
+  if (gb::panel_scratch_bytes(gmax, kStaticIb, w, tsize) > kStaticBytes) return LU_EINTERNAL;
+  // a panel too tall for the CTAs' shared memory is refused here, before
+  // anything is enqueued (dStatus and dInfo are left untouched)
+  if (gb::panel_grid_size(m, w, tsize, info, gmax) <= 0) return -3;
   gb::PanelScratch ps;
   gb::panel_scratch_carve(&ps, base, gmax, kStaticIb, w, tsize);
   cudaStream_t st = (cudaStream_t)cuda_stream;
