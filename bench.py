@@ -376,6 +376,9 @@ def timed_solves(ctx, stream, cfg: dict, nb, steps: int, warmup: int, rank: int,
     torch.cuda.synchronize()
     if sampler:
         sampler.start()
+    # the timed region carries one CUDA event pair per trailing-update launch
+    # (the roofline's kernel) and no other events
+    ctx.profile_select(["gemm"])
     ctx.profile(True)
     l0 = ctx.launch_count()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -391,12 +394,27 @@ def timed_solves(ctx, stream, cfg: dict, nb, steps: int, warmup: int, rank: int,
     barrier(ws)
     ck = sampler.stop() if sampler else None
     ms = max_over_ranks(ev0.elapsed_time(ev1) / steps, ws)
+    # the phase split from a separate pass with an event pair around every launch
+    psteps = max(1, min(steps, 3))
+    ctx.profile_select(None)
+    ctx.profile(True)
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(psteps):
+        step()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    phases = ctx.profile_read()
+    ctx.profile(False)
+    phases_ms = {k: round(v[0] / psteps, 3) for k, v in phases.items()}
+    profiled_ms = p0.elapsed_time(p1) / psteps
     norms = ctx.residual_norms(A, X, B)
     res = float(ctx.scaled_residual(A, X, B).max())
     # the paper's own shape of the check, ||r|| / (n ||b|| eps), eps = 2^-53
     res_paper = float(max(r[0] / (n * r[3] * 2.0 ** -53) if r[3] > 0 else math.inf for r in norms))
     return {"A": A, "B": B, "X": X, "ms": ms, "prof": prof, "launches": launches, "res": res, "clocks": ck,
-            "res_paper": res_paper,
+            "res_paper": res_paper, "phases_ms": phases_ms, "profiled_ms": profiled_ms,
             "refine_iters": iters[-1] if iters else None}
 
 
@@ -503,6 +521,25 @@ def served_measure(cfg: dict, rate: float = None, seconds: float = None) -> dict
             "wall_s": t_end - t0}
 
 
+def mixed_companion(ctx, stream, mname, args, rank, ws, peaks, f64_flops=None, f64_ms=None) -> dict:
+    """One mixed-precision companion line (BF16/FP16 tensor-core factor + FP64
+    refinement), timed by the same rules as the headline."""
+    import torch
+    mc = WORKLOADS[mname]
+    mr = timed_solves(ctx, stream, mc, mc["nb"], args.steps, args.warmup, rank, ws)
+    mv = hpl_flops(mc["n"], mc["nrhs"]) * ws / (mr["ms"] * 1e-3) / 1e12
+    line = {"workload": mname, "value": mv, "unit": "TFLOP/s", "ms_per_step": mr["ms"], "nrhs": mc["nrhs"],
+            "scaled_residual": mr["res"], "refine_iters": mr["refine_iters"],
+            "roofline": gemm_roofline(mr["prof"], mc["n"], mc["nb"], mc["prec"], args.steps, peaks, mname),
+            "phases_ms_per_step": mr["phases_ms"], "profiled_ms_per_step": mr["profiled_ms"],
+            "_launches": mr["launches"]}
+    if f64_flops:
+        line["speedup_vs_f64"] = mv / (f64_flops * ws / (f64_ms * 1e-3) / 1e12)
+    del mr
+    torch.cuda.empty_cache()
+    return line
+
+
 def run_ours(args, cfg, wname):
     import torch
     from paper_2202_13995_gb300 import lu
@@ -523,6 +560,7 @@ def run_ours(args, cfg, wname):
     A, B = r["A"], r["B"]
     ms, prof, launches = r["ms"], r["prof"], r["launches"]
     res, ck, res_paper = r["res"], r["clocks"], r["res_paper"]
+    phases_ms, profiled_ms = r["phases_ms"], r["profiled_ms"]
     ozaki = bool(cfg.get("ozaki", False))
     roofline = gemm_roofline(prof, n, nb, prec, args.steps, peaks, wname, ozaki)
 
@@ -541,16 +579,28 @@ def run_ours(args, cfg, wname):
         Xd = lu.colmajor_empty(n, nrhs)
         assert Ad.t().is_contiguous() and Bd.t().is_contiguous() and Xd.t().is_contiguous()
 
-        def e2e_step():
+        seg = []  # per step: events at start, after the H2D copies, after the solve, after the D2H copy
+
+        def e2e_step(record=False):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if record else None
+            if record:
+                ev[0].record(stream)
             Ad.t().copy_(Ah, non_blocking=True)
             Bd.t().copy_(Bh, non_blocking=True)
+            if record:
+                ev[1].record(stream)
             f = ctx.factor(Ad, prec, nb, sync=False, nopiv=bool(cfg.get("nopiv", False)), ozaki=ozaki)
             if mixed and not cfg.get("norefine", False):
                 f.refine(Ad, Bd, Xd, 16.0, 50)
             else:
                 Xd.copy_(Bd)
                 f.solve_(Xd)
+            if record:
+                ev[2].record(stream)
             Xh.copy_(Xd.t(), non_blocking=True)
+            if record:
+                ev[3].record(stream)
+                seg.append(ev)
             f.free()
 
         e2e_step()
@@ -561,12 +611,18 @@ def run_ours(args, cfg, wname):
         ke = max(1, min(args.steps, 3))
         e0.record(stream)
         for _ in range(ke):
-            e2e_step()
+            e2e_step(record=True)
         e1.record(stream)
         torch.cuda.synchronize()
         ems = max_over_ranks(e0.elapsed_time(e1) / ke, ws)
+        h2d_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in seg)
+        solve_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in seg)
+        d2h_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in seg)
+        h2d_bytes = int(A.numel() * 8 + n * nrhs * 8)
         e2e = {"value": flops * ws / (ems * 1e-3) / 1e12, "unit": "TFLOP/s", "ms_per_step": ems,
-               "h2d_bytes_per_step": int(A.numel() * 8 + n * nrhs * 8), "d2h_bytes_per_step": int(n * nrhs * 8)}
+               "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": int(n * nrhs * 8),
+               "segments_ms_per_step": {"h2d": h2d_ms, "solve": solve_ms, "d2h": d2h_ms},
+               "h2d_gbs": h2d_bytes / (h2d_ms * 1e-3) / 1e9 if h2d_ms > 0 else None}
         del Ah, Bh, Xh, Ad, Bd, Xd
     del r, A, B
     torch.cuda.empty_cache()
@@ -584,23 +640,17 @@ def run_ours(args, cfg, wname):
         nopiv_line = {"workload": pname, "value": pv, "unit": "TFLOP/s", "ms_per_step": pr["ms"],
                       "lu_only_tflops": 2.0 / 3.0 * pc["n"] ** 3 * ws / (pr["ms"] * 1e-3) / 1e12,
                       "scaled_residual": pr["res"], "refine_iters": pr["refine_iters"],
-                      "phases_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in pr["prof"].items()}}
+                      "phases_ms_per_step": pr["phases_ms"], "profiled_ms_per_step": pr["profiled_ms"]}
         launches += pr["launches"]
         del pr
         torch.cuda.empty_cache()
-        mname = "hpl_mixed_bf16_n32768"
-        mc = WORKLOADS[mname]
-        mr = timed_solves(ctx, stream, mc, mc["nb"], args.steps, args.warmup, rank, ws)
-        mflops = hpl_flops(mc["n"], mc["nrhs"])
-        mv = mflops * ws / (mr["ms"] * 1e-3) / 1e12
-        mixed_line = {"workload": mname, "value": mv, "unit": "TFLOP/s", "ms_per_step": mr["ms"],
-                      "speedup_vs_f64": mv / (flops * ws / (ms * 1e-3) / 1e12), "scaled_residual": mr["res"],
-                      "refine_iters": mr["refine_iters"],
-                      "roofline": gemm_roofline(mr["prof"], mc["n"], mc["nb"], mc["prec"], args.steps, peaks, mname),
-                      "phases_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in mr["prof"].items()}}
-        launches += mr["launches"]
-        del mr
-        torch.cuda.empty_cache()
+        mixed_line = mixed_companion(ctx, stream, "hpl_mixed_bf16_n32768", args, rank, ws, peaks, flops, ms)
+        launches += mixed_line.pop("_launches")
+        # the same configuration with FP16 operands, and with 32 right-hand sides
+        for key, nm in (("fp16", "hpl_mixed_fp16_n32768"), ("rhs32", "hpl_mixed_bf16_n32768_rhs32")):
+            ln = mixed_companion(ctx, stream, nm, args, rank, ws, peaks, None, None)
+            launches += ln.pop("_launches")
+            mixed_line[key] = ln
 
     ozaki_line = None
     if not mixed and not args.no_mixed and wname == DEFAULT:
@@ -613,7 +663,7 @@ def run_ours(args, cfg, wname):
                       "speedup_vs_f64": ov / (flops * ws / (ms * 1e-3) / 1e12), "scaled_residual": orr["res"],
                       "roofline": gemm_roofline(orr["prof"], oc["n"], oc["nb"], oc["prec"], args.steps, peaks, oname,
                                                 True),
-                      "phases_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in orr["prof"].items()}}
+                      "phases_ms_per_step": orr["phases_ms"], "profiled_ms_per_step": orr["profiled_ms"]}
         launches += orr["launches"]
         del orr
         torch.cuda.empty_cache()
@@ -646,7 +696,8 @@ def run_ours(args, cfg, wname):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
-            "phases_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in prof.items()},
+            "phases_ms_per_step": phases_ms,
+            "profiled_ms_per_step": profiled_ms,
             "clocks": ck,
             "mixed": mixed_line,
             "paper_nopiv": nopiv_line,

@@ -39,6 +39,7 @@ struct lu_ctx_s {
   // launch accounting and optional per-phase event timing
   long long launches = 0;
   bool prof = false;
+  unsigned prof_mask = ~0u;  // phases recorded while profiling (bit p = phase p)
   struct Rec {
     int phase;
     int nk;
@@ -70,13 +71,14 @@ static cudaEvent_t ev_get(lu_ctx c) {
 template <typename F>
 static cudaError_t run_phase(lu_ctx c, int phase, int nk, cudaStream_t st, F&& launch) {
   cudaEvent_t a = nullptr, b = nullptr;
-  if (c->prof) {
+  const bool rec = c->prof && ((c->prof_mask >> phase) & 1u);
+  if (rec) {
     a = ev_get(c);
     b = ev_get(c);
     cudaEventRecord(a, st);
   }
   cudaError_t e = launch();
-  if (c->prof) {
+  if (rec) {
     cudaEventRecord(b, st);
     c->recs.push_back({phase, nk, a, b});
   }
@@ -222,6 +224,12 @@ extern "C" long long lu_launch_count(lu_ctx c) { return c ? c->launches : 0; }
 extern "C" int lu_profile_enable(lu_ctx c, int enable) {
   if (!c) return -1;
   c->prof = enable != 0;
+  return LU_OK;
+}
+
+extern "C" int lu_profile_select(lu_ctx c, unsigned phase_mask) {
+  if (!c) return -1;
+  c->prof_mask = phase_mask;
   return LU_OK;
 }
 

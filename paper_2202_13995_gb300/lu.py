@@ -30,7 +30,7 @@ EXPORTED = [
     "lu_create", "lu_destroy", "lu_strerror", "lu_factor", "lu_fact_info", "lu_fact_ipiv", "lu_fact_lu",
     "lu_solve", "lu_refine", "lu_scaled_residual", "lu_residual_norms", "lu_fact_free",
     "lu_step_panel", "lu_step_trsm", "lu_step_gemm", "lu_ctx_status", "lu_device_sm_count", "lu_build_tag",
-    "lu_profile_enable", "lu_profile_read", "lu_launch_count", "lu_step_panel_static",
+    "lu_profile_enable", "lu_profile_select", "lu_profile_read", "lu_launch_count", "lu_step_panel_static",
     "lu_batch_create", "lu_batch_run", "lu_batch_shape", "lu_batch_free", "lu_solve_batched",
     "lu_server_create", "lu_server_submit", "lu_server_poll", "lu_server_wait", "lu_server_stats",
     "lu_server_destroy", "lu_fact_bytes", "lu_factor_ex", "lu_step_gemm_ozaki", "lu_step_wait_probe",
@@ -96,6 +96,7 @@ def load():
             "lu_device_sm_count": (I, [P]),
             "lu_build_tag": (C.c_char_p, []),
             "lu_profile_enable": (I, [P, I]),
+            "lu_profile_select": (I, [P, C.c_uint]),
             "lu_profile_read": (I, [P, DP, C.POINTER(C.c_longlong)]),
             "lu_launch_count": (C.c_longlong, [P]),
             "lu_step_panel_static": (I, [P, I, I, I, P, I, P, P, P]),
@@ -215,6 +216,11 @@ class Context:
 
     def profile(self, enable: bool = True):
         _check(load().lu_profile_enable(self._h, 1 if enable else 0), "lu_profile_enable")
+
+    def profile_select(self, phases=None):
+        """Record only these phases while profiling (names from PHASES; None = all)."""
+        mask = 0xFFFFFFFF if phases is None else sum(1 << PHASES.index(p) for p in phases)
+        _check(load().lu_profile_select(self._h, mask), "lu_profile_select")
 
     def profile_read(self) -> dict:
         """{phase: (milliseconds, launches)} since the last read (synchronizes)."""
