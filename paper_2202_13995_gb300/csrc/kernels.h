@@ -58,9 +58,14 @@ int panel_grid_size(int m, int w, int tsize, const DevInfo& dev, int gmax, int g
 // partial pivoting.  Writes ipiv[k..k+w) (1-based, absolute), lowers *info to
 // the first zero pivot (absolute, 1-based; the caller initialises it to
 // INT_MAX), and the panel's net row permutation into scratch.perm.
+// With spec_flag set (the diagonal-pivot check ran first, see SpecArgs) the
+// launch returns at once when the check passed, and otherwise restores the
+// rows the check changed from spec_backup (row-major, ld = w) before it
+// factors the panel.
 template <typename T>
 cudaError_t launch_panel(T* Wkk, int64_t ldw, int m, int w, int kabs, int* ipiv, int* info, int* status,
-                         const PanelScratch& s, const DevInfo& dev, cudaStream_t st);
+                         const PanelScratch& s, const DevInfo& dev, cudaStream_t st, const int* spec_flag = nullptr,
+                         const T* spec_backup = nullptr);
 
 // The FP32 panel on one thread-block cluster (panel_cluster.cu): same
 // arguments and outputs as launch_panel; used by launch_panel<float> when
@@ -91,12 +96,38 @@ cudaError_t launch_from_working(const T* W, int64_t ldw, double* LU, int64_t ldl
 cudaError_t launch_iota(int* v, int n, cudaStream_t st, int base = 0);
 
 // ---------------------------------------------------------------- nopiv.cu
+// Diagonal-pivot check of a pivoted panel (FP32 panels).  Partial pivoting
+// picks row j in column j when |a_jj| is the largest candidate; the two
+// kernels below first factor the m x w panel as if every pivot were on the
+// diagonal (its diagonal block, then the rows below it) and accept the result
+// only if every multiplier satisfies |l_ij| <= 1/2 (the diagonal candidate at
+// least twice any other, so the pivot search would have chosen it) and every
+// pivot is finite and nonzero.  Otherwise they record the failure, the panel
+// kernel restores the rows they changed from `backup` and factors the panel
+// with the full pivot search.
+//   flag[0]: 0 while every checked panel passed, 1 after a failure (sticky);
+//   flag[1]: kabs + 1 of the panel that failed;  flag[2]: the stage that
+//   failed (1: the diagonal block, only its w rows changed; 2: the rows below,
+//   every row changed).
+// A panel whose check fails leaves speculation off for the later panels of
+// the factorization (their check kernels return at once).
+struct SpecArgs {
+  int* flag = nullptr;   // 3 ints, device (zeroed per factorization)
+  void* backup = nullptr;  // m x w, row-major, ld = w: the panel's rows before the check
+  int* ipiv = nullptr;   // absolute ipiv (identity written on the diagonal block's pass)
+  int* perm = nullptr;   // panel permutation record (count 0 written likewise)
+};
+
 // The no-pivot variant's block operations: LU of the w x w diagonal block at D
-// (one CTA), and X (m x w) <- X U^-1 with U the upper w x w block at U.
+// (one CTA), and X (m x w) <- X U^-1 with U the upper w x w block at U.  With
+// spec.flag set they run as the two stages of the diagonal-pivot check of a
+// pivoted panel (kabs: the panel's first absolute column).
 template <typename T>
-cudaError_t launch_diag_lu(T* D, int64_t ld, int w, int kabs, int* info, cudaStream_t st);
+cudaError_t launch_diag_lu(T* D, int64_t ld, int w, int kabs, int* info, cudaStream_t st,
+                           const SpecArgs& spec = SpecArgs());
 template <typename T>
-cudaError_t launch_trsm_right_upper(const T* U, T* X, int64_t ld, int m, int w, cudaStream_t st);
+cudaError_t launch_trsm_right_upper(const T* U, T* X, int64_t ld, int m, int w, cudaStream_t st,
+                                    const SpecArgs& spec = SpecArgs(), int kabs = 0);
 
 // ---------------------------------------------------------------- gemm_simt.cu
 // C (m x n) -= A (m x k) * B (k x n), all row-major in T, CUDA-core FMA.

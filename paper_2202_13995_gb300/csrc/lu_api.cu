@@ -51,6 +51,10 @@ struct lu_ctx_s {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_next = nullptr, ev_panel = nullptr;
   bool lookahead = true;
+  // diagonal-pivot check of FP32 panels, and the SMs its lookahead panels keep
+  // (the trailing update gets the rest)
+  bool spec = true;
+  int spec_sms = 24;
 };
 
 enum { PH_PANEL = 0, PH_LASWP, PH_TRSM, PH_CAST, PH_GEMM, PH_SOLVE, PH_RESID, PH_OTHER, PH_N };
@@ -107,6 +111,8 @@ struct lu_fact_s {
   bool ozaki = false;   // FP64 trailing update by error-free splitting
   void* oz_ws = nullptr;
   double* oz_minv = nullptr;  // nb x nb: I - L11^-1 of the current block
+  int* spec_flag = nullptr;   // diagonal-pivot check flags (SpecArgs), FP32 panels
+  void* spec_backup = nullptr;  // n x nb FP32: a checked panel's rows before the check
   void* solve_mem = nullptr;
   SolveScratch ss{};
   double* vec_ws = nullptr;  // refinement: R, D, partial sums
@@ -190,6 +196,9 @@ extern "C" int lu_create(lu_ctx* out, void* cuda_stream) {
     return LU_ECUDA;
   }
   if (getenv("GB300LU_NO_LOOKAHEAD")) c->lookahead = false;
+  // the cluster panel kernel has no restore step for a failed check
+  if (getenv("GB300LU_NO_SPEC") || getenv("GB300LU_PANEL_CLUSTER")) c->spec = false;
+  if (const char* e = getenv("GB300LU_SPEC_SMS")) c->spec_sms = atoi(e);
   *out = c;
   return LU_OK;
 }
@@ -292,6 +301,41 @@ static cudaError_t top_solve_split(lu_fact f, const double* L11, double* A12, in
   return PHASE(c, PH_TRSM, 1, ozaki_gemm(A12, ld, f->oz_ws, w, N, w, 0, N, c->d_status, c->dev, st));
 }
 
+// Diagonal-pivot check (FP32 panels; SpecArgs in kernels.h).  The first
+// panel is checked and the host waits for the verdict: if it passed, the
+// later panels are checked too and their lookahead keeps only spec_sms SMs
+// (the check's two kernels and, should a check fail, the pivoted panel that
+// redoes it); if it failed, every panel takes the pivoted kernel at once and
+// the lookahead keeps its usual share.  A later failure is seen by the host
+// through an asynchronous copy of the flags and switches the rest of the
+// factorization to the pivoted kernel's split.
+enum { SPEC_OFF = 0, SPEC_TRY, SPEC_ON };
+
+template <typename T>
+static cudaError_t panel_step(lu_fact f, int mode, T* Wkk, int m, int w, int kabs, cudaStream_t s, int gtarget) {
+  lu_ctx c = f->ctx;
+  const int64_t ld = f->ldw;
+  PanelScratch ps = f->ps;
+  if (gtarget > 0) ps.gtarget = gtarget;
+  if (mode == SPEC_OFF)
+    return PHASE_ON(c, s, PH_PANEL, 1, launch_panel<T>(Wkk, ld, m, w, kabs, f->ipiv, f->info_d, c->d_status, ps,
+                                                      c->dev, s));
+  SpecArgs sa;
+  sa.flag = f->spec_flag;
+  sa.backup = f->spec_backup;
+  sa.ipiv = f->ipiv;
+  sa.perm = f->ps.perm;
+  cudaError_t e = PHASE_ON(c, s, PH_PANEL, 1, launch_diag_lu<T>(Wkk, ld, w, kabs, nullptr, s, sa));
+  if (e != cudaSuccess) return e;
+  if (m > w) {
+    e = PHASE_ON(c, s, PH_PANEL, 1,
+                 launch_trsm_right_upper<T>(Wkk, Wkk + (int64_t)w * ld, ld, m - w, w, s, sa, kabs));
+    if (e != cudaSuccess) return e;
+  }
+  return PHASE_ON(c, s, PH_PANEL, 1, launch_panel<T>(Wkk, ld, m, w, kabs, f->ipiv, f->info_d, c->d_status, ps,
+                                                    c->dev, s, f->spec_flag, (const T*)f->spec_backup));
+}
+
 template <typename T>
 static int factor_loop(lu_fact f) {
   lu_ctx c = f->ctx;
@@ -309,16 +353,25 @@ static int factor_loop(lu_fact f) {
   // runs fastest on every SM, and the update needs whole SMs for its shared
   // memory, so a concurrent panel would slow both)
   const bool lookahead = tc && c->lookahead && c->side != nullptr;
+  int mode = (sizeof(T) == 4 && f->spec_flag != nullptr && n > nb) ? SPEC_TRY : SPEC_OFF;
+  int* hflag = c->h_pinned + 48;  // [4]: verdict of the first panel; [4..8): later panels, copied asynchronously
+  const int spec_sms = c->spec_sms > 0 ? c->spec_sms : 1;
   bool panel_ready = false;
   for (int k = 0; k < n; k += nb) {
     const int w = (n - k) < nb ? (n - k) : nb;
     T* Wkk = W + (int64_t)k * ld + k;
+    if (mode == SPEC_ON && (hflag[4] != 0 || hflag[7] != 0)) mode = SPEC_OFF;  // a later panel failed its check
     if (panel_ready) {
       CU_TRY(cudaStreamWaitEvent(st, c->ev_panel, 0));
       panel_ready = false;
     } else {
-      CU_TRY(PHASE(c, PH_PANEL, 1, launch_panel<T>(Wkk, ld, n - k, w, k, f->ipiv, f->info_d, c->d_status, f->ps,
-                                                   c->dev, st)));
+      CU_TRY(panel_step<T>(f, mode, Wkk, n - k, w, k, st, 0));
+      if (mode == SPEC_TRY) {
+        CU_TRY(cudaMemcpyAsync(hflag, f->spec_flag, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CU_TRY(cudaStreamSynchronize(st));
+        mode = (hflag[0] == 0 && hflag[3] == 0) ? SPEC_ON : SPEC_OFF;
+        hflag[4] = hflag[7] = 0;
+      }
     }
     CU_TRY(PHASE(c, PH_LASWP, 1, launch_laswp<T>(W, ld, n, k, w, f->ps.perm, f->rowid, st)));
     const int rest = n - k - w;
@@ -356,13 +409,21 @@ static int factor_loop(lu_fact f) {
     CU_TRY(cudaEventRecord(c->ev_next, st));
     CU_TRY(cudaStreamWaitEvent(c->side, c->ev_next, 0));
     T* Wn = A22;  // W(k + w, k + w)
-    CU_TRY(PHASE_ON(c, c->side, PH_PANEL, 1, launch_panel<T>(Wn, ld, rest, w2, k + w, f->ipiv, f->info_d,
-                                                             c->d_status, f->ps, c->dev, c->side)));
+    // the SMs the lookahead panel keeps: its checked form needs few; the
+    // pivoted kernel keeps its usual share
+    int gp = panel_sm_use(rest, w2, sizeof(T), c->dev, f->ps);
+    if (mode == SPEC_ON) {
+      // (a tall panel needs a few more CTAs than spec_sms for its tile to fit)
+      const int gc = panel_grid_size(rest, w2, sizeof(T), c->dev, f->ps.gmax, spec_sms);
+      gp = gc > spec_sms ? gc : spec_sms;
+    }
+    CU_TRY(panel_step<T>(f, mode, Wn, rest, w2, k + w, c->side, mode == SPEC_ON ? spec_sms : 0));
+    if (mode == SPEC_ON)
+      CU_TRY(cudaMemcpyAsync(hflag + 4, f->spec_flag, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->side));
     CU_TRY(cudaEventRecord(c->ev_panel, c->side));
     panel_ready = true;
     // the rest of the trailing matrix on the SMs the panel leaves free (the
     // latency-bound panel runs slower on SMs it shares with the update)
-    const int gp = panel_sm_use(rest, w2, sizeof(T), c->dev, f->ps);
     const int cap = c->dev.sm_count - (gp > 0 ? gp : 0);
     const void* bop2 = (const char*)f->bop + (size_t)w2 * f->kpad * 2;
     CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)(A22 + w2), ld, f->aop, bop2, rest, rest - w2, f->kpad,
@@ -450,6 +511,8 @@ extern "C" void lu_fact_free(lu_fact f) {
   dfree(c, f->aop);
   dfree(c, f->oz_ws);
   dfree(c, f->oz_minv);
+  dfree(c, f->spec_flag);
+  dfree(c, f->spec_backup);
   dfree(c, f->solve_mem);
   dfree(c, f->ss.dinv);
   dfree(c, f->vec_ws);
@@ -519,6 +582,13 @@ extern "C" int lu_factor_ex(lu_ctx c, int n, const double* dA, int lda, lu_prec 
       return rc;
     }
   }
+  if (prec != LU_F64 && !nopiv && c->spec && n > f->nb) {
+    if ((rc = dalloc(c, (void**)&f->spec_flag, 4 * sizeof(int))) ||
+        (rc = dalloc(c, &f->spec_backup, (size_t)nn * f->nb * f->tsize))) {
+      lu_fact_free(f);
+      return rc;
+    }
+  }
   if (prec == LU_BF16 || prec == LU_FP16) {
     f->kpad = round_up(f->nb, 64);
     if ((rc = dalloc(c, &f->aop, (size_t)2 * nn * f->kpad * 2 + 1024))) {
@@ -533,6 +603,7 @@ extern "C" int lu_factor_ex(lu_ctx c, int n, const double* dA, int lda, lu_prec 
     return r;
   };
   if (cudaMemsetAsync(f->info_d, 0x7f, sizeof(int), st) != cudaSuccess) return fail(LU_ECUDA);
+  if (f->spec_flag && cudaMemsetAsync(f->spec_flag, 0, 4 * sizeof(int), st) != cudaSuccess) return fail(LU_ECUDA);
   if (n > 0) {
     if (PHASE(c, PH_OTHER, 1, launch_iota(f->rowid, n, st)) != cudaSuccess) return fail(LU_ECUDA);
     if (nopiv && PHASE(c, PH_OTHER, 1, launch_iota(f->ipiv, n, st, 1)) != cudaSuccess) return fail(LU_ECUDA);
@@ -937,6 +1008,7 @@ size_t gb_fact_bytes(int n, int nrhs, lu_prec prec, int nb, int sm_count) {
   size_t b = ldw * nn * tsize + (size_t)(2 * nn + 64) * sizeof(int) + panel_scratch_bytes(sm_count, 32, nb, tsize) +
              solve_scratch_bytes(nn, tsize);
   if (prec != LU_F64) b += solve_dinv_bytes(nn, tsize);
+  if (prec != LU_F64 && n > nb) b += 4 * sizeof(int) + (size_t)nn * nb * tsize;  // diagonal-pivot check
   if (prec == LU_BF16 || prec == LU_FP16) b += (size_t)2 * nn * round_up(nb, 64) * 2 + 1024;
   const int nr = nrhs > 32 ? 32 : (nrhs < 1 ? 1 : nrhs);
   b += 2 * (size_t)nn * nrhs * 8 + residual_partial_bytes(nn, nr) + 4096;

@@ -58,11 +58,32 @@ constexpr int np_threads() {
   return sizeof(T) == 8 ? 256 : 512;
 }
 
+// Device view of SpecArgs (the diagonal-pivot check of a pivoted panel).
+// Flags: [0] sticky failure, [1] kabs + 1 of a panel whose diagonal block
+// failed, [3] kabs + 1 of a panel whose rows below the block failed.
+template <typename T>
+struct SpecDev {
+  int* flag;
+  T* backup;
+  int* ipiv;
+  int* perm;
+};
+
+template <typename T>
+__device__ __forceinline__ bool spec_ok_mult(T l) {
+  return l <= T(0.5) && l >= T(-0.5);  // false for NaN
+}
+
 // In-place LU (no pivoting) of the w x w block at D (row-major, ld), blocked by
 // 32 columns; one CTA of np_threads<T>() threads.  Lowers *info to kabs + j + 1 at the
 // first exactly zero pivot j (and skips that column's scaling).
+// With sp.flag set it is the first stage of a pivoted panel's diagonal-pivot
+// check: it saves the block to sp.backup, writes the identity pivots and an
+// empty permutation record, leaves *info alone, and on a multiplier above 1/2
+// or a zero or non-finite pivot records the failure (flag[1], then flag[0]).
 template <typename T>
-__global__ void __launch_bounds__(np_threads<T>()) diag_lu_kernel(T* D, int64_t ld, int w, int kabs, int* info) {
+__global__ void __launch_bounds__(np_threads<T>()) diag_lu_kernel(T* D, int64_t ld, int w, int kabs, int* info,
+                                                                  SpecDev<T> sp) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int wp = (w + 3) & ~3;
   T* P = reinterpret_cast<T*>(smem_raw);  // [NP_NB][wp]: column c of the sub-panel, row r
@@ -71,6 +92,22 @@ __global__ void __launch_bounds__(np_threads<T>()) diag_lu_kernel(T* D, int64_t 
   constexpr int NP_NT = np_threads<T>();
   constexpr int CH = 16 / sizeof(T);  // elements per 16-byte access
   const bool vec = ((reinterpret_cast<uintptr_t>(D) & 15) == 0) && (ld % CH) == 0;
+  const bool spec = sp.flag != nullptr;
+  bool bad = false;  // a multiplier above 1/2 or a zero / non-finite pivot (spec only)
+  if (spec) {
+    // the check is off once a panel has failed it; a failure of the previous
+    // panel's rows below its block turns it off here
+    const int f0 = __ldcg(sp.flag), f3 = __ldcg(sp.flag + 3);
+    if (f0 != 0 || f3 != 0) {
+      if (tid == 0 && f0 == 0) sp.flag[0] = 1;
+      return;
+    }
+    for (int r = tid / 32; r < w; r += NP_NT / 32)
+      for (int c = tid % 32; c < w; c += 32) sp.backup[(int64_t)r * w + c] = D[(int64_t)r * ld + c];
+    for (int j = tid; j < w; j += NP_NT) sp.ipiv[kabs + j] = kabs + j + 1;
+    if (tid == 0) sp.perm[0] = 0;
+    __syncthreads();
+  }
   for (int k0 = 0; k0 < w; k0 += NP_NB) {
     const int kb = min(NP_NB, w - k0), m = w - k0;
     // thread = row (consecutive threads, consecutive rows: the column-major
@@ -91,10 +128,15 @@ __global__ void __launch_bounds__(np_threads<T>()) diag_lu_kernel(T* D, int64_t 
     __syncthreads();
     for (int j = 0; j < kb; ++j) {
       const T piv = P[j * wp + j];
-      if (tid == 0 && piv == T(0)) atomicMin(info, kabs + k0 + j + 1);
+      if (spec) {
+        if (tid == 0 && !(piv != T(0) && piv - piv == T(0))) bad = true;  // zero or non-finite pivot
+      } else if (tid == 0 && piv == T(0)) {
+        atomicMin(info, kabs + k0 + j + 1);
+      }
       for (int r = j + 1 + tid; r < m; r += NP_NT) {
         T l = P[j * wp + r];
         if (piv != T(0)) l = l / piv;
+        if (spec && !spec_ok_mult(l)) bad = true;
         P[j * wp + r] = l;
         for (int c = j + 1; c < kb; ++c) P[c * wp + r] -= l * P[c * wp + j];
       }
@@ -178,91 +220,169 @@ __global__ void __launch_bounds__(np_threads<T>()) diag_lu_kernel(T* D, int64_t 
       __syncthreads();
     }
   }
+  if (spec && __syncthreads_or(bad) && tid == 0) {
+    sp.flag[1] = kabs + 1;
+    __threadfence();
+    sp.flag[0] = 1;
+  }
 }
 
 // X (m x w, row-major, ld) <- X U^-1 with U the upper (non-unit) w x w block at
-// U (row-major, ld): the paper's "left" block update.  CTA = 32 rows of X in
-// shared memory; by 32-column blocks: warps solve their rows against the
-// diagonal block (division by the pivot, as in the definition), then all
-// threads update the columns to the right.
-template <typename T>
-__global__ void __launch_bounds__(256) trsm_right_upper_kernel(const T* __restrict__ U, T* X, int64_t ld, int m,
-                                                               int w) {
+// U (row-major, ld): the paper's "left" block update.  CTA = RB rows of X in
+// shared memory; by 32-column blocks:
+//   1. the diagonal block: one thread per row substitutes its 32 values in
+//      registers against U's 32 x 32 diagonal block, multiplying by the
+//      reciprocals of U's diagonal (computed once per CTA);
+//   2. the columns to the right: a rank-32 update, each thread a register tile
+//      of RB/16 rows x 4 columns per 64-column chunk, U's rows staged in shared
+//      memory.
+// With sp.flag set it is the second stage of a pivoted panel's diagonal-pivot
+// check: the rows are saved to sp.backup first, and a multiplier above 1/2 in
+// magnitude (or not finite) records the panel in flag[3].  It returns at once
+// when flag[0] is set (the check is off, or the diagonal block failed it).
+constexpr int LS_THREADS = 256;
+
+template <typename T, int RB>
+__global__ void __launch_bounds__(LS_THREADS) trsm_right_upper_kernel(const T* __restrict__ U, T* X, int64_t ld,
+                                                                      int m, int w, int kabs, SpecDev<T> sp) {
+  static_assert(RB % 16 == 0 && RB <= LS_THREADS, "RB rows: 16 row groups, one thread per row");
+  constexpr int RT = RB / 16;  // rows per thread in the update
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int wp = w + 1;
-  T* Xs = reinterpret_cast<T*>(smem_raw);  // [32][wp]
-  T* Ud = Xs + 32 * wp;                    // [32][33] diagonal block
-  T* Ub = Ud + 32 * 33;                    // [32][w] U rows b0.. b0+32, columns right of the block
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int r0 = blockIdx.x * 32;
-  const int rows = min(32, m - r0);
-  for (int e = threadIdx.x; e < 32 * w; e += 256) {
-    const int r = e / w, c = e % w;
-    Xs[r * wp + c] = r < rows ? X[(int64_t)(r0 + r) * ld + c] : T(0);
+  const int wx = w | 1;          // odd row stride: a row per thread is free of bank conflicts
+  const int wu = (w + 3) & ~3;   // U stage row stride: 16-byte rows
+  T* Us = reinterpret_cast<T*>(smem_raw);  // [32][wu]: rows c0 .. c0 + 31 of U, columns c0 .. w
+  T* rcp = Us + 32 * wu;                   // [wu]: 1 / U(j, j)
+  T* Xs = rcp + wu;                        // [RB][wx]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int r0 = blockIdx.x * RB;
+  const int rows = min(RB, m - r0);
+  const bool spec = sp.flag != nullptr;
+  if (spec && __ldcg(sp.flag) != 0) return;
+  bool bad = false;
+  for (int j = tid; j < w; j += LS_THREADS) rcp[j] = T(1) / U[(int64_t)j * ld + j];
+  for (int r = warp; r < RB; r += LS_THREADS / 32) {
+    const bool ok = r < rows;
+    for (int c = lane; c < w; c += 32) {
+      const T v = ok ? X[(int64_t)(r0 + r) * ld + c] : T(0);
+      Xs[r * wx + c] = v;
+      if (spec && ok) sp.backup[(int64_t)(r0 + r) * w + c] = v;
+    }
   }
-  for (int b0 = 0; b0 < w; b0 += 32) {
-    const int bw = min(32, w - b0);
-    const int c1 = b0 + bw, nr = w - c1;
-    for (int e = threadIdx.x; e < 32 * 32; e += 256) {
-      const int s = e >> 5, t = e & 31;
-      Ud[s * 33 + t] = (s < bw && t < bw) ? U[(int64_t)(b0 + s) * ld + b0 + t] : T(0);
-    }
-    for (int e = threadIdx.x; e < bw * nr; e += 256) {
-      const int s = e / nr, c = e % nr;
-      Ub[s * w + c] = U[(int64_t)(b0 + s) * ld + c1 + c];
-    }
+  for (int c0 = 0; c0 < w; c0 += 32) {
+    const int bw = min(32, w - c0);
+    __syncthreads();  // the previous block's update is done with Us
+    for (int k = warp; k < bw; k += LS_THREADS / 32)
+      for (int c = c0 + lane; c < w; c += 32) Us[k * wu + c] = U[(int64_t)(c0 + k) * ld + c];
     __syncthreads();
-    for (int r = warp; r < 32; r += 8) {
-      T x = lane < bw ? Xs[r * wp + b0 + lane] : T(0);
-      for (int s = 0; s < bw; ++s) {
-        if (lane == s) x = x / Ud[s * 33 + s];
-        const T xs = __shfl_sync(0xffffffffu, x, s);
-        if (lane > s && lane < bw) x -= xs * Ud[s * 33 + lane];
+    if (tid < rows) {
+      T a[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) a[j] = j < bw ? Xs[tid * wx + c0 + j] : T(0);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        if (j < bw) {
+          const T x = a[j] * rcp[c0 + j];
+          if (spec && !spec_ok_mult(x)) bad = true;
+          a[j] = x;
+#pragma unroll
+          for (int k = j + 1; k < 32; ++k)
+            if (k < bw) a[k] -= x * Us[j * wu + c0 + k];
+        }
       }
-      if (lane < bw) Xs[r * wp + b0 + lane] = x;
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (j < bw) Xs[tid * wx + c0 + j] = a[j];
     }
     __syncthreads();
-    // columns right of the block: X[r][c] -= sum_s X[r][b0 + s] U[b0 + s][c]
-    for (int e = threadIdx.x; e < 32 * nr; e += 256) {
-      const int r = e / nr, c = e % nr;
-      T acc = Xs[r * wp + c1 + c];
-      for (int s = 0; s < bw; ++s) acc -= Xs[r * wp + b0 + s] * Ub[s * w + c];
-      Xs[r * wp + c1 + c] = acc;
+    const int c1 = c0 + bw;  // columns [c1, w) remain (only when bw == 32)
+    const int rg = tid >> 4, cg = tid & 15;
+    for (int cc = c1 + 4 * cg; cc < w; cc += 64) {
+      T acc[RT][4];
+#pragma unroll
+      for (int i = 0; i < RT; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[i][q] = T(0);
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) {
+        T ub[4], xa[RT];
+        load4s<T>(&Us[k * wu + cc], ub);  // columns past w are never stored
+#pragma unroll
+        for (int i = 0; i < RT; ++i) xa[i] = Xs[(RT * rg + i) * wx + c0 + k];
+#pragma unroll
+        for (int i = 0; i < RT; ++i)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[i][q] = fma(xa[i], ub[q], acc[i][q]);
+      }
+#pragma unroll
+      for (int i = 0; i < RT; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (cc + q < w) Xs[(RT * rg + i) * wx + cc + q] -= acc[i][q];
     }
-    __syncthreads();
   }
-  for (int e = threadIdx.x; e < 32 * w; e += 256) {
-    const int r = e / w, c = e % w;
-    if (r < rows) X[(int64_t)(r0 + r) * ld + c] = Xs[r * wp + c];
-  }
+  __syncthreads();
+  for (int r = warp; r < rows; r += LS_THREADS / 32)
+    for (int c = lane; c < w; c += 32) X[(int64_t)(r0 + r) * ld + c] = Xs[r * wx + c];
+  if (spec && __syncthreads_or(bad) && tid == 0) sp.flag[3] = kabs + 1;
 }
 
 template <typename T>
-cudaError_t launch_diag_lu(T* D, int64_t ld, int w, int kabs, int* info, cudaStream_t st) {
+static SpecDev<T> spec_dev(const SpecArgs& a, int64_t backup_offset) {
+  SpecDev<T> d;
+  d.flag = a.flag;
+  d.backup = a.backup ? reinterpret_cast<T*>(a.backup) + backup_offset : nullptr;
+  d.ipiv = a.ipiv;
+  d.perm = a.perm;
+  return d;
+}
+
+template <typename T>
+cudaError_t launch_diag_lu(T* D, int64_t ld, int w, int kabs, int* info, cudaStream_t st, const SpecArgs& spec) {
   if (w <= 0) return cudaSuccess;
   const int wp = (w + 3) & ~3;
   const size_t smem = ((size_t)NP_NB * wp + (size_t)NP_NB * NP_CW) * sizeof(T);
   auto kern = diag_lu_kernel<T>;
   cudaError_t e = allow_max_smem((const void*)kern);
   if (e != cudaSuccess) return e;
-  kern<<<1, np_threads<T>(), smem, st>>>(D, ld, w, kabs, info);
+  kern<<<1, np_threads<T>(), smem, st>>>(D, ld, w, kabs, info, spec_dev<T>(spec, 0));
+  return cudaGetLastError();
+}
+
+static size_t ls_smem(int rb, int w, int tsize) {
+  const size_t wu = (size_t)((w + 3) & ~3);
+  return (32 * wu + wu + (size_t)rb * (w | 1)) * tsize;
+}
+
+template <typename T, int RB>
+static cudaError_t launch_ls(const T* U, T* X, int64_t ld, int m, int w, int kabs, const SpecDev<T>& sp,
+                             cudaStream_t st) {
+  auto kern = trsm_right_upper_kernel<T, RB>;
+  cudaError_t e = allow_max_smem((const void*)kern);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)cdiv(m, RB), LS_THREADS, ls_smem(RB, w, sizeof(T)), st>>>(U, X, ld, m, w, kabs, sp);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_trsm_right_upper(const T* U, T* X, int64_t ld, int m, int w, cudaStream_t st) {
+cudaError_t launch_trsm_right_upper(const T* U, T* X, int64_t ld, int m, int w, cudaStream_t st,
+                                    const SpecArgs& spec, int kabs) {
   if (m <= 0 || w <= 0) return cudaSuccess;
-  const size_t smem = ((size_t)32 * (w + 1) + 32 * 33 + (size_t)32 * w) * sizeof(T);
-  auto kern = trsm_right_upper_kernel<T>;
-  cudaError_t e = allow_max_smem((const void*)kern);
-  if (e != cudaSuccess) return e;
-  kern<<<(unsigned)cdiv(m, 32), 256, smem, st>>>(U, X, ld, m, w);
-  return cudaGetLastError();
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  // the rows below the panel's w x w block follow it in the backup
+  const SpecDev<T> sp = spec_dev<T>(spec, (int64_t)w * w);
+  if (ls_smem(64, w, sizeof(T)) <= (size_t)optin) return launch_ls<T, 64>(U, X, ld, m, w, kabs, sp, st);
+  if (ls_smem(32, w, sizeof(T)) <= (size_t)optin) return launch_ls<T, 32>(U, X, ld, m, w, kabs, sp, st);
+  if (ls_smem(16, w, sizeof(T)) <= (size_t)optin) return launch_ls<T, 16>(U, X, ld, m, w, kabs, sp, st);
+  return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_diag_lu<double>(double*, int64_t, int, int, int*, cudaStream_t);
-template cudaError_t launch_diag_lu<float>(float*, int64_t, int, int, int*, cudaStream_t);
-template cudaError_t launch_trsm_right_upper<double>(const double*, double*, int64_t, int, int, cudaStream_t);
-template cudaError_t launch_trsm_right_upper<float>(const float*, float*, int64_t, int, int, cudaStream_t);
+template cudaError_t launch_diag_lu<double>(double*, int64_t, int, int, int*, cudaStream_t, const SpecArgs&);
+template cudaError_t launch_diag_lu<float>(float*, int64_t, int, int, int*, cudaStream_t, const SpecArgs&);
+template cudaError_t launch_trsm_right_upper<double>(const double*, double*, int64_t, int, int, cudaStream_t,
+                                                     const SpecArgs&, int);
+template cudaError_t launch_trsm_right_upper<float>(const float*, float*, int64_t, int, int, cudaStream_t,
+                                                    const SpecArgs&, int);
 
 }  // namespace gb

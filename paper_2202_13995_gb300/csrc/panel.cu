@@ -90,6 +90,8 @@ struct PanelParams {
   T* xrow;
   T* xrowj;
   int* perm;
+  const int* spec;  // diagonal-pivot check flags (SpecArgs), or null
+  const T* spec_backup;
 };
 
 __host__ __device__ inline size_t panel_smem_bytes(int R, int ib, int w, int tsize) {
@@ -127,6 +129,20 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
   int* hsv = hsk + PNL_HS;
   int* misc = hsv + PNL_HS;      // 0: fcnt 1: scnt 2: barrier flag
   unsigned nbar = 0;
+
+  if (P.spec != nullptr) {
+    // the diagonal-pivot check ran first: nothing to do if the panel passed;
+    // otherwise put back the rows it changed (this CTA's own rows; other CTAs
+    // read them only after a grid barrier)
+    const int f0 = __ldcg(P.spec), f1 = __ldcg(P.spec + 1), f3 = __ldcg(P.spec + 3);
+    if (f0 == 0 && f3 == 0) return;
+    const int tag = P.kabs + 1;
+    const int rlim = f3 == tag ? P.m : (f1 == tag ? w : 0);
+    const int rend = min(rloc, rlim - row0);
+    for (int r = warp; r < rend; r += PNL_WARPS)
+      for (int c = lane; c < w; c += 32) P.A[(int64_t)(row0 + r) * ld + c] = P.spec_backup[(int64_t)(row0 + r) * w + c];
+    __syncthreads();
+  }
 
   for (int s = tid; s < w; s += PNL_THREADS) {
     fpos[s] = s;
@@ -324,15 +340,23 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
       }
     }
   }
-  // ---- whole-panel permutation for the row interchanges outside the panel
+  // ---- whole-panel permutation for the row interchanges outside the panel:
+  //      only the positions whose row moved (none when every pivot was on
+  //      the diagonal, and the interchange kernel then has nothing to do)
   if (cta == 0) {
     __syncthreads();
     const int fcnt = misc[0];
-    if (tid == 0) P.perm[0] = fcnt;
+    if (tid == 0) misc[3] = 0;
+    __syncthreads();
     for (int s2 = tid; s2 < fcnt; s2 += PNL_THREADS) {
-      P.perm[1 + s2] = fpos[s2];
-      P.perm[1 + 2 * w + s2] = fcur[s2];
+      if (fpos[s2] != fcur[s2]) {
+        const int q = atomicAdd(&misc[3], 1);
+        P.perm[1 + q] = fpos[s2];
+        P.perm[1 + 2 * w + q] = fcur[s2];
+      }
     }
+    __syncthreads();
+    if (tid == 0) P.perm[0] = misc[3];
   }
 }
 
@@ -368,14 +392,18 @@ int panel_grid_size(int m, int w, int tsize, const DevInfo& dev, int gmax, int g
   static const int forced = getenv("GB300LU_PANEL_G") ? atoi(getenv("GB300LU_PANEL_G")) : 0;
   if (forced > 0) target = forced < cap ? forced : cap;
   const size_t budget = (size_t)dev.max_smem_optin - 48 * 1024;
+  auto fits = [&](int r) {
+    return (size_t)PNL_IB * (r | 1) * tsize <= budget &&
+           panel_smem_bytes(r, PNL_IB, w, tsize) <= (size_t)dev.max_smem_optin;
+  };
   int R = (int)cdiv(m, target);
   if (R < 64) R = 64;
-  while ((size_t)PNL_IB * (R | 1) * tsize > budget && target < cap) {
+  while (!fits(R) && target < cap) {
     ++target;
     R = (int)cdiv(m, target);
+    if (R < 64) R = 64;
   }
-  if ((size_t)PNL_IB * (R | 1) * tsize > budget) return -1;
-  if (panel_smem_bytes(R, PNL_IB, w, tsize) > (size_t)dev.max_smem_optin) return -1;
+  if (!fits(R)) return -1;
   return (int)cdiv(m, R);
 }
 
@@ -396,10 +424,14 @@ int panel_sm_use(int m, int w, int tsize, const DevInfo& dev, const PanelScratch
 
 template <typename T>
 cudaError_t launch_panel(T* Wkk, int64_t ldw, int m, int w, int kabs, int* ipiv, int* info, int* status,
-                         const PanelScratch& s, const DevInfo& dev, cudaStream_t st) {
+                         const PanelScratch& s, const DevInfo& dev, cudaStream_t st, const int* spec_flag,
+                         const T* spec_backup) {
   if (w <= 0 || m < w || w > s.wmax) return cudaErrorInvalidValue;
   if constexpr (sizeof(T) == 4) {
-    if (use_cluster_panel(m, w, 4)) return launch_panel_cluster(Wkk, ldw, m, w, kabs, ipiv, info, status, s.perm, st);
+    if (use_cluster_panel(m, w, 4)) {
+      if (spec_flag != nullptr) return cudaErrorInvalidValue;  // no restore step in the cluster kernel
+      return launch_panel_cluster(Wkk, ldw, m, w, kabs, ipiv, info, status, s.perm, st);
+    }
   }
   if (s.gmax > PNL_XG) return cudaErrorInvalidValue;  // every candidate row fits the exchange buffer
   const int ib = PNL_IB < s.ibmax ? PNL_IB : s.ibmax;
@@ -435,6 +467,8 @@ cudaError_t launch_panel(T* Wkk, int64_t ldw, int m, int w, int kabs, int* ipiv,
   P.xrow = (T*)s.xrow;
   P.xrowj = (T*)s.xrowj;
   P.perm = s.perm;
+  P.spec = spec_flag;
+  P.spec_backup = spec_backup;
   void* args[] = {&P};
   // A cooperative launch is refused (without side effects) while other
   // in-flight cooperative grids -- other streams' panels -- hold the resources
@@ -652,7 +686,7 @@ cudaError_t launch_iota(int* v, int n, cudaStream_t st, int base) {
 
 #define GB_INST(T)                                                                                              \
   template cudaError_t launch_panel<T>(T*, int64_t, int, int, int, int*, int*, int*, const PanelScratch&,      \
-                                       const DevInfo&, cudaStream_t);                                           \
+                                       const DevInfo&, cudaStream_t, const int*, const T*);                     \
   template cudaError_t launch_laswp<T>(T*, int64_t, int, int, int, const int*, int*, cudaStream_t);            \
   template cudaError_t launch_trsm_lower<T>(const T*, T*, int64_t, int, int, cudaStream_t);                    \
   template cudaError_t launch_to_working<T>(const double*, int64_t, T*, int64_t, int, cudaStream_t);           \

@@ -31,7 +31,8 @@ def _dev(a):
     return t
 
 
-@pytest.mark.parametrize("n,nb", [(1, 64), (63, 64), (500, 64), (1500, 256), (2049, 128), (700, 100)])
+@pytest.mark.parametrize("n,nb", [(1, 64), (63, 64), (500, 64), (1500, 256), (2049, 128), (700, 100), (1100, 512),
+                                  (1000, 384)])
 def test_nopiv_f64_vs_oracle(ctx, n, nb):
     A = I.hpl_matrix(n, 80 + n, diag_shift=n / 4)
     B = I.hpl_rhs(n, 2, 80 + n)
