@@ -418,6 +418,18 @@ cudaError_t launch_cast_operands(int kind, const float* L21, const float* U12, i
   return cudaGetLastError();
 }
 
+cudaError_t launch_cast_b(int kind, const float* U12, int64_t ldw, int n, int k, void* Bop, int kpad, int* status,
+                          cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  if ((kpad % 64) != 0 || k > kpad) return cudaErrorInvalidValue;
+  dim3 gb_((unsigned)cdiv(n, 32), (unsigned)cdiv(kpad, 32));
+  if (kind == 1)
+    cast_b_kernel<__nv_bfloat16><<<gb_, dim3(32, 8), 0, st>>>(U12, ldw, n, k, (__nv_bfloat16*)Bop, kpad, status);
+  else
+    cast_b_kernel<__half><<<gb_, dim3(32, 8), 0, st>>>(U12, ldw, n, k, (__half*)Bop, kpad, status);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ host side
 typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                     const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,

@@ -97,37 +97,40 @@ cudaError_t launch_iota(int* v, int n, cudaStream_t st, int base = 0);
 
 // ---------------------------------------------------------------- nopiv.cu
 // Diagonal-pivot check of a pivoted panel (FP32 panels).  Partial pivoting
-// picks row j in column j when |a_jj| is the largest candidate; the two
-// kernels below first factor the m x w panel as if every pivot were on the
-// diagonal (its diagonal block, then the rows below it) and accept the result
-// only if every multiplier satisfies |l_ij| <= 1/2 (the diagonal candidate at
-// least twice any other, so the pivot search would have chosen it) and every
-// pivot is finite and nonzero.  Otherwise they record the failure, the panel
-// kernel restores the rows they changed from `backup` and factors the panel
-// with the full pivot search.
-//   flag[0]: 0 while every checked panel passed, 1 after a failure (sticky);
-//   flag[1]: kabs + 1 of the panel that failed;  flag[2]: the stage that
-//   failed (1: the diagonal block, only its w rows changed; 2: the rows below,
-//   every row changed).
+// picks row j in column j when |a_jj| is the largest candidate; the block
+// column kernels below first factor the m x w panel as if every pivot were on
+// the diagonal and accept the result only if every multiplier satisfies
+// |l_ij| <= 1/2 (the diagonal candidate at least twice any other, so the pivot
+// search would have chosen it) and every pivot is finite and nonzero.
+// Otherwise they record the failure, the panel kernel restores the rows they
+// changed from `backup` and factors the panel with the full pivot search.
+//   flag[0]: 0 while every checked stage passed, 1 after a failure (sticky);
+//   flag[1]: kabs + 1 of a panel whose slab (see launch_block_column) failed,
+//            flag[2]: the rows to restore then (the first slab's rows, or all);
+//   flag[3]: kabs + 1 of a panel whose rows below a slab failed (all rows).
 // A panel whose check fails leaves speculation off for the later panels of
 // the factorization (their check kernels return at once).
 struct SpecArgs {
-  int* flag = nullptr;   // 3 ints, device (zeroed per factorization)
+  int* flag = nullptr;     // 4 ints, device (zeroed per factorization)
   void* backup = nullptr;  // m x w, row-major, ld = w: the panel's rows before the check
-  int* ipiv = nullptr;   // absolute ipiv (identity written on the diagonal block's pass)
-  int* perm = nullptr;   // panel permutation record (count 0 written likewise)
+  int* ipiv = nullptr;     // absolute ipiv (identity written by the first slab)
+  int* perm = nullptr;     // panel permutation record (count 0 written likewise)
 };
 
-// The no-pivot variant's block operations: LU of the w x w diagonal block at D
-// (one CTA), and X (m x w) <- X U^-1 with U the upper w x w block at U.  With
-// spec.flag set they run as the two stages of the diagonal-pivot check of a
-// pivoted panel (kabs: the panel's first absolute column).
+// Factor the m x w block column at P (row-major, ld; m >= w) without
+// pivoting -- the paper's "LU" (diagonal block) and "left" (A21 U11^-1)
+// operations -- slab by slab: one CTA factors a slab of up to 128 rows in
+// shared memory (its diagonal block and U rows), then a CTA per 64 rows below
+// solves their L columns and updates the rest.  Zero pivots lower *info
+// (absolute column + 1; kabs = P's first column).  With spec.flag set the
+// kernels are the diagonal-pivot check of a pivoted panel instead (info
+// unused).  block_column_launches gives the number of kernels it launches.
+// uinv: scratch of w x 32 elements (the inverses of U's 32 x 32 diagonal
+// blocks, passed from the slab kernel to the kernel of the rows below).
 template <typename T>
-cudaError_t launch_diag_lu(T* D, int64_t ld, int w, int kabs, int* info, cudaStream_t st,
-                           const SpecArgs& spec = SpecArgs());
-template <typename T>
-cudaError_t launch_trsm_right_upper(const T* U, T* X, int64_t ld, int m, int w, cudaStream_t st,
-                                    const SpecArgs& spec = SpecArgs(), int kabs = 0);
+cudaError_t launch_block_column(T* P, int64_t ld, int m, int w, int kabs, int* info, T* uinv, cudaStream_t st,
+                                const SpecArgs& spec = SpecArgs());
+int block_column_launches(int m, int w, int tsize);
 
 // ---------------------------------------------------------------- gemm_simt.cu
 // C (m x n) -= A (m x k) * B (k x n), all row-major in T, CUDA-core FMA.
@@ -142,6 +145,9 @@ cudaError_t launch_gemm_simt(T* C, int64_t ldc, const T* A, int64_t lda, const T
 // kpad >= k is a multiple of 64 with zero fill.  Overflow or NaN sets ST_RANGE.
 cudaError_t launch_cast_operands(int kind, const float* L21, const float* U12, int64_t ldw, int m, int n, int k,
                                  void* Aop, void* Bop, int kpad, int* status, cudaStream_t st);
+// The B half of launch_cast_operands alone (columns of U12 into Bop).
+cudaError_t launch_cast_b(int kind, const float* U12, int64_t ldw, int n, int k, void* Bop, int kpad, int* status,
+                          cudaStream_t st);
 // C (row-major FP32, m x n) -= Aop * Bop^T on tcgen05 (FP32 accumulate in TMEM).
 // max_ctas > 0 caps the persistent grid (to leave SMs to a concurrent kernel).
 cudaError_t tc_gemm_run(int kind, float* C, int64_t ldc, const void* Aop, const void* Bop, int m, int n, int kpad,

@@ -113,6 +113,7 @@ struct lu_fact_s {
   double* oz_minv = nullptr;  // nb x nb: I - L11^-1 of the current block
   int* spec_flag = nullptr;   // diagonal-pivot check flags (SpecArgs), FP32 panels
   void* spec_backup = nullptr;  // n x nb FP32: a checked panel's rows before the check
+  void* uinv = nullptr;         // nb x 32: inverses of the diagonal blocks of a block column's U
   void* solve_mem = nullptr;
   SolveScratch ss{};
   double* vec_ws = nullptr;  // refinement: R, D, partial sums
@@ -325,13 +326,9 @@ static cudaError_t panel_step(lu_fact f, int mode, T* Wkk, int m, int w, int kab
   sa.backup = f->spec_backup;
   sa.ipiv = f->ipiv;
   sa.perm = f->ps.perm;
-  cudaError_t e = PHASE_ON(c, s, PH_PANEL, 1, launch_diag_lu<T>(Wkk, ld, w, kabs, nullptr, s, sa));
+  cudaError_t e = PHASE_ON(c, s, PH_PANEL, block_column_launches(m, w, sizeof(T)),
+                           launch_block_column<T>(Wkk, ld, m, w, kabs, nullptr, (T*)f->uinv, s, sa));
   if (e != cudaSuccess) return e;
-  if (m > w) {
-    e = PHASE_ON(c, s, PH_PANEL, 1,
-                 launch_trsm_right_upper<T>(Wkk, Wkk + (int64_t)w * ld, ld, m - w, w, s, sa, kabs));
-    if (e != cudaSuccess) return e;
-  }
   return PHASE_ON(c, s, PH_PANEL, 1, launch_panel<T>(Wkk, ld, m, w, kabs, f->ipiv, f->info_d, c->d_status, ps,
                                                     c->dev, s, f->spec_flag, (const T*)f->spec_backup));
 }
@@ -379,12 +376,16 @@ static int factor_loop(lu_fact f) {
     T* U12 = Wkk + w;
     T* L21 = Wkk + (int64_t)w * ld;
     T* A22 = L21 + w;
+    const int w2 = rest < nb ? rest : nb;
+    // with the lookahead, only the next panel's columns of the top block row
+    // are solved and cast before the next panel starts; the rest follow on
+    // this stream while the next panel runs on the side stream
+    const bool split_top = tc && lookahead && rest > w2;
     if (f->ozaki) {
       CU_TRY(top_solve_split(f, (double*)Wkk, (double*)U12, ld, w, rest));
     } else {
-      CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12, ld, w, rest, st)));
+      CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12, ld, w, split_top ? w2 : rest, st)));
     }
-    const int w2 = rest < nb ? rest : nb;
     if (f->ozaki) {
       CU_TRY(PHASE(c, PH_CAST, 2, ozaki_split((const double*)L21, ld, (const double*)U12, ld, rest, rest, w,
                                                f->oz_ws, c->d_status, st)));
@@ -396,9 +397,10 @@ static int factor_loop(lu_fact f) {
       CU_TRY(PHASE(c, PH_GEMM, 1, launch_gemm_simt<T>(A22, ld, L21, ld, U12, ld, rest, rest, w, st)));
       continue;
     }
-    CU_TRY(PHASE(c, PH_CAST, 2, launch_cast_operands(kind, (const float*)L21, (const float*)U12, ld, rest, rest, w,
-                                                      f->aop, f->bop, f->kpad, c->d_status, st)));
-    if (!lookahead || rest <= w2) {
+    CU_TRY(PHASE(c, PH_CAST, 2, launch_cast_operands(kind, (const float*)L21, (const float*)U12, ld, rest,
+                                                      split_top ? w2 : rest, w, f->aop, f->bop, f->kpad, c->d_status,
+                                                      st)));
+    if (!split_top) {
       CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)A22, ld, f->aop, f->bop, rest, rest, f->kpad,
                                                c->d_status, c->dev, st)));
       continue;
@@ -422,10 +424,14 @@ static int factor_loop(lu_fact f) {
       CU_TRY(cudaMemcpyAsync(hflag + 4, f->spec_flag, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->side));
     CU_TRY(cudaEventRecord(c->ev_panel, c->side));
     panel_ready = true;
-    // the rest of the trailing matrix on the SMs the panel leaves free (the
-    // latency-bound panel runs slower on SMs it shares with the update)
-    const int cap = c->dev.sm_count - (gp > 0 ? gp : 0);
+    // the rest of the top block row, then the rest of the trailing matrix on
+    // the SMs the panel leaves free (the latency-bound panel runs slower on
+    // SMs it shares with the update)
     const void* bop2 = (const char*)f->bop + (size_t)w2 * f->kpad * 2;
+    CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12 + w2, ld, w, rest - w2, st)));
+    CU_TRY(PHASE(c, PH_CAST, 1, launch_cast_b(kind, (const float*)(U12 + w2), ld, rest - w2, w, (void*)bop2, f->kpad,
+                                              c->d_status, st)));
+    const int cap = c->dev.sm_count - (gp > 0 ? gp : 0);
     CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)(A22 + w2), ld, f->aop, bop2, rest, rest - w2, f->kpad,
                                              c->d_status, c->dev, st, cap > 8 ? cap : 8)));
   }
@@ -436,6 +442,14 @@ static int factor_loop(lu_fact f) {
 // The paper's no-pivot iteration: LU of the diagonal block, left and top
 // block solves, inner update.
 template <typename T>
+static cudaError_t nopiv_panel(lu_fact f, T* Wkk, int m, int w, int kabs, cudaStream_t s) {
+  lu_ctx c = f->ctx;
+  const int64_t ld = f->ldw;
+  return PHASE_ON(c, s, PH_PANEL, block_column_launches(m, w, sizeof(T)),
+                  launch_block_column<T>(Wkk, ld, m, w, kabs, f->info_d, (T*)f->uinv, s));
+}
+
+template <typename T>
 static int factor_loop_nopiv(lu_fact f) {
   lu_ctx c = f->ctx;
   cudaStream_t st = c->stream;
@@ -444,30 +458,32 @@ static int factor_loop_nopiv(lu_fact f) {
   const int64_t ld = f->ldw;
   const bool tc = f->prec == LU_BF16 || f->prec == LU_FP16;
   const int kind = f->prec == LU_BF16 ? 1 : 2;
-  // Lookahead (tensor-core form): the next diagonal block's columns are
-  // updated first, then its LU (one CTA) runs on the side stream while the
-  // rest of the trailing matrix is updated on the other SMs.
+  // Lookahead (tensor-core form): the next block column is updated first, then
+  // its diagonal-block LU and left-block solve run on the side stream, on the
+  // few SMs the rest of the trailing update leaves them.
   const bool lookahead = tc && !f->ozaki && c->lookahead && c->side != nullptr;
-  bool diag_ready = false;
+  const int keep = c->spec_sms > 0 ? c->spec_sms : 1;
+  bool panel_ready = false;
   for (int k = 0; k < n; k += nb) {
     const int w = (n - k) < nb ? (n - k) : nb;
     T* Wkk = W + (int64_t)k * ld + k;
-    if (diag_ready) {
+    if (panel_ready) {
       CU_TRY(cudaStreamWaitEvent(st, c->ev_panel, 0));
-      diag_ready = false;
+      panel_ready = false;
     } else {
-      CU_TRY(PHASE(c, PH_PANEL, 1, launch_diag_lu<T>(Wkk, ld, w, k, f->info_d, st)));
+      CU_TRY(nopiv_panel<T>(f, Wkk, n - k, w, k, st));
     }
     const int rest = n - k - w;
     if (rest <= 0) continue;
     T* U12 = Wkk + w;
     T* L21 = Wkk + (int64_t)w * ld;
     T* A22 = L21 + w;
-    CU_TRY(PHASE(c, PH_PANEL, 1, launch_trsm_right_upper<T>(Wkk, L21, ld, rest, w, st)));
+    const int w2 = rest < nb ? rest : nb;
+    const bool split_top = tc && lookahead && rest > w2;  // as in factor_loop
     if (f->ozaki) {
       CU_TRY(top_solve_split(f, (double*)Wkk, (double*)U12, ld, w, rest));
     } else {
-      CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12, ld, w, rest, st)));
+      CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12, ld, w, split_top ? w2 : rest, st)));
     }
     if (f->ozaki) {
       CU_TRY(PHASE(c, PH_CAST, 2, ozaki_split((const double*)L21, ld, (const double*)U12, ld, rest, rest, w,
@@ -475,30 +491,34 @@ static int factor_loop_nopiv(lu_fact f) {
       CU_TRY(PHASE(c, PH_GEMM, 1, ozaki_gemm((double*)A22, ld, f->oz_ws, rest, rest, w, 0, rest, c->d_status, c->dev,
                                               st)));
     } else if (tc) {
-      CU_TRY(PHASE(c, PH_CAST, 2, launch_cast_operands(kind, (const float*)L21, (const float*)U12, ld, rest, rest,
-                                                        w, f->aop, f->bop, f->kpad, c->d_status, st)));
-      const int w2 = rest < nb ? rest : nb;
-      if (!lookahead || rest <= w2) {
+      CU_TRY(PHASE(c, PH_CAST, 2, launch_cast_operands(kind, (const float*)L21, (const float*)U12, ld, rest,
+                                                        split_top ? w2 : rest, w, f->aop, f->bop, f->kpad,
+                                                        c->d_status, st)));
+      if (!split_top) {
         CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)A22, ld, f->aop, f->bop, rest, rest, f->kpad,
                                                  c->d_status, c->dev, st)));
         continue;
       }
-      // the next diagonal block's columns, then its LU beside the rest
+      // the next block column, then its diagonal block and left blocks beside the rest
       CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)A22, ld, f->aop, f->bop, rest, w2, f->kpad,
                                                c->d_status, c->dev, st)));
       CU_TRY(cudaEventRecord(c->ev_next, st));
       CU_TRY(cudaStreamWaitEvent(c->side, c->ev_next, 0));
-      CU_TRY(PHASE_ON(c, c->side, PH_PANEL, 1, launch_diag_lu<T>(A22, ld, w2, k + w, f->info_d, c->side)));
+      CU_TRY(nopiv_panel<T>(f, A22, rest, w2, k + w, c->side));
       CU_TRY(cudaEventRecord(c->ev_panel, c->side));
-      diag_ready = true;
+      panel_ready = true;
       const void* bop2 = (const char*)f->bop + (size_t)w2 * f->kpad * 2;
+      CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12 + w2, ld, w, rest - w2, st)));
+      CU_TRY(PHASE(c, PH_CAST, 1, launch_cast_b(kind, (const float*)(U12 + w2), ld, rest - w2, w, (void*)bop2,
+                                                f->kpad, c->d_status, st)));
+      const int cap = c->dev.sm_count - keep;
       CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)(A22 + w2), ld, f->aop, bop2, rest, rest - w2, f->kpad,
-                                               c->d_status, c->dev, st, c->dev.sm_count - 1)));
+                                               c->d_status, c->dev, st, cap > 8 ? cap : 8)));
     } else {
       CU_TRY(PHASE(c, PH_GEMM, 1, launch_gemm_simt<T>(A22, ld, L21, ld, U12, ld, rest, rest, w, st)));
     }
   }
-  if (diag_ready) CU_TRY(cudaStreamWaitEvent(st, c->ev_panel, 0));
+  if (panel_ready) CU_TRY(cudaStreamWaitEvent(st, c->ev_panel, 0));
   return LU_OK;
 }
 
@@ -513,6 +533,7 @@ extern "C" void lu_fact_free(lu_fact f) {
   dfree(c, f->oz_minv);
   dfree(c, f->spec_flag);
   dfree(c, f->spec_backup);
+  dfree(c, f->uinv);
   dfree(c, f->solve_mem);
   dfree(c, f->ss.dinv);
   dfree(c, f->vec_ws);
@@ -582,9 +603,16 @@ extern "C" int lu_factor_ex(lu_ctx c, int n, const double* dA, int lda, lu_prec 
       return rc;
     }
   }
-  if (prec != LU_F64 && !nopiv && c->spec && n > f->nb) {
+  const bool spec = prec != LU_F64 && !nopiv && c->spec && n > f->nb;
+  if (spec) {
     if ((rc = dalloc(c, (void**)&f->spec_flag, 4 * sizeof(int))) ||
         (rc = dalloc(c, &f->spec_backup, (size_t)nn * f->nb * f->tsize))) {
+      lu_fact_free(f);
+      return rc;
+    }
+  }
+  if (spec || nopiv) {
+    if ((rc = dalloc(c, &f->uinv, (size_t)round_up(f->nb, 32) * 32 * f->tsize))) {
       lu_fact_free(f);
       return rc;
     }
@@ -1008,7 +1036,8 @@ size_t gb_fact_bytes(int n, int nrhs, lu_prec prec, int nb, int sm_count) {
   size_t b = ldw * nn * tsize + (size_t)(2 * nn + 64) * sizeof(int) + panel_scratch_bytes(sm_count, 32, nb, tsize) +
              solve_scratch_bytes(nn, tsize);
   if (prec != LU_F64) b += solve_dinv_bytes(nn, tsize);
-  if (prec != LU_F64 && n > nb) b += 4 * sizeof(int) + (size_t)nn * nb * tsize;  // diagonal-pivot check
+  if (prec != LU_F64 && n > nb)  // diagonal-pivot check
+    b += 4 * sizeof(int) + (size_t)nn * nb * tsize + (size_t)round_up(nb, 32) * 32 * tsize;
   if (prec == LU_BF16 || prec == LU_FP16) b += (size_t)2 * nn * round_up(nb, 64) * 2 + 1024;
   const int nr = nrhs > 32 ? 32 : (nrhs < 1 ? 1 : nrhs);
   b += 2 * (size_t)nn * nrhs * 8 + residual_partial_bytes(nn, nr) + 4096;

@@ -1,66 +1,32 @@
 // The paper's own LU variant: no pivoting on a diagonally dominant A (HPL-AI
 // rules, arxiv 2202.13995, section "High Performance Linpack"), with the four
 // per-block operations of its "Base Implementation" (figure "lu_iteration"):
-//   LU    -- factor the diagonal block (one CTA: no grid-wide step at all),
+//   LU    -- factor the diagonal block,
 //   top   -- A12 <- L11^-1 A12           (trsm_lower_kernel, panel.cu),
-//   left  -- A21 <- A21 U11^-1           (trsm_right_upper_kernel, here),
+//   left  -- A21 <- A21 U11^-1           (below_solve_kernel, here),
 //   inner -- A22 <- A22 - A21 A12        (the trailing-update GEMMs).
 // Without pivoting no column needs a search over all rows, so the latency of
 // the partial-pivot panel disappears; the price is stability, which the
 // diagonal dominance of the matrix provides.
+//
+// Here the "LU" and "left" operations factor a whole m x w block column
+// without pivoting, slab by slab: the block column's top h rows (a slab) are
+// factored by one CTA in shared memory -- the LU of the slab's h x h diagonal
+// block and its U rows to the right -- and then every row below the slab gets
+// its L columns (X <- X U^-1 for the slab's h columns) and the update of the
+// block column's remaining columns, a CTA per 64 rows.  The next slab starts
+// h rows and h columns further down.  The same two kernels serve the
+// diagonal-pivot check of a pivoted panel (SpecArgs in kernels.h).
+#include <cstdlib>
+
 #include "common.cuh"
 #include "kernels.h"
 
 namespace gb {
 
-constexpr int NP_NB = 32;
-
-// 16-byte global accesses of 16 / sizeof(T) elements, and a 4-element
-// shared-memory load (one or two 16-byte accesses); the addresses are aligned.
-template <typename T>
-__device__ __forceinline__ void load16(const T* p, T* v);
-template <>
-__device__ __forceinline__ void load16<float>(const float* p, float* v) {
-  const float4 x = *reinterpret_cast<const float4*>(p);
-  v[0] = x.x;
-  v[1] = x.y;
-  v[2] = x.z;
-  v[3] = x.w;
-}
-template <>
-__device__ __forceinline__ void load16<double>(const double* p, double* v) {
-  const double2 x = *reinterpret_cast<const double2*>(p);
-  v[0] = x.x;
-  v[1] = x.y;
-}
-template <typename T>
-__device__ __forceinline__ void store16(T* p, const T* v);
-template <>
-__device__ __forceinline__ void store16<float>(float* p, const float* v) {
-  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-}
-template <>
-__device__ __forceinline__ void store16<double>(double* p, const double* v) {
-  *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
-}
-template <typename T>
-__device__ __forceinline__ void load4s(const T* p, T* v) {
-  load16<T>(p, v);
-  if (sizeof(T) == 8) load16<T>(p + 2, v + 2);
-}
-constexpr int NP_CW = 128;  // column chunk of the in-block update
-// threads of the diagonal-block CTA: 512 for FP32 (the update loads its C
-// tile ahead of the products, which needs more than the 64 registers a thread
-// of a 1024-thread CTA has), 256 for FP64 (a thread holds 32 doubles in
-// registers)
-template <typename T>
-constexpr int np_threads() {
-  return sizeof(T) == 8 ? 256 : 512;
-}
-
-// Device view of SpecArgs (the diagonal-pivot check of a pivoted panel).
-// Flags: [0] sticky failure, [1] kabs + 1 of a panel whose diagonal block
-// failed, [3] kabs + 1 of a panel whose rows below the block failed.
+// Device view of SpecArgs.  Flags: [0] sticky failure, [1] kabs + 1 of a panel
+// whose slab failed and [2] the rows to restore then, [3] kabs + 1 of a panel
+// whose rows below a slab failed (every row to restore).
 template <typename T>
 struct SpecDev {
   int* flag;
@@ -74,238 +40,417 @@ __device__ __forceinline__ bool spec_ok_mult(T l) {
   return l <= T(0.5) && l >= T(-0.5);  // false for NaN
 }
 
-// In-place LU (no pivoting) of the w x w block at D (row-major, ld), blocked by
-// 32 columns; one CTA of np_threads<T>() threads.  Lowers *info to kabs + j + 1 at the
-// first exactly zero pivot j (and skips that column's scaling).
-// With sp.flag set it is the first stage of a pivoted panel's diagonal-pivot
-// check: it saves the block to sp.backup, writes the identity pivots and an
-// empty permutation record, leaves *info alone, and on a multiplier above 1/2
-// or a zero or non-finite pivot records the failure (flag[1], then flag[0]).
 template <typename T>
-__global__ void __launch_bounds__(np_threads<T>()) diag_lu_kernel(T* D, int64_t ld, int w, int kabs, int* info,
-                                                                  SpecDev<T> sp) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int wp = (w + 3) & ~3;
-  T* P = reinterpret_cast<T*>(smem_raw);  // [NP_NB][wp]: column c of the sub-panel, row r
-  T* Us = P + (size_t)NP_NB * wp;         // [NP_NB][NP_CW]
-  const int tid = threadIdx.x;
-  constexpr int NP_NT = np_threads<T>();
-  constexpr int CH = 16 / sizeof(T);  // elements per 16-byte access
-  const bool vec = ((reinterpret_cast<uintptr_t>(D) & 15) == 0) && (ld % CH) == 0;
-  const bool spec = sp.flag != nullptr;
-  bool bad = false;  // a multiplier above 1/2 or a zero / non-finite pivot (spec only)
-  if (spec) {
-    // the check is off once a panel has failed it; a failure of the previous
-    // panel's rows below its block turns it off here
-    const int f0 = __ldcg(sp.flag), f3 = __ldcg(sp.flag + 3);
-    if (f0 != 0 || f3 != 0) {
-      if (tid == 0 && f0 == 0) sp.flag[0] = 1;
-      return;
-    }
-    for (int r = tid / 32; r < w; r += NP_NT / 32)
-      for (int c = tid % 32; c < w; c += 32) sp.backup[(int64_t)r * w + c] = D[(int64_t)r * ld + c];
-    for (int j = tid; j < w; j += NP_NT) sp.ipiv[kabs + j] = kabs + j + 1;
-    if (tid == 0) sp.perm[0] = 0;
-    __syncthreads();
-  }
-  for (int k0 = 0; k0 < w; k0 += NP_NB) {
-    const int kb = min(NP_NB, w - k0), m = w - k0;
-    // thread = row (consecutive threads, consecutive rows: the column-major
-    // sub-panel is written without bank conflicts), CH columns per load
-    for (int e = tid; e < m * (NP_NB / CH); e += NP_NT) {
-      const int r = e % m, c = (e / m) * CH;
-      if (c >= kb) continue;
-      const T* src = D + (int64_t)(k0 + r) * ld + k0 + c;
-      if (vec && c + CH <= kb) {
-        T v[CH];
-        load16<T>(src, v);
+__device__ __forceinline__ bool finite_nonzero(T v) {
+  return v != T(0) && v - v == T(0);
+}
+
+// 16-byte vector of T
+template <typename T>
+struct V16;
+template <>
+struct V16<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <>
+struct V16<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
+template <typename T>
+__device__ __forceinline__ void v16_get(const typename V16<T>::type& v, T* out);
+template <>
+__device__ __forceinline__ void v16_get<float>(const float4& v, float* o) {
+  o[0] = v.x;
+  o[1] = v.y;
+  o[2] = v.z;
+  o[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void v16_get<double>(const double2& v, double* o) {
+  o[0] = v.x;
+  o[1] = v.y;
+}
+
+// Rows [0, nrows) x columns [0, ncol) of G (row-major, ld) into S (row
+// stride sld), and, when B is set, to B too (row stride ncol).  Each warp
+// takes four rows at a time with all their loads in flight; 16-byte loads
+// when G's rows are 16-byte aligned.  Rows nrows .. rows_alloc of S are
+// zero-filled.
+template <typename T, int NT>
+__device__ __forceinline__ void load_rows(const T* G, int64_t ld, int nrows, int rows_alloc, int ncol, T* S,
+                                          int sld, T* B) {
+  constexpr int VN = V16<T>::n;
+  using VT = typename V16<T>::type;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NW = NT / 32;
+  const bool vec = ((reinterpret_cast<uintptr_t>(G) & 15) == 0) && ((ld * (int64_t)sizeof(T)) & 15) == 0;
+  const int nvec = vec ? ncol / VN : 0;  // whole vectors per row
+  for (int r0 = warp * 4; r0 < rows_alloc; r0 += NW * 4) {
+    // the vector part: 4 rows x 4 vectors per lane in flight at a time
+    for (int v0 = 0; v0 < nvec; v0 += 32 * 4) {
+      VT buf[4][4];
 #pragma unroll
-        for (int x = 0; x < CH; ++x) P[(c + x) * wp + r] = v[x];
-      } else {
-        for (int x = 0; c + x < kb; ++x) P[(c + x) * wp + r] = src[x];
-      }
-    }
-    __syncthreads();
-    for (int j = 0; j < kb; ++j) {
-      const T piv = P[j * wp + j];
-      if (spec) {
-        if (tid == 0 && !(piv != T(0) && piv - piv == T(0))) bad = true;  // zero or non-finite pivot
-      } else if (tid == 0 && piv == T(0)) {
-        atomicMin(info, kabs + k0 + j + 1);
-      }
-      for (int r = j + 1 + tid; r < m; r += NP_NT) {
-        T l = P[j * wp + r];
-        if (piv != T(0)) l = l / piv;
-        if (spec && !spec_ok_mult(l)) bad = true;
-        P[j * wp + r] = l;
-        for (int c = j + 1; c < kb; ++c) P[c * wp + r] -= l * P[c * wp + j];
-      }
-      __syncthreads();
-    }
-    for (int e = tid; e < m * (NP_NB / CH); e += NP_NT) {
-      const int r = e % m, c = (e / m) * CH;
-      if (c >= kb) continue;
-      T* dst = D + (int64_t)(k0 + r) * ld + k0 + c;
-      if (vec && c + CH <= kb) {
-        T v[CH];
+      for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int x = 0; x < CH; ++x) v[x] = P[(c + x) * wp + r];
-        store16<T>(dst, v);
-      } else {
-        for (int x = 0; c + x < kb; ++x) dst[x] = P[(c + x) * wp + r];
-      }
-    }
-    __syncthreads();
-    for (int c0 = k0 + kb; c0 < w; c0 += NP_CW) {
-      const int cw = min(NP_CW, w - c0);
-      for (int c = tid; c < cw; c += NP_NT) {
-        // the column's kb values in registers (loads issued together), then
-        // forward substitution with the unit-lower block
-        T v[NP_NB];
-#pragma unroll
-        for (int j = 0; j < NP_NB; ++j) v[j] = j < kb ? D[(int64_t)(k0 + j) * ld + c0 + c] : T(0);
-#pragma unroll
-        for (int j = 1; j < NP_NB; ++j) {
-#pragma unroll
-          for (int i = 0; i < NP_NB; ++i)
-            if (i < j) v[j] -= P[i * wp + j] * v[i];
+        for (int q = 0; q < 4; ++q) {
+          const int r = r0 + i, v = v0 + lane + 32 * q;
+          if (r < nrows && v < nvec) buf[i][q] = reinterpret_cast<const VT*>(G + (int64_t)r * ld)[v];
         }
 #pragma unroll
-        for (int j = 0; j < NP_NB; ++j) {
-          if (j < kb) {
-            Us[j * NP_CW + c] = v[j];
-            D[(int64_t)(k0 + j) * ld + c0 + c] = v[j];
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int r = r0 + i, v = v0 + lane + 32 * q;
+          if (r < rows_alloc && v < nvec) {
+            T e[VN];
+            if (r < nrows) {
+              v16_get<T>(buf[i][q], e);
+            } else {
+#pragma unroll
+              for (int x = 0; x < VN; ++x) e[x] = T(0);
+            }
+#pragma unroll
+            for (int x = 0; x < VN; ++x) {
+              S[(size_t)r * sld + v * VN + x] = e[x];
+              if (B && r < nrows) B[(int64_t)r * ncol + v * VN + x] = e[x];
+            }
           }
         }
+    }
+    // the scalar rest of each row
+    for (int i = 0; i < 4; ++i) {
+      const int r = r0 + i;
+      if (r >= rows_alloc) break;
+      for (int c = nvec * VN + lane; c < ncol; c += 32) {
+        const T e = r < nrows ? G[(int64_t)r * ld + c] : T(0);
+        S[(size_t)r * sld + c] = e;
+        if (B && r < nrows) B[(int64_t)r * ncol + c] = e;
+      }
+    }
+  }
+}
+
+// y[k] += a * x[k] for k in [k0, k1), shared-memory vectors: eight loads of
+// each issued before their products and stores, so that the stores (which
+// might alias later loads, as far as the compiler knows) do not serialize
+// the loop on the load latency.
+template <typename T>
+__device__ __forceinline__ void axpy_batched(T* y, const T* x, T a, int k0, int k1) {
+  for (int k = k0; k < k1; k += 8) {
+    T yv[8], xv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int kk = k + u < k1 ? k + u : k1 - 1;
+      yv[u] = y[kk];
+      xv[u] = x[kk];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (k + u < k1) y[k + u] = fma(a, xv[u], yv[u]);
+  }
+}
+
+// ============================================================ slab LU
+// One CTA factors the slab D (hs rows x wt columns, row-major, ld) in shared
+// memory: the LU of its hs x hs diagonal block without pivoting, blocked by 32
+// columns, and U's rows right of the block (columns hs .. wt).  Per block of
+// 32 columns:
+//   (i)  the block's columns, one at a time: the multipliers of the column (a
+//        thread per row, dividing by the pivot as in the definition), then a
+//        rank-1 update of the block's rows across the whole slab width (which
+//        leaves U's rows right of the block final) and of the rows below the
+//        block within the block's columns; two barriers per column;
+//   (ii) a rank-32 update of the rows below the block and the columns right
+//        of it (register tiles).
+// The loops stay rolled, with their shared-memory loads batched ahead of the
+// products: the kernel runs once per launch on one SM, where a long
+// straight-line body would be fetched from L2 at every block.
+// A zero pivot lowers *info to its absolute column + 1 (kabs = D's first
+// column) and skips its scaling.  With sp.flag set it is a stage of a pivoted
+// panel's diagonal-pivot check: the first slab (first != 0) saves its rows to
+// sp.backup and writes the identity pivots and an empty permutation record
+// for the panel's wt columns; *info is left alone; a multiplier above 1/2, or
+// a zero or non-finite pivot, records the failure (flag[1] = tag, flag[2] =
+// restore_rows, then flag[0]).  It returns at once when an earlier stage or
+// panel failed.
+constexpr int SL_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(SL_THREADS) slab_lu_kernel(T* D, int64_t ld, int hs, int wt, int kabs, int* info,
+                                                             SpecDev<T> sp, int first, int tag, int restore_rows) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int wp = wt | 1;  // odd row stride: a row per thread is free of bank conflicts
+  T* A = reinterpret_cast<T*>(smem_raw);  // [hs][wp]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool spec = sp.flag != nullptr;
+  bool bad = false;
+  if (spec) {
+    const int f0 = __ldcg(sp.flag), f3 = __ldcg(sp.flag + 3);
+    if (f0 != 0 || f3 != 0) {
+      if (tid == 0 && f0 == 0) sp.flag[0] = 1;  // a failure of the rows below an earlier slab
+      return;
+    }
+  }
+  load_rows<T, SL_THREADS>(D, ld, hs, hs, wt, A, wp, (spec && first) ? sp.backup : nullptr);
+  if (spec && first) {
+    for (int j = tid; j < wt; j += SL_THREADS) sp.ipiv[kabs + j] = kabs + j + 1;
+    if (tid == 0) sp.perm[0] = 0;
+  }
+  __syncthreads();
+  T* lcol = A + (size_t)hs * wp;  // [hs]: the current column's multipliers
+  for (int c0 = 0; c0 < hs; c0 += 32) {
+    const int bw = min(32, hs - c0);
+    const int r1 = c0 + bw;
+    // (i) the block's columns, one at a time.  Column cj: (a) a thread per
+    //     row below the pivot divides by the pivot (as in the definition);
+    //     (b) all threads apply the rank-1 update to the block's rows right of
+    //     cj (so U's rows right of the block come out final: the forward
+    //     substitution with the block's L) and to the rows below the block
+    //     within the block's columns.
+    for (int j = 0; j < bw; ++j) {
+      const int cj = c0 + j;
+      const T piv = A[cj * wp + cj];
+      const bool pz = !(piv != T(0));
+      if (tid == 0) {
+        if (spec) {
+          if (!finite_nonzero(piv)) bad = true;
+        } else if (pz) {
+          atomicMin(info, kabs + cj + 1);
+        }
+      }
+      for (int r = cj + 1 + tid; r < hs; r += SL_THREADS) {
+        T l = A[r * wp + cj];
+        if (!pz) l = l / piv;
+        if (spec && !spec_ok_mult(l)) bad = true;
+        A[r * wp + cj] = l;
+        lcol[r] = l;
       }
       __syncthreads();
-      const int rows = m - kb;
-      const int rt = (rows + 3) / 4, ct = (cw + 3) / 4;
-      for (int t = tid; t < rt * ct; t += NP_NT) {
-        const int r0 = kb + (t / ct) * 4, cc = (t % ct) * 4;
-        // the tile's entries of D first: their latency runs under the products
-        T dv[4][4];
+      const T* prow = A + cj * wp;
+      // the rank-1 update of an L-shaped region: (b1) the block's rows
+      // (cj, r1) x the columns right of cj, a thread per column, eight rows at
+      // a time with their loads ahead of the products; (b2) the rows below the
+      // block x the block's columns right of cj, a thread per row
+      for (int k = cj + 1 + tid; k < wt; k += SL_THREADS) {
+        const T x = prow[k];
+        for (int r0 = cj + 1; r0 < r1; r0 += 8) {
+          T yv[8], lv[8];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const T* dr = D + (int64_t)(k0 + min(r0 + i, m - 1)) * ld + c0 + cc;
+          for (int u = 0; u < 8; ++u) {
+            const int r = r0 + u < r1 ? r0 + u : r1 - 1;
+            yv[u] = A[r * wp + k];
+            lv[u] = lcol[r];
+          }
 #pragma unroll
-          for (int q = 0; q < 4; ++q) dv[i][q] = (r0 + i < m && cc + q < cw) ? dr[q] : T(0);
+          for (int u = 0; u < 8; ++u)
+            if (r0 + u < r1) A[(r0 + u) * wp + k] = fma(-lv[u], x, yv[u]);
         }
+      }
+      for (int r = r1 + tid; r < hs; r += SL_THREADS) axpy_batched<T>(A + r * wp, prow, -lcol[r], cj + 1, r1);
+      __syncthreads();
+    }
+    // (ii) rank-bw update of rows [r1, hs) x columns [r1, wt): a thread per
+    //       4 rows x 4 columns 32 apart (the warp reads consecutive columns)
+    const int nr = hs - r1, nc = wt - r1;
+    if (nr > 0 && nc > 0) {
+      const int ntr = (nr + 3) / 4, ncg = (nc + 127) / 128;
+      for (int it = tid; it < ntr * ncg * 32; it += SL_THREADS) {
+        const int cl = it & 31, g = (it >> 5) % ncg, tr = (it >> 5) / ncg;
+        const int rr = r1 + 4 * tr, cc = r1 + 128 * g + cl;
         T acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[i][q] = T(0);
-        // kb = NP_NB here (the last block has no rows below it), so r0 and cc
-        // are multiples of 4: 16-byte shared loads.  Lanes past m or cw read
-        // stale entries into rows / columns of acc that are never stored.
-        for (int k = 0; k < kb; ++k) {
-          T a[4], b[4];
-          load4s<T>(&P[k * wp + r0], a);
-          load4s<T>(&Us[k * NP_CW + cc], b);
+#pragma unroll 4
+        for (int j = 0; j < bw; ++j) {
+          T av[4], bv[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) av[i] = rr + i < hs ? A[(rr + i) * wp + c0 + j] : T(0);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) bv[q] = cc + 32 * q < wt ? A[(c0 + j) * wp + cc + 32 * q] : T(0);
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) acc[i][q] = fma(a[i], b[q], acc[i][q]);
+            for (int q = 0; q < 4; ++q) acc[i][q] = fma(av[i], bv[q], acc[i][q]);
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          if (r0 + i >= m) break;
-          T* dr = D + (int64_t)(k0 + r0 + i) * ld + c0 + cc;
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int q = 0; q < 4; ++q)
-            if (cc + q < cw) dr[q] = dv[i][q] - acc[i][q];
-        }
+            if (rr + i < hs && cc + 32 * q < wt) A[(rr + i) * wp + cc + 32 * q] -= acc[i][q];
       }
-      __syncthreads();
     }
+    __syncthreads();
   }
+  for (int r = warp; r < hs; r += SL_THREADS / 32)
+    for (int c = lane; c < wt; c += 32) D[(int64_t)r * ld + c] = A[r * wp + c];
   if (spec && __syncthreads_or(bad) && tid == 0) {
-    sp.flag[1] = kabs + 1;
+    sp.flag[1] = tag;
+    sp.flag[2] = restore_rows;
     __threadfence();
     sp.flag[0] = 1;
   }
 }
 
-// X (m x w, row-major, ld) <- X U^-1 with U the upper (non-unit) w x w block at
-// U (row-major, ld): the paper's "left" block update.  CTA = RB rows of X in
-// shared memory; by 32-column blocks:
-//   1. the diagonal block: one thread per row substitutes its 32 values in
-//      registers against U's 32 x 32 diagonal block, multiplying by the
-//      reciprocals of U's diagonal (computed once per CTA);
-//   2. the columns to the right: a rank-32 update, each thread a register tile
-//      of RB/16 rows x 4 columns per 64-column chunk, U's rows staged in shared
-//      memory.
-// With sp.flag set it is the second stage of a pivoted panel's diagonal-pivot
-// check: the rows are saved to sp.backup first, and a multiplier above 1/2 in
-// magnitude (or not finite) records the panel in flag[3].  It returns at once
-// when flag[0] is set (the check is off, or the diagonal block failed it).
+// ============================================================ inverses of U's diagonal blocks
+// The inverse of each 32 x 32 diagonal block of a factored slab's U (for the
+// rows below the slab): a CTA per block, a thread per column of the inverse,
+// column-oriented back substitution with the division by U's diagonal;
+// uinv[b] (32 x 32, row-major) for the slab's block b.
+template <typename T>
+__global__ void __launch_bounds__(32) uinv_kernel(const T* __restrict__ D, int64_t ld, int hs, T* uinv) {
+  __shared__ T Us[32][33];
+  __shared__ T Z[32][33];
+  const int lane = threadIdx.x, c0 = blockIdx.x * 32, bw = min(32, hs - c0);
+  for (int t = 0; t < 32; ++t) {
+    Us[t][lane] = (t < bw && lane < bw) ? D[(int64_t)(c0 + t) * ld + c0 + lane] : T(0);
+    Z[t][lane] = (t == lane) ? T(1) : T(0);
+  }
+  __syncwarp();
+  for (int t = bw - 1; t >= 0; --t) {
+    const T zt = Z[t][lane] / Us[t][t];
+    Z[t][lane] = zt;
+    for (int q0 = 0; q0 < t; q0 += 8) {
+      T uq[8], zq[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u < t ? q0 + u : t - 1;
+        uq[u] = Us[q][t];
+        zq[u] = Z[q][lane];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (q0 + u < t) Z[q0 + u][lane] = zq[u] - uq[u] * zt;
+    }
+    __syncwarp();
+  }
+  T* ub = uinv + (size_t)blockIdx.x * 1024;
+  for (int t = 0; t < 32; ++t) ub[t * 32 + lane] = Z[t][lane];
+}
+
+// ============================================================ rows below a slab
+// X (m x wt, row-major, ld): the ws columns of a slab's rows below it are
+// solved against the slab's upper ws x ws block U (X <- X U^-1, the paper's
+// "left" block update) and the other wt - ws columns updated with U's rows
+// right of the block (U is ws x wt at U, row-major, ld).  CTA = RB rows of X
+// in shared memory; by 32-column blocks of the ws:
+//   1. U's 32 rows of the block staged in shared memory (cp.async);
+//   2. the diagonal block: X_b <- X_b U_bb^-1, a small product with the
+//      inverse of U's 32 x 32 diagonal block, which the slab kernel wrote to
+//      uinv (32 x 32 per block, row-major);
+//   3. the columns to the right: a rank-32 update, each thread a register
+//      tile of RB/16 rows x 4 columns per 64-column chunk.
+// With sp.flag set it is a stage of the diagonal-pivot check: for the first
+// slab (first != 0) the rows are saved to sp.backup first and the stage runs
+// unless flag[0] is set; a later stage returns on flag[0] or flag[3].  A
+// multiplier above 1/2 in magnitude (or not finite) records flag[3] = tag.
 constexpr int LS_THREADS = 256;
 
 template <typename T, int RB>
-__global__ void __launch_bounds__(LS_THREADS) trsm_right_upper_kernel(const T* __restrict__ U, T* X, int64_t ld,
-                                                                      int m, int w, int kabs, SpecDev<T> sp) {
+__global__ void __launch_bounds__(LS_THREADS) below_solve_kernel(const T* __restrict__ U, const T* __restrict__ uinv,
+                                                                 T* X, int64_t ld, int m, int ws, int wt,
+                                                                 SpecDev<T> sp, int first, int tag) {
   static_assert(RB % 16 == 0 && RB <= LS_THREADS, "RB rows: 16 row groups, one thread per row");
   constexpr int RT = RB / 16;  // rows per thread in the update
+  constexpr int VN = V16<T>::n;
+  using VT = typename V16<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int wx = w | 1;          // odd row stride: a row per thread is free of bank conflicts
-  const int wu = (w + 3) & ~3;   // U stage row stride: 16-byte rows
-  T* Us = reinterpret_cast<T*>(smem_raw);  // [32][wu]: rows c0 .. c0 + 31 of U, columns c0 .. w
-  T* rcp = Us + 32 * wu;                   // [wu]: 1 / U(j, j)
-  T* Xs = rcp + wu;                        // [RB][wx]
+  const int wx = wt | 1;          // odd row stride: a row per thread is free of bank conflicts
+  const int wu = (wt + 3) & ~3;   // U stage row stride: 16-byte rows
+  T* Us = reinterpret_cast<T*>(smem_raw);  // [32][wu]: rows c0 .. c0 + 31 of U, columns c0 .. wt
+  T* Ui = Us + 32 * wu;                    // [32][32]: the inverse of U's current 32 x 32 diagonal block
+  T* Xs = Ui + 32 * 32;                    // [RB][wx]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r0 = blockIdx.x * RB;
   const int rows = min(RB, m - r0);
   const bool spec = sp.flag != nullptr;
-  if (spec && __ldcg(sp.flag) != 0) return;
-  bool bad = false;
-  for (int j = tid; j < w; j += LS_THREADS) rcp[j] = T(1) / U[(int64_t)j * ld + j];
-  for (int r = warp; r < RB; r += LS_THREADS / 32) {
-    const bool ok = r < rows;
-    for (int c = lane; c < w; c += 32) {
-      const T v = ok ? X[(int64_t)(r0 + r) * ld + c] : T(0);
-      Xs[r * wx + c] = v;
-      if (spec && ok) sp.backup[(int64_t)(r0 + r) * w + c] = v;
-    }
+  if (spec) {
+    const bool stop = first ? __ldcg(sp.flag) != 0 : (__ldcg(sp.flag) != 0 || __ldcg(sp.flag + 3) != 0);
+    if (stop) return;
   }
-  for (int c0 = 0; c0 < w; c0 += 32) {
-    const int bw = min(32, w - c0);
+  bool bad = false;
+  const bool uvec = ((reinterpret_cast<uintptr_t>(U) & 15) == 0) && ((ld * (int64_t)sizeof(T)) & 15) == 0;
+  load_rows<T, LS_THREADS>(X + (int64_t)r0 * ld, ld, rows, RB, wt, Xs, wx,
+                           (spec && first) ? sp.backup + (int64_t)r0 * wt : nullptr);
+  for (int c0 = 0; c0 < ws; c0 += 32) {
+    const int bw = min(32, ws - c0);
     __syncthreads();  // the previous block's update is done with Us
-    for (int k = warp; k < bw; k += LS_THREADS / 32)
-      for (int c = c0 + lane; c < w; c += 32) Us[k * wu + c] = U[(int64_t)(c0 + k) * ld + c];
+    // U's rows c0 .. c0 + bw, columns c0 .. wt: asynchronous copies, all in flight together
+    {
+      const int nv = uvec ? (wt - c0) / VN : 0;  // c0 is a multiple of 32: 16-byte aligned when U's rows are
+      for (int e = tid; e < bw * nv; e += LS_THREADS) {
+        const int k = e / nv, v = e % nv;
+        cp_async<16>(&Us[k * wu + c0 + v * VN], &U[(int64_t)(c0 + k) * ld + c0 + v * VN]);
+      }
+      const int done = c0 + nv * VN, rest = wt - done;
+      for (int e = tid; e < bw * rest; e += LS_THREADS) {
+        const int k = e / rest, c = done + e % rest;
+        cp_async<sizeof(T)>(&Us[k * wu + c], &U[(int64_t)(c0 + k) * ld + c]);
+      }
+      const T* ub = uinv + (size_t)(c0 / 32) * 1024;
+      for (int e = tid; e < 1024 / VN; e += LS_THREADS) cp_async<16>(&Ui[e * VN], &ub[e * VN]);
+      cp_async_wait_all();
+    }
     __syncthreads();
-    if (tid < rows) {
-      T a[32];
+    // the diagonal block: X_b <- X_b Ui, a small product over the whole CTA
+    // (rows x quads of columns; results held until every thread has read)
+    {
+      T res[(RB * 8 + LS_THREADS - 1) / LS_THREADS][4];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) a[j] = j < bw ? Xs[tid * wx + c0 + j] : T(0);
+      for (int it = 0; it < (RB * 8 + LS_THREADS - 1) / LS_THREADS; ++it) {
+        const int e = tid + it * LS_THREADS;
+        const int r = e >> 3, cq = (e & 7) * 4;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        if (j < bw) {
-          const T x = a[j] * rcp[c0 + j];
-          if (spec && !spec_ok_mult(x)) bad = true;
-          a[j] = x;
+        for (int q = 0; q < 4; ++q) res[it][q] = T(0);
+        if (e < RB * 8) {
+#pragma unroll 8
+          for (int k = 0; k < bw; ++k) {
+            const T xk = Xs[r * wx + c0 + k];
+            T uv[4];
+            v16_get<T>(*reinterpret_cast<const VT*>(&Ui[k * 32 + cq]), uv);
+            if (VN == 2) v16_get<T>(*reinterpret_cast<const VT*>(&Ui[k * 32 + cq + 2]), uv + 2);
 #pragma unroll
-          for (int k = j + 1; k < 32; ++k)
-            if (k < bw) a[k] -= x * Us[j * wu + c0 + k];
+            for (int q = 0; q < 4; ++q) res[it][q] = fma(xk, uv[q], res[it][q]);
+          }
         }
       }
+      __syncthreads();
 #pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (j < bw) Xs[tid * wx + c0 + j] = a[j];
+      for (int it = 0; it < (RB * 8 + LS_THREADS - 1) / LS_THREADS; ++it) {
+        const int e = tid + it * LS_THREADS;
+        const int r = e >> 3, cq = (e & 7) * 4;
+        if (e < RB * 8) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (cq + q < bw) {
+              Xs[r * wx + c0 + cq + q] = res[it][q];
+              if (spec && r < rows && !spec_ok_mult(res[it][q])) bad = true;
+            }
+          }
+        }
+      }
     }
     __syncthreads();
-    const int c1 = c0 + bw;  // columns [c1, w) remain (only when bw == 32)
+    const int c1 = c0 + bw;  // columns [c1, wt) remain
     const int rg = tid >> 4, cg = tid & 15;
-    for (int cc = c1 + 4 * cg; cc < w; cc += 64) {
+    for (int cc = c1 + 4 * cg; cc < wt; cc += 64) {
       T acc[RT][4];
 #pragma unroll
       for (int i = 0; i < RT; ++i)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[i][q] = T(0);
-#pragma unroll 8
-      for (int k = 0; k < 32; ++k) {
+#pragma unroll 4
+      for (int k = 0; k < bw; ++k) {
+        // columns past wt are never stored; c1 and cc are multiples of 4 (a
+        // remaining column exists only after a full 32-column block), so the
+        // 16-byte loads stay inside the stage's 16-byte rows
         T ub[4], xa[RT];
-        load4s<T>(&Us[k * wu + cc], ub);  // columns past w are never stored
+        const T* up = &Us[k * wu + cc];
+        v16_get<T>(*reinterpret_cast<const VT*>(up), ub);
+        if (VN == 2) v16_get<T>(*reinterpret_cast<const VT*>(up + 2), ub + 2);
 #pragma unroll
         for (int i = 0; i < RT; ++i) xa[i] = Xs[(RT * rg + i) * wx + c0 + k];
 #pragma unroll
@@ -317,15 +462,16 @@ __global__ void __launch_bounds__(LS_THREADS) trsm_right_upper_kernel(const T* _
       for (int i = 0; i < RT; ++i)
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-          if (cc + q < w) Xs[(RT * rg + i) * wx + cc + q] -= acc[i][q];
+          if (cc + q < wt) Xs[(RT * rg + i) * wx + cc + q] -= acc[i][q];
     }
   }
   __syncthreads();
   for (int r = warp; r < rows; r += LS_THREADS / 32)
-    for (int c = lane; c < w; c += 32) X[(int64_t)(r0 + r) * ld + c] = Xs[r * wx + c];
-  if (spec && __syncthreads_or(bad) && tid == 0) sp.flag[3] = kabs + 1;
+    for (int c = lane; c < wt; c += 32) X[(int64_t)(r0 + r) * ld + c] = Xs[r * wx + c];
+  if (spec && __syncthreads_or(bad) && tid == 0) sp.flag[3] = tag;
 }
 
+// ============================================================ launchers
 template <typename T>
 static SpecDev<T> spec_dev(const SpecArgs& a, int64_t backup_offset) {
   SpecDev<T> d;
@@ -336,53 +482,100 @@ static SpecDev<T> spec_dev(const SpecArgs& a, int64_t backup_offset) {
   return d;
 }
 
-template <typename T>
-cudaError_t launch_diag_lu(T* D, int64_t ld, int w, int kabs, int* info, cudaStream_t st, const SpecArgs& spec) {
-  if (w <= 0) return cudaSuccess;
-  const int wp = (w + 3) & ~3;
-  const size_t smem = ((size_t)NP_NB * wp + (size_t)NP_NB * NP_CW) * sizeof(T);
-  auto kern = diag_lu_kernel<T>;
-  cudaError_t e = allow_max_smem((const void*)kern);
-  if (e != cudaSuccess) return e;
-  kern<<<1, np_threads<T>(), smem, st>>>(D, ld, w, kabs, info, spec_dev<T>(spec, 0));
-  return cudaGetLastError();
-}
-
-static size_t ls_smem(int rb, int w, int tsize) {
-  const size_t wu = (size_t)((w + 3) & ~3);
-  return (32 * wu + wu + (size_t)rb * (w | 1)) * tsize;
-}
-
-template <typename T, int RB>
-static cudaError_t launch_ls(const T* U, T* X, int64_t ld, int m, int w, int kabs, const SpecDev<T>& sp,
-                             cudaStream_t st) {
-  auto kern = trsm_right_upper_kernel<T, RB>;
-  cudaError_t e = allow_max_smem((const void*)kern);
-  if (e != cudaSuccess) return e;
-  kern<<<(unsigned)cdiv(m, RB), LS_THREADS, ls_smem(RB, w, sizeof(T)), st>>>(U, X, ld, m, w, kabs, sp);
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_trsm_right_upper(const T* U, T* X, int64_t ld, int m, int w, cudaStream_t st,
-                                    const SpecArgs& spec, int kabs) {
-  if (m <= 0 || w <= 0) return cudaSuccess;
+static int device_smem_optin() {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  // the rows below the panel's w x w block follow it in the backup
-  const SpecDev<T> sp = spec_dev<T>(spec, (int64_t)w * w);
-  if (ls_smem(64, w, sizeof(T)) <= (size_t)optin) return launch_ls<T, 64>(U, X, ld, m, w, kabs, sp, st);
-  if (ls_smem(32, w, sizeof(T)) <= (size_t)optin) return launch_ls<T, 32>(U, X, ld, m, w, kabs, sp, st);
-  if (ls_smem(16, w, sizeof(T)) <= (size_t)optin) return launch_ls<T, 16>(U, X, ld, m, w, kabs, sp, st);
+  return optin;
+}
+
+// Slab height: the largest multiple of 32, at most 128, whose rows fit in
+// 136 KB of shared memory.
+static int slab_rows(int w, int tsize) {
+  const size_t row = (size_t)(w | 1) * tsize;
+  int h = 128;
+  while (h > 32 && (size_t)h * row > 136 * 1024) h -= 32;
+  return h;
+}
+
+static size_t ls_smem(int rb, int wt, int tsize) {
+  const size_t wu = (size_t)((wt + 3) & ~3);
+  return (32 * wu + 32 * 32 + (size_t)rb * (wt | 1)) * tsize;
+}
+
+template <typename T, int RB>
+static cudaError_t launch_ls(const T* U, const T* uinv, T* X, int64_t ld, int m, int ws, int wt,
+                             const SpecDev<T>& sp, int first, int tag, cudaStream_t st) {
+  auto kern = below_solve_kernel<T, RB>;
+  cudaError_t e = allow_max_smem((const void*)kern);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)cdiv(m, RB), LS_THREADS, ls_smem(RB, wt, sizeof(T)), st>>>(U, uinv, X, ld, m, ws, wt, sp, first,
+                                                                               tag);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t launch_below(const T* U, const T* uinv, T* X, int64_t ld, int m, int ws, int wt,
+                                const SpecDev<T>& sp, int first, int tag, cudaStream_t st) {
+  const int optin = device_smem_optin();
+  if (ls_smem(64, wt, sizeof(T)) <= (size_t)optin)
+    return launch_ls<T, 64>(U, uinv, X, ld, m, ws, wt, sp, first, tag, st);
+  if (ls_smem(32, wt, sizeof(T)) <= (size_t)optin)
+    return launch_ls<T, 32>(U, uinv, X, ld, m, ws, wt, sp, first, tag, st);
+  if (ls_smem(16, wt, sizeof(T)) <= (size_t)optin)
+    return launch_ls<T, 16>(U, uinv, X, ld, m, ws, wt, sp, first, tag, st);
   return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_diag_lu<double>(double*, int64_t, int, int, int*, cudaStream_t, const SpecArgs&);
-template cudaError_t launch_diag_lu<float>(float*, int64_t, int, int, int*, cudaStream_t, const SpecArgs&);
-template cudaError_t launch_trsm_right_upper<double>(const double*, double*, int64_t, int, int, cudaStream_t,
-                                                     const SpecArgs&, int);
-template cudaError_t launch_trsm_right_upper<float>(const float*, float*, int64_t, int, int, cudaStream_t,
-                                                    const SpecArgs&, int);
+template <typename T>
+cudaError_t launch_block_column(T* P, int64_t ld, int m, int w, int kabs, int* info, T* uinv, cudaStream_t st,
+                                const SpecArgs& spec) {
+  if (w <= 0) return cudaSuccess;
+  if (m < w) return cudaErrorInvalidValue;
+  const int h = slab_rows(w, sizeof(T));
+  auto kern = slab_lu_kernel<T>;
+  cudaError_t e = allow_max_smem((const void*)kern);
+  if (e != cudaSuccess) return e;
+  const int tag = kabs + 1;
+  for (int s0 = 0; s0 < w; s0 += h) {
+    const int hs = (w - s0) < h ? (w - s0) : h;
+    const int wt = w - s0;
+    const int first = s0 == 0;
+    T* D = P + (int64_t)s0 * ld + s0;
+    // a failed check of the first slab changed only its rows; any later
+    // failure, every row of the block column
+    const int restore = first ? hs : m;
+    const size_t smem = ((size_t)hs * (wt | 1) + hs) * sizeof(T);
+    kern<<<1, SL_THREADS, smem, st>>>(D, ld, hs, wt, kabs + s0, info, spec_dev<T>(spec, 0), first, tag, restore);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int below = m - s0 - hs;
+    T* ui = uinv + (size_t)(s0 / 32) * 1024;  // the slab's diagonal blocks' inverses
+    if (below > 0) {
+      uinv_kernel<T><<<(hs + 31) / 32, 32, 0, st>>>(D, ld, hs, ui);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      // the first slab's rows below it follow its rows in the backup (row stride w)
+      e = launch_below<T>(D, ui, D + (int64_t)hs * ld, ld, below, hs, wt, spec_dev<T>(spec, (int64_t)hs * w), first,
+                          tag, st);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+int block_column_launches(int m, int w, int tsize) {
+  if (w <= 0) return 0;
+  const int h = slab_rows(w, tsize);
+  int n = 0;
+  for (int s0 = 0; s0 < w; s0 += h) {
+    const int hs = (w - s0) < h ? (w - s0) : h;
+    n += (m - s0 - hs) > 0 ? 3 : 1;
+  }
+  return n;
+}
+
+template cudaError_t launch_block_column<double>(double*, int64_t, int, int, int, int*, double*, cudaStream_t,
+                                                 const SpecArgs&);
+template cudaError_t launch_block_column<float>(float*, int64_t, int, int, int, int*, float*, cudaStream_t,
+                                                const SpecArgs&);
 
 }  // namespace gb

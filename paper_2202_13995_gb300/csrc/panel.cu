@@ -134,10 +134,10 @@ __global__ void __launch_bounds__(PNL_THREADS) panel_getrf_kernel(PanelParams<T>
     // the diagonal-pivot check ran first: nothing to do if the panel passed;
     // otherwise put back the rows it changed (this CTA's own rows; other CTAs
     // read them only after a grid barrier)
-    const int f0 = __ldcg(P.spec), f1 = __ldcg(P.spec + 1), f3 = __ldcg(P.spec + 3);
+    const int f0 = __ldcg(P.spec), f1 = __ldcg(P.spec + 1), f2 = __ldcg(P.spec + 2), f3 = __ldcg(P.spec + 3);
     if (f0 == 0 && f3 == 0) return;
     const int tag = P.kabs + 1;
-    const int rlim = f3 == tag ? P.m : (f1 == tag ? w : 0);
+    const int rlim = f3 == tag ? P.m : (f1 == tag ? min(f2, P.m) : 0);
     const int rend = min(rloc, rlim - row0);
     for (int r = warp; r < rend; r += PNL_WARPS)
       for (int c = lane; c < w; c += 32) P.A[(int64_t)(row0 + r) * ld + c] = P.spec_backup[(int64_t)(row0 + r) * w + c];

@@ -15,7 +15,7 @@ import pytest
 
 import oracle as O
 from paper_2202_13995_gb300 import inputs as I
-from tests.conftest import check_full_size_f64
+from tests.conftest import check_full_size_f64, oracle_cache
 
 pytestmark = pytest.mark.gpu
 EPS = 2.0 ** -53
@@ -267,3 +267,29 @@ def test_full_size_mixed_n32768(ctx, mixed_n32768, prec, nrhs):
     assert err <= 1e-10, err
     assert np.all(np.atleast_1d(O.scaled_residual(M["A"], Xg, M["B"][:, :nrhs])) < 16.0)
     assert ctx.status() == 0
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+def test_full_size_mixed_n32768_vs_oracle(ctx, mixed_n32768, prec):
+    """The mixed configuration exactly as benchmarked (A + (n/4) I and b of
+    seed 3): pivots and the refined x against the oracle's cached FP64 run
+    (tests/golden/make_oracle_cache.py), x within 1e-10 (kappa ~ 4)."""
+    import torch
+    from paper_2202_13995_gb300 import lu
+    ref = oracle_cache("hpl_shift_n32768_seed3")
+    M = mixed_n32768
+    n = M["n"]
+    assert int(ref["n"]) == n
+    f = ctx.factor(M["Ad"], prec, 0)
+    assert f.info == 0
+    assert np.array_equal(f.ipiv().cpu().numpy(), ref["ipiv"])
+    bd = I.hpl_rhs_torch(n, 1, 3, device="cuda")
+    X = lu.colmajor_empty(n, 1)
+    iters, res = f.refine(M["Ad"], bd, X, 16.0, 50)
+    f.free()
+    torch.cuda.synchronize()
+    assert res < 16.0
+    xo = ref["x"][:, 0]
+    err = np.abs(X.cpu().numpy()[:, 0] - xo).max() / np.abs(xo).max()
+    assert err <= max(1e-10, 10 * float(ref["kappa1_est"]) * EPS), err
