@@ -181,11 +181,10 @@ def max_over_ranks(v: float, ws: int) -> float:
     return float(t.item())
 
 
-def default_nb(n: int, prec: str) -> int:
-    # mirrors the library's default block width (nb = 0)
-    if prec in ("f64", "f32"):
-        return 256 if n >= 4096 else 64
-    return 256 if n >= 2048 else 64
+def default_nb(n: int, prec: str, ozaki: bool = False) -> int:
+    """The block width the library picks for nb = 0 (its tuning table)."""
+    from paper_2202_13995_gb300 import lu
+    return lu.default_nb(n, prec, ozaki)
 
 
 def gemm_roofline(prof: dict, n: int, nb: int, prec: str, steps: int, peaks: dict, wname: str,
@@ -201,7 +200,7 @@ def gemm_roofline(prof: dict, n: int, nb: int, prec: str, steps: int, peaks: dic
     (tcgen05, BF16 slices): bound by the tensor pipe; algorithmic FLOPs per
     launch = 36 slice pairs x 2 m' n' kpad."""
     gemm_ms, gemm_n = prof["gemm"]
-    nbx = nb or default_nb(n, prec)
+    nbx = nb or default_nb(n, prec, ozaki)
     kpad = -(-nbx // 64) * 64
     flops = bytes_ = 0.0
     dram_alg = 0.0  # algorithmic DRAM bytes of the kernel's own data type, all launches of one step
@@ -224,8 +223,9 @@ def gemm_roofline(prof: dict, n: int, nb: int, prec: str, steps: int, peaks: dic
     sec = gemm_ms * 1e-3
     kernel = "oz_gemm_kernel" if ozaki else ("gemm_simt_kernel<double>" if prec == "f64" else "tc_gemm_kernel")
     # traffic per launch: the ratio of ncu DRAM bytes to algorithmic bytes of
-    # launches captured at full size (profiles/traffic.json, one entry per
-    # kernel), times this step's mean algorithmic bytes per update
+    # launches captured on a small case of the same kernel (profiles/traffic.json,
+    # one entry per kernel; counters beyond the launch time are collected only
+    # on small cases), times this step's mean algorithmic bytes per update
     traffic = traffic_ratio = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath) and nlaunch:
@@ -508,6 +508,13 @@ def served_measure(cfg: dict, rate: float = None, seconds: float = None) -> dict
     for r, (_, n, k, _) in zip(res, tickets):
         flops += (0.0 if r.reused_factor else 2.0 / 3.0 * n ** 3) + 2.0 * n * n * k * (1 + r.iters)
     ok = sum(1 for r in res if r.status == 0)
+    # service time (start to done) by size bucket: where the capacity goes
+    buckets = {}
+    for r, (_, n, k, rp) in zip(res, tickets):
+        key = "repeat" if r.reused_factor else ("n<=512" if n <= 512 else ("n<=2048" if n <= 2048 else "n>2048"))
+        buckets.setdefault(key, []).append((r.t_done_ns - r.t_start_ns) * 1e-6)
+    by_size = {kk: {"count": len(v), "service_p50_ms": float(np.percentile(v, 50)),
+                    "service_p99_ms": float(np.percentile(v, 99))} for kk, v in sorted(buckets.items())}
     status_hist = {}
     for r in res:
         status_hist[str(r.status)] = status_hist.get(str(r.status), 0) + 1
@@ -517,6 +524,7 @@ def served_measure(cfg: dict, rate: float = None, seconds: float = None) -> dict
             "reused_factor": int(sum(r.reused_factor for r in res)),
             "refactored": int(sum(r.refactored for r in res)), "evictions": int(stats["evictions"]),
             "max_scaled_residual": float(max(r.scaled_resid for r in res)), "tflops": flops / span / 1e12,
+            "service_by_size": by_size,
             "slots": cfg["slots"], "budget_gb": cfg["budget_gb"], "prec": cfg["prec"],
             "wall_s": t_end - t0}
 

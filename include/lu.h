@@ -58,9 +58,33 @@ typedef struct lu_fact_s *lu_fact;
 
 /* Create a context bound to the current CUDA device and to `cuda_stream`
  * (a cudaStream_t; NULL = the legacy default stream).  The context owns a few
- * KB of device scratch and a pinned status word.  Not thread-safe: one host
- * thread per context at a time. */
+ * KB of device scratch and a pinned status word; its device memory comes from
+ * the stream-ordered pool (lu_create_ex takes an allocator instead).  Not
+ * thread-safe: one host thread per context at a time. */
 int lu_create(lu_ctx *out, void *cuda_stream);
+
+/* Device-memory callbacks for a context's workspace (lu_create_ex).
+ * alloc(user, bytes, stream) returns device memory usable by work enqueued on
+ * `stream` from now on (NULL on failure: the call then returns LU_ENOMEM);
+ * release(user, ptr, bytes, stream) gives a block back once the work already
+ * enqueued on `stream` has no further use for it -- the block must not be
+ * reused for other work until that work has finished, as with cudaFreeAsync
+ * or a caching allocator that records the stream (torch's
+ * caching_allocator_alloc / caching_allocator_delete behave this way).
+ * `bytes` is the size the block was allocated with.  The callbacks run on
+ * the host thread that calls into the library. */
+typedef void *(*lu_alloc_fn)(void *user, size_t bytes, void *cuda_stream);
+typedef void (*lu_free_fn)(void *user, void *ptr, size_t bytes, void *cuda_stream);
+
+/* lu_create with the context's device memory drawn from the caller's
+ * allocator: every buffer the context and the factorizations, solves,
+ * refinements, batches and step calls made through it allocate (factors,
+ * pivots, workspaces, status words) comes from alloc and goes back through
+ * release, on the context's stream; lu_destroy releases the context's own.
+ * Factors keep the allocator of the context that created them.  alloc and
+ * release both NULL = the stream-ordered pool (cudaMallocAsync), as
+ * lu_create; -3 when only one of them is given. */
+int lu_create_ex(lu_ctx *out, void *cuda_stream, lu_alloc_fn alloc, lu_free_fn release, void *user);
 
 /* Synchronize the context's stream and free everything the context owns.
  * Factors created from it must be freed first. */
@@ -71,8 +95,9 @@ const char *lu_strerror(int code);
 
 /* Factor P A = L U of the n x n matrix dA (not modified; read during this
  * call's enqueued work only).  nb is the block width of the paper's blocked
- * iteration (its LOCAL_MEM_BLOCK size); nb = 0 picks the tuned default for
- * (n, prec).  The factors, pivots and workspace are owned by *out, which
+ * iteration (its LOCAL_MEM_BLOCK size); nb = 0 picks the block width of the
+ * library's tuning table for (n, prec, flags) -- the fastest of an offline
+ * sweep of whole solves on this GPU (lu_default_nb tells which).  The factors, pivots and workspace are owned by *out, which
  * lu_fact_free releases.  If info is non-NULL the call synchronizes the stream
  * and stores the LAPACK info (0, or the first zero pivot j, 1-based); with
  * info NULL the call is asynchronous and lu_fact_info reads it later.
@@ -147,6 +172,11 @@ int lu_scaled_residual(lu_ctx ctx, int n, int nrhs, const double *dA, int lda, c
  * way).  Synchronizes.  Errors as lu_scaled_residual. */
 int lu_residual_norms(lu_ctx ctx, int n, int nrhs, const double *dA, int lda, const double *dX, int ldx,
                       const double *dB, int ldb, double *out);
+
+/* The block width nb = 0 selects for an n x n factorization of precision
+ * prec with lu_factor_ex flags `flags` (the tuning table's entry; at most n).
+ * Returns -1 (n < 0), -2 (prec invalid). */
+int lu_default_nb(int n, lu_prec prec, int flags);
 
 /* Device bytes that lu_factor (block width nb, 0 = default) plus lu_refine
  * with nrhs right-hand sides allocate for an n x n system on the current

@@ -91,6 +91,15 @@ int lu_step_gemm_ozaki(lu_ctx ctx, int m, int n, int k, double *dC, int ldc, con
  * usable.  Synchronizes.  Returns -1 (ctx NULL), -2 (kind not 0..2). */
 int lu_step_wait_probe(lu_ctx ctx, int kind);
 
+/* Arithmetic-rate probe of the current device, for roofline denominators
+ * (the paper has no counterpart): kind 0 = FP64 fused multiply-add on the
+ * CUDA cores, 1 = FP64 warp matrix multiply-accumulate (mma.sync m8n8k4),
+ * 2 = FP32 fused multiply-add on the CUDA cores.  Runs a register-only kernel
+ * on every SM for a few tens of milliseconds and stores the best of three
+ * timed launches in *tflops (host).  Synchronizes; allocates 64 bytes.
+ * Returns -1 (kind not 0..2), -2 (tflops NULL), LU_ECUDA / LU_ENOMEM. */
+int lu_peak_probe(int kind, double *tflops);
+
 /* Read and clear the context's device status bits (synchronizes): returns
  * LU_OK, LU_ETIMEOUT or LU_ERANGE. */
 int lu_ctx_status(lu_ctx ctx);

@@ -514,6 +514,8 @@ cudaStream_t gb_ctx_stream(lu_ctx c);
 int gb_ctx_sm_count(lu_ctx c);
 int* gb_ctx_status(lu_ctx c);
 void gb_ctx_count_launches(lu_ctx c, long long k);
+void* gb_ctx_alloc(lu_ctx c, size_t bytes);
+void gb_ctx_free(lu_ctx c, void* p);
 
 template <int NT>
 static cudaError_t launch_batched(lu_batch b, int* info, int* iters, double* resid, cudaStream_t st) {
@@ -547,8 +549,8 @@ static int occupancy(int threads) {
 extern "C" void lu_batch_free(lu_batch b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->d_desc) cudaFreeAsync(b->d_desc, b->stream);
-  if (b->d_scratch) cudaFreeAsync(b->d_scratch, b->stream);
+  gb_ctx_free(b->ctx, b->d_desc);
+  gb_ctx_free(b->ctx, b->d_scratch);
   delete b;
 }
 
@@ -596,17 +598,16 @@ extern "C" int lu_batch_create(lu_ctx ctx, int count, const int* n, const int* n
   const int slots = b->sm_count * maxper;
   const size_t desc_bytes = ((sizeof(BatchDesc) * std::max(count, 1) + 255) / 256) * 256;
   const size_t order_bytes = ((sizeof(int) * std::max(count, 1) + 255) / 256) * 256;
-  void* p = nullptr;
-  if (cudaMallocAsync(&p, desc_bytes + order_bytes + 256, b->stream) != cudaSuccess) {
-    cudaGetLastError();
+  void* p = gb_ctx_alloc(ctx, desc_bytes + order_bytes + 256);
+  if (!p) {
     delete b;
     return LU_ENOMEM;
   }
   b->d_desc = (BatchDesc*)p;
   b->d_order = (int*)((char*)p + desc_bytes);
   b->d_next = (int*)((char*)p + desc_bytes + order_bytes);
-  if (cudaMallocAsync((void**)&b->d_scratch, sizeof(float) * b->slot_floats * slots, b->stream) != cudaSuccess) {
-    cudaGetLastError();
+  b->d_scratch = (float*)gb_ctx_alloc(ctx, sizeof(float) * b->slot_floats * slots);
+  if (!b->d_scratch) {
     lu_batch_free(b);
     return LU_ENOMEM;
   }
@@ -624,9 +625,8 @@ extern "C" int lu_batch_create(lu_ctx ctx, int count, const int* n, const int* n
   b->grid = std::min(std::max(count, 1), b->sm_count * b->ctas_per_sm);
   if (tune && count > 0) {
     // time each candidate shape on this batch and keep the fastest
-    int* tinfo = nullptr;
-    if (cudaMallocAsync((void**)&tinfo, sizeof(int) * count, b->stream) != cudaSuccess) {
-      cudaGetLastError();
+    int* tinfo = (int*)gb_ctx_alloc(ctx, sizeof(int) * count);
+    if (!tinfo) {
       lu_batch_free(b);
       return LU_ENOMEM;
     }
@@ -661,7 +661,7 @@ extern "C" int lu_batch_create(lu_ctx ctx, int count, const int* n, const int* n
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFreeAsync(tinfo, b->stream);
+    gb_ctx_free(ctx, tinfo);
     b->threads = bt;
     b->ctas_per_sm = bc;
     b->grid = std::min(count, b->sm_count * bc);

@@ -14,18 +14,66 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "lu.h"
 #include "lu_steps.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "nb_table.h"
 
 using namespace gb;
 
+// Workspace allocation of a context: the caller's callbacks (lu_create_ex),
+// or the stream-ordered pool (cudaMallocAsync).  Sizes are remembered so that
+// a release can hand them back to the callback.
+struct Allocator {
+  lu_alloc_fn alloc = nullptr;
+  lu_free_fn release = nullptr;
+  void* user = nullptr;
+  std::mutex mu;
+  std::unordered_map<void*, size_t> sizes;
+  void* get(size_t bytes, cudaStream_t st) {
+    void* p = nullptr;
+    if (alloc) {
+      p = alloc(user, bytes, (void*)st);
+      if (p) {
+        std::lock_guard<std::mutex> lk(mu);
+        sizes[p] = bytes;
+      }
+      return p;
+    }
+    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void put(void* p, cudaStream_t st) {
+    if (!p) return;
+    if (release) {
+      size_t bytes = 0;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = sizes.find(p);
+        if (it != sizes.end()) {
+          bytes = it->second;
+          sizes.erase(it);
+        }
+      }
+      release(user, p, bytes, (void*)st);
+      return;
+    }
+    cudaFreeAsync(p, st);
+  }
+};
+
 struct lu_ctx_s {
   cudaStream_t stream = nullptr;
+  Allocator* mem = nullptr;  // owned; outlives the factors created from this context
   int device = 0;
   DevInfo dev{};
   int* d_status = nullptr;   // device status bits
@@ -94,6 +142,7 @@ static cudaError_t run_phase(lu_ctx c, int phase, int nk, cudaStream_t st, F&& l
 
 struct lu_fact_s {
   lu_ctx ctx = nullptr;
+  Allocator* mem = nullptr;  // the creating context's (the context outlives the factor)
   int n = 0;
   lu_prec prec = LU_F64;
   int nb = 0;
@@ -151,24 +200,38 @@ extern "C" const char* lu_build_tag(void) { return "gb300lu sm_103a"; }
 static int dalloc(lu_ctx c, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return LU_OK;
-  cudaError_t e = cudaMallocAsync(p, bytes, c->stream);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    *p = nullptr;
-    return LU_ENOMEM;
-  }
-  return LU_OK;
+  *p = c->mem->get(bytes, c->stream);
+  return *p ? LU_OK : LU_ENOMEM;
 }
 
-static void dfree(lu_ctx c, void* p) {
-  if (p) cudaFreeAsync(p, c->stream);
-}
+static void dfree(lu_ctx c, void* p) { c->mem->put(p, c->stream); }
 
-extern "C" int lu_create(lu_ctx* out, void* cuda_stream) {
+// a factor's buffers go back to the allocator it came from, on the stream of
+// the context it is bound to now
+static int falloc(lu_fact f, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return LU_OK;
+  *p = f->mem->get(bytes, f->ctx->stream);
+  return *p ? LU_OK : LU_ENOMEM;
+}
+static void ffree(lu_fact f, void* p) { f->mem->put(p, f->ctx->stream); }
+
+extern "C" int lu_create(lu_ctx* out, void* cuda_stream) { return lu_create_ex(out, cuda_stream, nullptr, nullptr, nullptr); }
+
+extern "C" int lu_create_ex(lu_ctx* out, void* cuda_stream, lu_alloc_fn alloc, lu_free_fn release, void* user) {
   if (!out) return -1;
   *out = nullptr;
+  if ((alloc == nullptr) != (release == nullptr)) return -3;
   lu_ctx c = new (std::nothrow) lu_ctx_s();
   if (!c) return LU_ENOMEM;
+  c->mem = new (std::nothrow) Allocator();
+  if (!c->mem) {
+    delete c;
+    return LU_ENOMEM;
+  }
+  c->mem->alloc = alloc;
+  c->mem->release = release;
+  c->mem->user = user;
   c->stream = (cudaStream_t)cuda_stream;
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     delete c;
@@ -176,16 +239,18 @@ extern "C" int lu_create(lu_ctx* out, void* cuda_stream) {
   }
   cudaDeviceGetAttribute(&c->dev.sm_count, cudaDevAttrMultiProcessorCount, c->device);
   cudaDeviceGetAttribute(&c->dev.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
-  if (cudaMalloc(&c->d_status, 64 * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&c->d_small, 128 * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&c->d_active, 64 * sizeof(int)) != cudaSuccess ||
+  if (dalloc(c, (void**)&c->d_status, 64 * sizeof(int)) != LU_OK ||
+      dalloc(c, (void**)&c->d_small, 128 * sizeof(double)) != LU_OK ||
+      dalloc(c, (void**)&c->d_active, 64 * sizeof(int)) != LU_OK ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess ||
       cudaMallocHost(&c->h_pinned, 64 * sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&c->h_norms, 128 * sizeof(double)) != cudaSuccess) {
     lu_destroy(c);
     return LU_ENOMEM;
   }
-  cudaMemset(c->d_status, 0, 64 * sizeof(int));
-  cudaMemset(c->d_small, 0, 128 * sizeof(double));
+  cudaMemsetAsync(c->d_status, 0, 64 * sizeof(int), c->stream);
+  cudaMemsetAsync(c->d_small, 0, 128 * sizeof(double), c->stream);
+  cudaStreamSynchronize(c->stream);
   // the side stream (lookahead panels) has the highest priority, so that a
   // panel waiting for SMs is placed before the concurrent update's CTAs
   int prio_lo = 0, prio_hi = 0;
@@ -218,12 +283,16 @@ extern "C" void lu_destroy(lu_ctx c) {
   }
   if (c->ev_next) cudaEventDestroy(c->ev_next);
   if (c->ev_panel) cudaEventDestroy(c->ev_panel);
-  if (c->step_ws) cudaFree(c->step_ws);
-  if (c->d_status) cudaFree(c->d_status);
-  if (c->d_small) cudaFree(c->d_small);
-  if (c->d_active) cudaFree(c->d_active);
+  if (c->mem) {
+    dfree(c, c->step_ws);
+    dfree(c, c->d_status);
+    dfree(c, c->d_small);
+    dfree(c, c->d_active);
+    cudaStreamSynchronize(c->stream);
+  }
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   if (c->h_norms) cudaFreeHost(c->h_norms);
+  delete c->mem;
   delete c;
 }
 
@@ -281,9 +350,13 @@ extern "C" int lu_ctx_status(lu_ctx c) {
   return read_status(c);
 }
 
-static int default_nb(int n, lu_prec prec) {
-  if (prec == LU_F64 || prec == LU_F32) return n >= 4096 ? 256 : 64;
-  return n >= 2048 ? 256 : 64;
+// nb = 0: the block width of the offline sweep's table (nb_table.h), by
+// factorization kind and size
+static int default_nb(int n, lu_prec prec, bool split) {
+  const int kind = prec == LU_F64 ? (split ? 1 : 0) : (prec == LU_F32 ? 3 : 2);
+  for (const NbEntry& e : kNbTable)
+    if (e.kind == kind && n <= e.nmax) return e.nb;
+  return 256;
 }
 
 static int round_up(int v, int a) { return (v + a - 1) / a * a; }
@@ -524,19 +597,9 @@ static int factor_loop_nopiv(lu_fact f) {
 
 extern "C" void lu_fact_free(lu_fact f) {
   if (!f) return;
-  lu_ctx c = f->ctx;
-  dfree(c, f->W);
-  dfree(c, f->ipiv);
-  dfree(c, f->panel_mem);
-  dfree(c, f->aop);
-  dfree(c, f->oz_ws);
-  dfree(c, f->oz_minv);
-  dfree(c, f->spec_flag);
-  dfree(c, f->spec_backup);
-  dfree(c, f->uinv);
-  dfree(c, f->solve_mem);
-  dfree(c, f->ss.dinv);
-  dfree(c, f->vec_ws);
+  for (void* p : {f->W, (void*)f->ipiv, f->panel_mem, f->aop, f->oz_ws, (void*)f->oz_minv, (void*)f->spec_flag,
+                  f->spec_backup, f->uinv, f->solve_mem, f->ss.dinv, (void*)f->vec_ws})
+    ffree(f, p);
   delete f;
 }
 
@@ -558,11 +621,12 @@ extern "C" int lu_factor_ex(lu_ctx c, int n, const double* dA, int lda, lu_prec 
   if (nb < 0 || nb > 512) return -6;
   if (!out) return -8;
   *out = nullptr;
-  if (nb == 0) nb = default_nb(n, prec);
+  if (nb == 0) nb = default_nb(n, prec, (flags & LU_FACTOR_OZAKI) != 0);
   if ((flags & LU_FACTOR_OZAKI) && nb > 256) return -6;
   lu_fact f = new (std::nothrow) lu_fact_s();
   if (!f) return LU_ENOMEM;
   f->ctx = c;
+  f->mem = c->mem;
   f->n = n;
   f->prec = prec;
   f->nb = nb < n ? nb : (n > 0 ? n : 1);
@@ -572,10 +636,10 @@ extern "C" int lu_factor_ex(lu_ctx c, int n, const double* dA, int lda, lu_prec 
   int rc = LU_OK;
   const int gmax = c->dev.sm_count;
   size_t pbytes = panel_scratch_bytes(gmax, 32, f->nb, f->tsize);
-  if ((rc = dalloc(c, &f->W, (size_t)f->ldw * nn * f->tsize)) ||
-      (rc = dalloc(c, (void**)&f->ipiv, (size_t)(2 * nn + 64) * sizeof(int))) ||
-      (rc = dalloc(c, &f->panel_mem, pbytes)) ||
-      (rc = dalloc(c, &f->solve_mem, solve_scratch_bytes(nn, f->tsize)))) {
+  if ((rc = falloc(f, &f->W, (size_t)f->ldw * nn * f->tsize)) ||
+      (rc = falloc(f, (void**)&f->ipiv, (size_t)(2 * nn + 64) * sizeof(int))) ||
+      (rc = falloc(f, &f->panel_mem, pbytes)) ||
+      (rc = falloc(f, &f->solve_mem, solve_scratch_bytes(nn, f->tsize)))) {
     lu_fact_free(f);
     return rc;
   }
@@ -590,36 +654,36 @@ extern "C" int lu_factor_ex(lu_ctx c, int n, const double* dA, int lda, lu_prec 
   solve_scratch_carve(&f->ss, f->solve_mem, nn, f->tsize);
   if (prec != LU_F64) {
     // FP32 factors: inverted diagonal blocks for the correction solves
-    if ((rc = dalloc(c, &f->ss.dinv, solve_dinv_bytes(nn, f->tsize)))) {
+    if ((rc = falloc(f, &f->ss.dinv, solve_dinv_bytes(nn, f->tsize)))) {
       lu_fact_free(f);
       return rc;
     }
   }
   if (flags & LU_FACTOR_OZAKI) {
     f->ozaki = true;
-    if ((rc = dalloc(c, &f->oz_ws, ozaki_ws_bytes(nn, nn, f->nb, c->dev.sm_count))) ||
-        (rc = dalloc(c, (void**)&f->oz_minv, (size_t)f->nb * f->nb * sizeof(double)))) {
+    if ((rc = falloc(f, &f->oz_ws, ozaki_ws_bytes(nn, nn, f->nb, c->dev.sm_count))) ||
+        (rc = falloc(f, (void**)&f->oz_minv, (size_t)f->nb * f->nb * sizeof(double)))) {
       lu_fact_free(f);
       return rc;
     }
   }
   const bool spec = prec != LU_F64 && !nopiv && c->spec && n > f->nb;
   if (spec) {
-    if ((rc = dalloc(c, (void**)&f->spec_flag, 4 * sizeof(int))) ||
-        (rc = dalloc(c, &f->spec_backup, (size_t)nn * f->nb * f->tsize))) {
+    if ((rc = falloc(f, (void**)&f->spec_flag, 4 * sizeof(int))) ||
+        (rc = falloc(f, &f->spec_backup, (size_t)nn * f->nb * f->tsize))) {
       lu_fact_free(f);
       return rc;
     }
   }
   if (spec || nopiv) {
-    if ((rc = dalloc(c, &f->uinv, (size_t)round_up(f->nb, 32) * 32 * f->tsize))) {
+    if ((rc = falloc(f, &f->uinv, (size_t)round_up(f->nb, 32) * 32 * f->tsize))) {
       lu_fact_free(f);
       return rc;
     }
   }
   if (prec == LU_BF16 || prec == LU_FP16) {
     f->kpad = round_up(f->nb, 64);
-    if ((rc = dalloc(c, &f->aop, (size_t)2 * nn * f->kpad * 2 + 1024))) {
+    if ((rc = falloc(f, &f->aop, (size_t)2 * nn * f->kpad * 2 + 1024))) {
       lu_fact_free(f);
       return rc;
     }
@@ -740,10 +804,10 @@ static int ensure_vec_ws(lu_fact f, int nrhs) {
   const size_t n = (size_t)f->n;
   const size_t need = 2 * n * nrhs * 8 + residual_partial_bytes(f->n, nrhs > 32 ? 32 : nrhs) + 4096;
   if (f->vec_ws_bytes >= need) return LU_OK;
-  dfree(f->ctx, f->vec_ws);
+  ffree(f, f->vec_ws);
   f->vec_ws = nullptr;
   f->vec_ws_bytes = 0;
-  int rc = dalloc(f->ctx, (void**)&f->vec_ws, need);
+  int rc = falloc(f, (void**)&f->vec_ws, need);
   if (rc) return rc;
   f->vec_ws_bytes = need;
   return LU_OK;
@@ -899,14 +963,11 @@ extern "C" int lu_residual_norms(lu_ctx c, int n, int nrhs, const double* dA, in
 // ------------------------------------------------------------------ step-level entry points
 static int ensure_step_ws(lu_ctx c, size_t bytes) {
   if (c->step_ws_bytes >= bytes) return LU_OK;
-  cudaStreamSynchronize(c->stream);
-  if (c->step_ws) cudaFree(c->step_ws);
+  dfree(c, c->step_ws);  // stream-ordered: work already enqueued keeps it until done
   c->step_ws = nullptr;
   c->step_ws_bytes = 0;
-  if (cudaMalloc(&c->step_ws, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return LU_ENOMEM;
-  }
+  int rc = dalloc(c, &c->step_ws, bytes);
+  if (rc) return rc;
   c->step_ws_bytes = bytes;
   return LU_OK;
 }
@@ -1024,12 +1085,17 @@ cudaStream_t gb_ctx_stream(lu_ctx c) { return c->stream; }
 int gb_ctx_sm_count(lu_ctx c) { return c->dev.sm_count; }
 int* gb_ctx_status(lu_ctx c) { return c->d_status; }
 void gb_ctx_count_launches(lu_ctx c, long long k) { c->launches += k; }
+void* gb_ctx_alloc(lu_ctx c, size_t bytes) {
+  void* p = nullptr;
+  return dalloc(c, &p, bytes) == LU_OK ? p : nullptr;
+}
+void gb_ctx_free(lu_ctx c, void* p) { dfree(c, p); }
 
 // Bytes lu_factor (+ lu_refine's workspace for nrhs columns) allocates; the
 // server's admission counts requests with it.
 size_t gb_fact_bytes(int n, int nrhs, lu_prec prec, int nb, int sm_count) {
   const int nn = n > 0 ? n : 1;
-  if (nb == 0) nb = default_nb(n, prec);
+  if (nb == 0) nb = default_nb(n, prec, false);
   nb = nb < nn ? nb : nn;
   const int tsize = prec == LU_F64 ? 8 : 4;
   const size_t ldw = (size_t)round_up(nn, 64);
@@ -1048,6 +1114,13 @@ size_t gb_fact_bytes(int n, int nrhs, lu_prec prec, int nb, int sm_count) {
 // pinned buffers).  The caller guarantees that no work on the old context
 // still uses it.
 void gb_fact_rebind(lu_fact f, lu_ctx c) { f->ctx = c; }
+
+extern "C" int lu_default_nb(int n, lu_prec prec, int flags) {
+  if (n < 0) return -1;
+  if (prec < LU_F64 || prec > LU_F32) return -2;
+  const int nb = default_nb(n, prec, (flags & LU_FACTOR_OZAKI) != 0);
+  return n > 0 && nb > n ? n : nb;
+}
 
 extern "C" size_t lu_fact_bytes(int n, int nrhs, lu_prec prec, int nb) {
   if (n < 1 || nrhs < 0 || prec < LU_F64 || prec > LU_F32 || nb < 0 || nb > 512) return 0;

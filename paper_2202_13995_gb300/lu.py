@@ -30,7 +30,7 @@ EXPORTED = [
     "lu_create", "lu_destroy", "lu_strerror", "lu_factor", "lu_fact_info", "lu_fact_ipiv", "lu_fact_lu",
     "lu_solve", "lu_refine", "lu_scaled_residual", "lu_residual_norms", "lu_fact_free",
     "lu_step_panel", "lu_step_trsm", "lu_step_gemm", "lu_ctx_status", "lu_device_sm_count", "lu_build_tag",
-    "lu_profile_enable", "lu_profile_select", "lu_profile_read", "lu_launch_count", "lu_step_panel_static",
+    "lu_create_ex", "lu_peak_probe", "lu_default_nb", "lu_profile_enable", "lu_profile_select", "lu_profile_read", "lu_launch_count", "lu_step_panel_static",
     "lu_batch_create", "lu_batch_run", "lu_batch_shape", "lu_batch_free", "lu_solve_batched",
     "lu_server_create", "lu_server_submit", "lu_server_poll", "lu_server_wait", "lu_server_stats",
     "lu_server_destroy", "lu_fact_bytes", "lu_factor_ex", "lu_step_gemm_ozaki", "lu_step_wait_probe",
@@ -39,6 +39,12 @@ PHASES = ["panel", "laswp", "trsm", "cast", "gemm", "solve", "residual", "other"
 
 _lock = threading.Lock()
 _lib = None
+
+
+# device-memory callbacks of lu_create_ex: alloc(user, bytes, stream) -> ptr,
+# release(user, ptr, bytes, stream)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p)
 
 
 class LuRequest(C.Structure):
@@ -76,6 +82,9 @@ def load():
         DP = C.POINTER(C.c_double)
         sig = {
             "lu_create": (I, [PP, P]),
+            "lu_create_ex": (I, [PP, P, ALLOC_FN, FREE_FN, P]),
+            "lu_peak_probe": (I, [I, DP]),
+            "lu_default_nb": (I, [I, I, I]),
             "lu_destroy": (None, [P]),
             "lu_strerror": (C.c_char_p, [I]),
             "lu_factor": (I, [P, I, P, I, I, I, PP, IP]),
@@ -155,6 +164,20 @@ def _rowmajor(t, name: str):
     return t.data_ptr(), max(1, ld)
 
 
+def default_nb(n: int, prec="f64", ozaki: bool = False) -> int:
+    """The block width nb = 0 selects (the library's tuning table)."""
+    v = load().lu_default_nb(int(n), _prec(prec), LU_FACTOR_OZAKI if ozaki else 0)
+    _check(0 if v > 0 or n == 0 else v, "lu_default_nb")
+    return int(v)
+
+
+def peak_probe(kind: int) -> float:
+    """TFLOP/s of an arithmetic-rate probe (0 FP64 FMA, 1 FP64 mma.sync, 2 FP32 FMA) on the current device."""
+    out = C.c_double(0.0)
+    _check(load().lu_peak_probe(int(kind), C.byref(out)), "lu_peak_probe")
+    return float(out.value)
+
+
 def fact_bytes(n: int, nrhs: int, prec="fp16", nb: int = 0) -> int:
     """Device bytes lu_factor + lu_refine allocate for this system (budgeting)."""
     return int(load().lu_fact_bytes(int(n), int(nrhs), _prec(prec), int(nb)))
@@ -169,7 +192,11 @@ def colmajor_empty(n: int, k: int, device="cuda", dtype=None):
 class Context:
     """A library context bound to a CUDA stream (default: torch's current stream)."""
 
-    def __init__(self, stream=None):
+    def __init__(self, stream=None, allocator=None):
+        """allocator: None (the library's stream-ordered pool) or a pair of
+        callables (alloc(nbytes, stream_handle) -> device pointer int, release(
+        ptr, nbytes, stream_handle)) through which every device buffer of this
+        context passes (lu_create_ex)."""
         import torch
         lib = load()
         if stream is None:
@@ -178,7 +205,24 @@ class Context:
         h = C.c_void_p()
         self._h = None
         self._factors = weakref.WeakSet()
-        _check(lib.lu_create(C.byref(h), C.c_void_p(stream.cuda_stream)), "lu_create")
+        if allocator is None:
+            _check(lib.lu_create(C.byref(h), C.c_void_p(stream.cuda_stream)), "lu_create")
+        else:
+            alloc, release = allocator
+
+            def _alloc(user, nbytes, st):
+                try:
+                    return int(alloc(int(nbytes), st or 0)) or None
+                except Exception:
+                    return None
+
+            def _release(user, ptr, nbytes, st):
+                release(int(ptr), int(nbytes), st or 0)
+
+            # the ctypes callback objects must live as long as the context
+            self._cb = (ALLOC_FN(_alloc), FREE_FN(_release))
+            _check(lib.lu_create_ex(C.byref(h), C.c_void_p(stream.cuda_stream), self._cb[0], self._cb[1], None),
+                   "lu_create_ex")
         self._h = h
 
     @property
