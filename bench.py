@@ -61,7 +61,7 @@ WORKLOADS = {
     # the served configuration: Poisson arrivals, n log-uniform 64..8192, 1-16
     # right-hand sides, 30% repeat-RHS on resident factors, FP16 factor + FP64
     # refinement, admission by a 120 GB HBM budget
-    "served_2000": dict(rate=2000.0, seconds=5.0, nmin=64, nmax=8192, kmax=16, repeat=0.3, seed=6, prec="fp16",
+    "served_2000": dict(rate=2000.0, seconds=60.0, nmin=64, nmax=8192, kmax=16, repeat=0.3, seed=6, prec="fp16",
                         budget_gb=120, slots=8, pool=48),
 }
 DEFAULT = "hpl_f64_n16384_nb256"
@@ -676,10 +676,35 @@ def run_ours(args, cfg, wname):
         del orr
         torch.cuda.empty_cache()
 
+    # arithmetic-rate probes of this GPU (the denominators of the CUDA-core
+    # kernels: the FP32 batched factor; the FP64 update keeps the rate derived
+    # from unit counts and clock, which it reaches, above the probe's)
+    rates = None
+    if not args.no_mixed and wname == DEFAULT:
+        rates = {"fp64_fma_tflops": lu.peak_probe(0), "fp64_mma_tflops": lu.peak_probe(1),
+                 "fp32_fma_tflops": lu.peak_probe(2),
+                 "how": "lu_peak_probe: register-only kernels on every SM, best of 3 timed launches of ~150 ms"}
+
     batched_line = None
     if not mixed and not args.no_mixed and wname == DEFAULT:
         batched_line = batched_measure(ctx, stream, WORKLOADS["batched_4096"], args.steps, args.warmup)
         launches += batched_line["launches"]
+        # the batched kernel: FP32 factor on the CUDA cores (plus FP64
+        # refinement); bound = the FP32 FMA pipe, measured by the probe above
+        fpk = rates["fp32_fma_tflops"]
+        batched_line["roofline"] = {"bound": "alu", "kernel": "batched_kernel", "achieved": batched_line["value"],
+                                    "peak": fpk, "unit": "TFLOP/s", "frac": batched_line["value"] / fpk,
+                                    "peak_source": "fp32_fma_tflops of lu_peak_probe (measured in this run)",
+                                    "traffic": None}
+        torch.cuda.empty_cache()
+
+    # the served configuration: Poisson arrivals at 2000/s for 60 s, and the
+    # same mix at a rate the server sustains (latencies that stay bounded)
+    served_line = None
+    if not mixed and not args.no_mixed and not args.no_served and wname == DEFAULT and ws == 1:
+        sc = WORKLOADS["served_2000"]
+        served_line = served_measure(sc, sc["rate"], args.served_seconds)
+        served_line["sustainable"] = served_measure(sc, args.served_low_rate, 20.0)
         torch.cuda.empty_cache()
 
     cpu = None
@@ -711,6 +736,8 @@ def run_ours(args, cfg, wname):
             "paper_nopiv": nopiv_line,
             "f64_ozaki": ozaki_line,
             "batched": batched_line,
+            "served": served_line,
+            "measured_rates": rates,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -736,6 +763,10 @@ def main():
     ap.add_argument("--rate", type=float, default=None, help="served: offered requests per second")
     ap.add_argument("--seconds", type=float, default=None, help="served: seconds of arrivals")
     ap.add_argument("--slots", type=int, default=None, help="served: worker slots of the server")
+    ap.add_argument("--no-served", action="store_true", help="skip the served companion of the default run")
+    ap.add_argument("--served-seconds", type=float, default=60.0, help="served companion: seconds of arrivals")
+    ap.add_argument("--served-low-rate", type=float, default=500.0,
+                    help="served companion: the lower offered rate reported beside 2000/s")
     args = ap.parse_args()
     cfg = WORKLOADS[args.workload]
     if args.workload.startswith("served"):
