@@ -350,8 +350,10 @@ def timed_solves(ctx, stream, cfg: dict, nb, steps: int, warmup: int, rank: int,
     n, prec, nrhs = cfg["n"], cfg["prec"], cfg["nrhs"]
     shift = cfg["shift"] * n
     mixed = prec != "f64"
-    A = I.hpl_matrix_torch(n, replica_seed(cfg["seed"], rank), diag_shift=shift, device="cuda")
-    B = I.hpl_rhs_torch(n, nrhs, replica_seed(cfg["seed"], rank), device="cuda")
+    # the seeded inputs, generated on the device (lu_generate: the same bits
+    # as inputs.hpl_matrix / hpl_rhs)
+    A = lu.generate(lu.colmajor_empty(n, n), replica_seed(cfg["seed"], rank), 0, shift)
+    B = lu.generate(lu.colmajor_empty(n, nrhs), replica_seed(cfg["seed"], rank), 1)
     X = lu.colmajor_empty(n, nrhs)
     torch.cuda.synchronize()
     iters = []

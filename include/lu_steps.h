@@ -91,6 +91,20 @@ int lu_step_gemm_ozaki(lu_ctx ctx, int m, int n, int k, double *dC, int ldc, con
  * usable.  Synchronizes.  Returns -1 (ctx NULL), -2 (kind not 0..2). */
 int lu_step_wait_probe(lu_ctx ctx, int kind);
 
+/* The seeded synthetic input of the benchmarks, generated on the device
+ * (HPL generates its input: arxiv 2202.13995, section "High Performance
+ * Linpack").  Fills the rows x cols column-major FP64 block dA (ld >= rows):
+ * element (i, j) is draw k = i + j * rows of stream stream_id of `seed` --
+ * SplitMix64 in counter mode, z = mix64(mix64(seed ^ stream_id *
+ * 0xD1B54A32D192ED03) + (k + 1) * 0x9E3779B97F4A7C15), value (z >> 11) *
+ * 2^-53 - 0.5, uniform in [-0.5, 0.5) -- plus diag_shift where i == j.
+ * Stream 0 with rows = cols = n is the matrix A of the workloads (shift 0 or
+ * n/4), stream 1 with rows = n, cols = nrhs their right-hand sides.  The same
+ * bits as the package's host generator.  Enqueued on cuda_stream (a
+ * cudaStream_t); returns -1..-4 for invalid arguments. */
+int lu_generate(double *dA, int rows, int cols, int ld, uint64_t seed, int stream_id, double diag_shift,
+                void *cuda_stream);
+
 /* Arithmetic-rate probe of the current device, for roofline denominators
  * (the paper has no counterpart): kind 0 = FP64 fused multiply-add on the
  * CUDA cores, 1 = FP64 warp matrix multiply-accumulate (mma.sync m8n8k4),

@@ -199,6 +199,10 @@ cudaError_t launch_residual(const double* A, int64_t lda, const double* X, int64
                             int64_t ldb, double* R, int64_t ldr, int n, int nrhs, double* partial, double* norms,
                             cudaStream_t st);
 // anorm[0] = ||A||_inf (max row sum of |A|).
+// Per-column max |r|, |x|, |b| (norms layout as launch_residual) of an R
+// formed by another kernel.
+cudaError_t launch_colmax3(const double* R, int64_t ldr, const double* X, int64_t ldx, const double* B, int64_t ldb,
+                           int n, int nrhs, double* norms, cudaStream_t st);
 cudaError_t launch_norm_inf(const double* A, int64_t lda, int n, double* partial, double* anorm, cudaStream_t st);
 // X[:, q] += D[:, q] for columns q with active[q] != 0.
 cudaError_t launch_add_update(double* X, int64_t ldx, const double* D, int64_t ldd, int n, int nrhs,

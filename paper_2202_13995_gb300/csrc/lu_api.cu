@@ -103,6 +103,7 @@ struct lu_ctx_s {
   // (the trailing update gets the rest)
   bool spec = true;
   int spec_sms = 24;
+  bool split_residual = true;  // the refinement's residual by the split product for >= 4 right-hand sides
 };
 
 enum { PH_PANEL = 0, PH_LASWP, PH_TRSM, PH_CAST, PH_GEMM, PH_SOLVE, PH_RESID, PH_OTHER, PH_N };
@@ -166,6 +167,8 @@ struct lu_fact_s {
   void* solve_mem = nullptr;
   SolveScratch ss{};
   double* vec_ws = nullptr;  // refinement: R, D, partial sums
+  void* res_ws = nullptr;    // refinement with >= 4 right-hand sides: split operands of the residual product
+  size_t res_ws_bytes = 0;
   size_t vec_ws_bytes = 0;
   int info = -1;             // cached host info (-1 = unknown)
 };
@@ -265,6 +268,7 @@ extern "C" int lu_create_ex(lu_ctx* out, void* cuda_stream, lu_alloc_fn alloc, l
   // the cluster panel kernel has no restore step for a failed check
   if (getenv("GB300LU_NO_SPEC") || getenv("GB300LU_PANEL_CLUSTER")) c->spec = false;
   if (const char* e = getenv("GB300LU_SPEC_SMS")) c->spec_sms = atoi(e);
+  if (getenv("GB300LU_RESIDUAL_DFMA")) c->split_residual = false;
   *out = c;
   return LU_OK;
 }
@@ -598,7 +602,7 @@ static int factor_loop_nopiv(lu_fact f) {
 extern "C" void lu_fact_free(lu_fact f) {
   if (!f) return;
   for (void* p : {f->W, (void*)f->ipiv, f->panel_mem, f->aop, f->oz_ws, (void*)f->oz_minv, (void*)f->spec_flag,
-                  f->spec_backup, f->uinv, f->solve_mem, f->ss.dinv, (void*)f->vec_ws})
+                  f->spec_backup, f->uinv, f->solve_mem, f->ss.dinv, (void*)f->vec_ws, f->res_ws})
     ffree(f, p);
   delete f;
 }
@@ -823,6 +827,41 @@ static int residual_chunk(lu_ctx c, int n, int nr, const double* dA, int64_t lda
   return LU_OK;
 }
 
+// The refinement's residual R = B - A X for a chunk of nr >= 4 right-hand
+// sides on the tensor cores: the product A X in FP64 accuracy by error-free
+// splitting (the split update's kernels, k = 256 columns of A at a time,
+// each chunk's product exact before its one FP64 subtraction), in the
+// transposed form R^T -= X^T A^T, so that both operands are read along their
+// contiguous columns.  The FP64 CUDA-core residual does 2 n^2 nr FMAs on
+// GB300's slow FP64 pipes; here that work goes to the BF16 tensor cores.
+static bool split_residual_applies(lu_fact f, int n, int nr) { return f->ctx->split_residual && nr >= 4 && n >= 1024; }
+
+static int residual_chunk_split(lu_fact f, int n, int nr, const double* dA, int64_t lda, const double* dX,
+                                int64_t ldx, const double* dB, int64_t ldb, double* dR, int64_t ldr) {
+  lu_ctx c = f->ctx;
+  cudaStream_t st = c->stream;
+  const size_t need = ozaki_ws_bytes(32, n, 256, c->dev.sm_count);
+  if (f->res_ws_bytes < need) {
+    ffree(f, f->res_ws);
+    f->res_ws = nullptr;
+    f->res_ws_bytes = 0;
+    int rc = falloc(f, &f->res_ws, need);
+    if (rc) return rc;
+    f->res_ws_bytes = need;
+  }
+  double* norms = c->d_small + 4;
+  CU_TRY(cudaMemcpy2DAsync(dR, (size_t)ldr * 8, dB, (size_t)ldb * 8, (size_t)n * 8, nr, cudaMemcpyDeviceToDevice, st));
+  for (int kc = 0; kc < n; kc += 256) {
+    const int k = (n - kc) < 256 ? (n - kc) : 256;
+    CU_TRY(PHASE(c, PH_RESID, 2, ozaki_split(dX + kc, ldx, dA + (int64_t)kc * lda, lda, nr, n, k, f->res_ws,
+                                             c->d_status, st)));
+    CU_TRY(PHASE(c, PH_RESID, 1, ozaki_gemm(dR, ldr, f->res_ws, nr, n, k, 0, n, c->d_status, c->dev, st)));
+  }
+  CU_TRY(PHASE(c, PH_RESID, 1, launch_colmax3(dR, ldr, dX, ldx, dB, ldb, n, nr, norms, st)));
+  CU_TRY(cudaMemcpyAsync(c->h_norms + 4, norms, (size_t)3 * nr * sizeof(double), cudaMemcpyDeviceToHost, st));
+  return LU_OK;
+}
+
 extern "C" int lu_refine(lu_fact f, const double* dA, int lda, const double* dB, int ldb, double* dX, int ldx,
                          int nrhs, double tol, int max_iter, int* iters, double* scaled_resid) {
   if (!f) return -1;
@@ -863,8 +902,12 @@ extern "C" int lu_refine(lu_fact f, const double* dA, int lda, const double* dB,
     int nactive = 0;
     for (int q0 = 0; q0 < nrhs; q0 += 32) {
       const int nr = (nrhs - q0) < 32 ? (nrhs - q0) : 32;
-      rc = residual_chunk(c, n, nr, dA, lda, dX + (int64_t)q0 * ldx, ldx, dB + (int64_t)q0 * ldb, ldb,
-                          R + (size_t)q0 * n, n, partial);
+      if (split_residual_applies(f, n, nr))
+        rc = residual_chunk_split(f, n, nr, dA, lda, dX + (int64_t)q0 * ldx, ldx, dB + (int64_t)q0 * ldb, ldb,
+                                  R + (size_t)q0 * n, n);
+      else
+        rc = residual_chunk(c, n, nr, dA, lda, dX + (int64_t)q0 * ldx, ldx, dB + (int64_t)q0 * ldb, ldb,
+                            R + (size_t)q0 * n, n, partial);
       if (rc) return rc;
       rc = read_status(c);  // synchronizes
       if (rc) return rc;
@@ -1107,6 +1150,7 @@ size_t gb_fact_bytes(int n, int nrhs, lu_prec prec, int nb, int sm_count) {
   if (prec == LU_BF16 || prec == LU_FP16) b += (size_t)2 * nn * round_up(nb, 64) * 2 + 1024;
   const int nr = nrhs > 32 ? 32 : (nrhs < 1 ? 1 : nrhs);
   b += 2 * (size_t)nn * nrhs * 8 + residual_partial_bytes(nn, nr) + 4096;
+  if (nrhs >= 4 && nn >= 1024) b += ozaki_ws_bytes(32, nn, 256, sm_count);  // the split residual
   return b;
 }
 

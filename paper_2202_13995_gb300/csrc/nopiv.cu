@@ -233,22 +233,30 @@ __global__ void __launch_bounds__(SL_THREADS) slab_lu_kernel(T* D, int64_t ld, i
       // (cj, r1) x the columns right of cj, a thread per column, eight rows at
       // a time with their loads ahead of the products; (b2) the rows below the
       // block x the block's columns right of cj, a thread per row
-      for (int k = cj + 1 + tid; k < wt; k += SL_THREADS) {
-        const T x = prow[k];
-        for (int r0 = cj + 1; r0 < r1; r0 += 8) {
-          T yv[8], lv[8];
+      // one list of items, spread evenly over the threads: the columns of
+      // (b1), then the rows of (b2) -- the same r1 - cj - 1 updates each
+      const int ncol1 = wt - cj - 1;
+      for (int it = tid; it < ncol1 + (hs - r1); it += SL_THREADS) {
+        if (it < ncol1) {
+          const int k = cj + 1 + it;
+          const T x = prow[k];
+          for (int r0 = cj + 1; r0 < r1; r0 += 8) {
+            T yv[8], lv[8];
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int r = r0 + u < r1 ? r0 + u : r1 - 1;
-            yv[u] = A[r * wp + k];
-            lv[u] = lcol[r];
+            for (int u = 0; u < 8; ++u) {
+              const int r = r0 + u < r1 ? r0 + u : r1 - 1;
+              yv[u] = A[r * wp + k];
+              lv[u] = lcol[r];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              if (r0 + u < r1) A[(r0 + u) * wp + k] = fma(-lv[u], x, yv[u]);
           }
-#pragma unroll
-          for (int u = 0; u < 8; ++u)
-            if (r0 + u < r1) A[(r0 + u) * wp + k] = fma(-lv[u], x, yv[u]);
+        } else {
+          const int r = r1 + it - ncol1;
+          axpy_batched<T>(A + r * wp, prow, -lcol[r], cj + 1, r1);
         }
       }
-      for (int r = r1 + tid; r < hs; r += SL_THREADS) axpy_batched<T>(A + r * wp, prow, -lcol[r], cj + 1, r1);
       __syncthreads();
     }
     // (ii) rank-bw update of rows [r1, hs) x columns [r1, wt): a thread per

@@ -564,6 +564,38 @@ cudaError_t launch_residual(const double* A, int64_t lda, const double* X, int64
   return cudaGetLastError();
 }
 
+// max |r|, max |x|, max |b| per column of R, X, B (n x nrhs, column-major)
+// into norms (layout as launch_residual), after R was formed elsewhere
+__global__ void colmax3_kernel(const double* __restrict__ R, int64_t ldr, const double* __restrict__ X, int64_t ldx,
+                               const double* __restrict__ B, int64_t ldb, int n, int nrhs, double* norms) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.y;
+  double rv = 0.0, xv = 0.0, bv = 0.0;
+  if (i < n) {
+    rv = fabs(R[(int64_t)q * ldr + i]);
+    xv = fabs(X[(int64_t)q * ldx + i]);
+    bv = fabs(B[(int64_t)q * ldb + i]);
+  }
+  rv = warp_max(rv);
+  xv = warp_max(xv);
+  bv = warp_max(bv);
+  if ((threadIdx.x & 31) == 0) {
+    atomic_max_nonneg(norms + q, rv);
+    atomic_max_nonneg(norms + nrhs + q, xv);
+    atomic_max_nonneg(norms + 2 * nrhs + q, bv);
+  }
+}
+
+cudaError_t launch_colmax3(const double* R, int64_t ldr, const double* X, int64_t ldx, const double* B, int64_t ldb,
+                           int n, int nrhs, double* norms, cudaStream_t st) {
+  if (n <= 0 || nrhs <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(norms, 0, (size_t)3 * nrhs * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  colmax3_kernel<<<dim3((unsigned)cdiv(n, 256), (unsigned)nrhs), 256, 0, st>>>(R, ldr, X, ldx, B, ldb, n, nrhs,
+                                                                               norms);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_norm_inf(const double* A, int64_t lda, int n, double* partial, double* anorm, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int ks = residual_splits(n);

@@ -30,7 +30,7 @@ EXPORTED = [
     "lu_create", "lu_destroy", "lu_strerror", "lu_factor", "lu_fact_info", "lu_fact_ipiv", "lu_fact_lu",
     "lu_solve", "lu_refine", "lu_scaled_residual", "lu_residual_norms", "lu_fact_free",
     "lu_step_panel", "lu_step_trsm", "lu_step_gemm", "lu_ctx_status", "lu_device_sm_count", "lu_build_tag",
-    "lu_create_ex", "lu_peak_probe", "lu_default_nb", "lu_profile_enable", "lu_profile_select", "lu_profile_read", "lu_launch_count", "lu_step_panel_static",
+    "lu_create_ex", "lu_peak_probe", "lu_default_nb", "lu_generate", "lu_profile_enable", "lu_profile_select", "lu_profile_read", "lu_launch_count", "lu_step_panel_static",
     "lu_batch_create", "lu_batch_run", "lu_batch_shape", "lu_batch_free", "lu_solve_batched",
     "lu_server_create", "lu_server_submit", "lu_server_poll", "lu_server_wait", "lu_server_stats",
     "lu_server_destroy", "lu_fact_bytes", "lu_factor_ex", "lu_step_gemm_ozaki", "lu_step_wait_probe",
@@ -85,6 +85,7 @@ def load():
             "lu_create_ex": (I, [PP, P, ALLOC_FN, FREE_FN, P]),
             "lu_peak_probe": (I, [I, DP]),
             "lu_default_nb": (I, [I, I, I]),
+            "lu_generate": (I, [P, I, I, I, C.c_uint64, I, D, P]),
             "lu_destroy": (None, [P]),
             "lu_strerror": (C.c_char_p, [I]),
             "lu_factor": (I, [P, I, P, I, I, I, PP, IP]),
@@ -162,6 +163,20 @@ def _rowmajor(t, name: str):
         raise ValueError(f"{name}: expected a row-major (m, n) tensor with strides (ld, 1)")
     ld = t.stride(0) if t.shape[0] > 1 else max(1, t.shape[1])
     return t.data_ptr(), max(1, ld)
+
+
+def generate(out, seed: int, stream_id: int = 0, diag_shift: float = 0.0, cuda_stream=None):
+    """Fill the column-major FP64 CUDA tensor `out` (rows x cols) with the
+    seeded draws of lu_generate (element (i, j) = draw i + j*rows of the
+    stream, + diag_shift on the diagonal): the device form of
+    inputs.hpl_matrix / hpl_rhs."""
+    import torch
+    ptr, ld, cols = _colmajor(out, "out")
+    rows = out.shape[0]
+    st = cuda_stream if cuda_stream is not None else torch.cuda.current_stream().cuda_stream
+    _check(load().lu_generate(C.c_void_p(ptr), rows, cols, ld, C.c_uint64(seed & ((1 << 64) - 1)), int(stream_id),
+                              float(diag_shift), C.c_void_p(st)), "lu_generate")
+    return out
 
 
 def default_nb(n: int, prec="f64", ozaki: bool = False) -> int:
