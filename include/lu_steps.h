@@ -61,7 +61,11 @@ int lu_step_panel_static(void *cuda_stream, lu_prec prec, int m, int w, void *dP
                          int *dStatus);
 
 /* Top-block update U12 = L11^-1 A12: dL (w x w row-major, only the strict
- * lower triangle is read; unit diagonal), dX (w x N row-major) overwritten. */
+ * lower triangle is read; unit diagonal), dX (w x N row-major) overwritten,
+ * 1 <= w <= 512.  LU_F64 and LU_F32: substitution in that precision.
+ * LU_BF16 / LU_FP16: the form the mixed-precision factorizations use -- FP32,
+ * with each 32 x 32 diagonal block of L11 inverted and applied as a product
+ * (the rounding of U12 differs from substitution; the factor is refined). */
 int lu_step_trsm(lu_ctx ctx, lu_prec prec, int w, int N, const void *dL, int ldl, void *dX, int ldx);
 
 /* Inner-block update C -= A B with C m x n, A m x k, B k x n, row-major.

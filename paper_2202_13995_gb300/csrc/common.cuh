@@ -187,6 +187,12 @@ __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(smem)), "l"(gmem), "n"(BYTES) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// close the copies issued so far into a group; wait until at most N groups are pending
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // ---- thread-block clusters: rank, peer shared-memory addresses, barrier
 __device__ __forceinline__ uint32_t cluster_rank() {

@@ -27,6 +27,7 @@
 
 #include <mutex>
 
+#include "cast16.cuh"
 #include "common.cuh"
 #include "kernels.h"
 #include "tc_ptx.cuh"
@@ -345,27 +346,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // ------------------------------------------------------------ operand casts
 // Aop[i*kpad + t] = L21(i, t), Bop[j*kpad + t] = U12(t, j), zero for t >= k.
 template <typename H>
-__device__ __forceinline__ H to16(float v);
-template <>
-__device__ __forceinline__ __nv_bfloat16 to16<__nv_bfloat16>(float v) {
-  return __float2bfloat16_rn(v);
-}
-template <>
-__device__ __forceinline__ __half to16<__half>(float v) {
-  return __float2half_rn(v);
-}
-template <typename H>
-__device__ __forceinline__ bool bad16(H h);
-template <>
-__device__ __forceinline__ bool bad16<__nv_bfloat16>(__nv_bfloat16 h) {
-  return (__bfloat16_as_ushort(h) & 0x7f80u) == 0x7f80u;
-}
-template <>
-__device__ __forceinline__ bool bad16<__half>(__half h) {
-  return (__half_as_ushort(h) & 0x7c00u) == 0x7c00u;
-}
-
-template <typename H>
 __global__ void cast_a_kernel(const float* __restrict__ L21, int64_t ld, int m, int k, H* __restrict__ Aop, int kpad,
                               int* status) {
   const int i = blockIdx.y;
@@ -418,15 +398,15 @@ cudaError_t launch_cast_operands(int kind, const float* L21, const float* U12, i
   return cudaGetLastError();
 }
 
-cudaError_t launch_cast_b(int kind, const float* U12, int64_t ldw, int n, int k, void* Bop, int kpad, int* status,
+cudaError_t launch_cast_a(int kind, const float* L21, int64_t ldw, int m, int k, void* Aop, int kpad, int* status,
                           cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  if ((kpad % 64) != 0 || k > kpad) return cudaErrorInvalidValue;
-  dim3 gb_((unsigned)cdiv(n, 32), (unsigned)cdiv(kpad, 32));
+  if (m <= 0) return cudaSuccess;
+  if (m > 65535 || (kpad % 64) != 0 || k > kpad) return cudaErrorInvalidValue;
+  dim3 ga((unsigned)cdiv(kpad, 256), (unsigned)m);
   if (kind == 1)
-    cast_b_kernel<__nv_bfloat16><<<gb_, dim3(32, 8), 0, st>>>(U12, ldw, n, k, (__nv_bfloat16*)Bop, kpad, status);
+    cast_a_kernel<__nv_bfloat16><<<ga, 256, 0, st>>>(L21, ldw, m, k, (__nv_bfloat16*)Aop, kpad, status);
   else
-    cast_b_kernel<__half><<<gb_, dim3(32, 8), 0, st>>>(U12, ldw, n, k, (__half*)Bop, kpad, status);
+    cast_a_kernel<__half><<<ga, 256, 0, st>>>(L21, ldw, m, k, (__half*)Aop, kpad, status);
   return cudaGetLastError();
 }
 

@@ -86,6 +86,17 @@ cudaError_t launch_laswp(T* W, int64_t ldw, int n, int k, int w, const int* perm
 template <typename T>
 cudaError_t launch_trsm_lower(const T* L11, T* A12, int64_t ldw, int w, int N, cudaStream_t st);
 
+// ---------------------------------------------------------------- trsm_inv.cu
+// The same top-block solve in FP32 for the mixed-precision factorizations, by
+// the inverses of L11's 32 x 32 diagonal blocks (each CTA inverts them, then
+// applies each block as a product and updates the rows below it), w <= 512.
+// With kind 1 (BF16) or 2 (FP16) it also writes the trailing update's B
+// operand of the solved columns, Bop[j * kpad + t] = U12(t, j) rounded (zero
+// for w <= t < kpad), and raises ST_RANGE in *status for a non-finite result,
+// as launch_cast_b does; kind 0 writes no operand.
+cudaError_t launch_trsm_inv(const float* L11, float* A12, int64_t ldw, int w, int N, int kind, void* Bop, int kpad,
+                            int* status, cudaStream_t st);
+
 // W (row-major T) <- A (column-major FP64), n x n.
 template <typename T>
 cudaError_t launch_to_working(const double* A, int64_t lda, T* W, int64_t ldw, int n, cudaStream_t st);
@@ -145,8 +156,8 @@ cudaError_t launch_gemm_simt(T* C, int64_t ldc, const T* A, int64_t lda, const T
 // kpad >= k is a multiple of 64 with zero fill.  Overflow or NaN sets ST_RANGE.
 cudaError_t launch_cast_operands(int kind, const float* L21, const float* U12, int64_t ldw, int m, int n, int k,
                                  void* Aop, void* Bop, int kpad, int* status, cudaStream_t st);
-// The B half of launch_cast_operands alone (columns of U12 into Bop).
-cudaError_t launch_cast_b(int kind, const float* U12, int64_t ldw, int n, int k, void* Bop, int kpad, int* status,
+// The A half of launch_cast_operands alone (rows of L21 into Aop).
+cudaError_t launch_cast_a(int kind, const float* L21, int64_t ldw, int m, int k, void* Aop, int kpad, int* status,
                           cudaStream_t st);
 // C (row-major FP32, m x n) -= Aop * Bop^T on tcgen05 (FP32 accumulate in TMEM).
 // max_ctas > 0 caps the persistent grid (to leave SMs to a concurrent kernel).

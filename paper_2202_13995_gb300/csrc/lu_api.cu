@@ -460,6 +460,10 @@ static int factor_loop(lu_fact f) {
     const bool split_top = tc && lookahead && rest > w2;
     if (f->ozaki) {
       CU_TRY(top_solve_split(f, (double*)Wkk, (double*)U12, ld, w, rest));
+    } else if (tc) {
+      // (the tensor-core form also writes the solved columns' B operand)
+      CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_inv((const float*)Wkk, (float*)U12, ld, w, split_top ? w2 : rest, kind,
+                                                   f->bop, f->kpad, c->d_status, st)));
     } else {
       CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12, ld, w, split_top ? w2 : rest, st)));
     }
@@ -474,9 +478,7 @@ static int factor_loop(lu_fact f) {
       CU_TRY(PHASE(c, PH_GEMM, 1, launch_gemm_simt<T>(A22, ld, L21, ld, U12, ld, rest, rest, w, st)));
       continue;
     }
-    CU_TRY(PHASE(c, PH_CAST, 2, launch_cast_operands(kind, (const float*)L21, (const float*)U12, ld, rest,
-                                                      split_top ? w2 : rest, w, f->aop, f->bop, f->kpad, c->d_status,
-                                                      st)));
+    CU_TRY(PHASE(c, PH_CAST, 1, launch_cast_a(kind, (const float*)L21, ld, rest, w, f->aop, f->kpad, c->d_status, st)));
     if (!split_top) {
       CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)A22, ld, f->aop, f->bop, rest, rest, f->kpad,
                                                c->d_status, c->dev, st)));
@@ -504,10 +506,9 @@ static int factor_loop(lu_fact f) {
     // the rest of the top block row, then the rest of the trailing matrix on
     // the SMs the panel leaves free (the latency-bound panel runs slower on
     // SMs it shares with the update)
-    const void* bop2 = (const char*)f->bop + (size_t)w2 * f->kpad * 2;
-    CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12 + w2, ld, w, rest - w2, st)));
-    CU_TRY(PHASE(c, PH_CAST, 1, launch_cast_b(kind, (const float*)(U12 + w2), ld, rest - w2, w, (void*)bop2, f->kpad,
-                                              c->d_status, st)));
+    void* bop2 = (char*)f->bop + (size_t)w2 * f->kpad * 2;
+    CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_inv((const float*)Wkk, (float*)(U12 + w2), ld, w, rest - w2, kind, bop2,
+                                                 f->kpad, c->d_status, st)));
     const int cap = c->dev.sm_count - (gp > 0 ? gp : 0);
     CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)(A22 + w2), ld, f->aop, bop2, rest, rest - w2, f->kpad,
                                              c->d_status, c->dev, st, cap > 8 ? cap : 8)));
@@ -559,6 +560,9 @@ static int factor_loop_nopiv(lu_fact f) {
     const bool split_top = tc && lookahead && rest > w2;  // as in factor_loop
     if (f->ozaki) {
       CU_TRY(top_solve_split(f, (double*)Wkk, (double*)U12, ld, w, rest));
+    } else if (tc) {
+      CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_inv((const float*)Wkk, (float*)U12, ld, w, split_top ? w2 : rest, kind,
+                                                   f->bop, f->kpad, c->d_status, st)));
     } else {
       CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12, ld, w, split_top ? w2 : rest, st)));
     }
@@ -568,9 +572,8 @@ static int factor_loop_nopiv(lu_fact f) {
       CU_TRY(PHASE(c, PH_GEMM, 1, ozaki_gemm((double*)A22, ld, f->oz_ws, rest, rest, w, 0, rest, c->d_status, c->dev,
                                               st)));
     } else if (tc) {
-      CU_TRY(PHASE(c, PH_CAST, 2, launch_cast_operands(kind, (const float*)L21, (const float*)U12, ld, rest,
-                                                        split_top ? w2 : rest, w, f->aop, f->bop, f->kpad,
-                                                        c->d_status, st)));
+      CU_TRY(PHASE(c, PH_CAST, 1, launch_cast_a(kind, (const float*)L21, ld, rest, w, f->aop, f->kpad, c->d_status,
+                                                st)));
       if (!split_top) {
         CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)A22, ld, f->aop, f->bop, rest, rest, f->kpad,
                                                  c->d_status, c->dev, st)));
@@ -584,10 +587,9 @@ static int factor_loop_nopiv(lu_fact f) {
       CU_TRY(nopiv_panel<T>(f, A22, rest, w2, k + w, c->side));
       CU_TRY(cudaEventRecord(c->ev_panel, c->side));
       panel_ready = true;
-      const void* bop2 = (const char*)f->bop + (size_t)w2 * f->kpad * 2;
-      CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_lower<T>(Wkk, U12 + w2, ld, w, rest - w2, st)));
-      CU_TRY(PHASE(c, PH_CAST, 1, launch_cast_b(kind, (const float*)(U12 + w2), ld, rest - w2, w, (void*)bop2,
-                                                f->kpad, c->d_status, st)));
+      void* bop2 = (char*)f->bop + (size_t)w2 * f->kpad * 2;
+      CU_TRY(PHASE(c, PH_TRSM, 1, launch_trsm_inv((const float*)Wkk, (float*)(U12 + w2), ld, w, rest - w2, kind,
+                                                   bop2, f->kpad, c->d_status, st)));
       const int cap = c->dev.sm_count - keep;
       CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)(A22 + w2), ld, f->aop, bop2, rest, rest - w2, f->kpad,
                                                c->d_status, c->dev, st, cap > 8 ? cap : 8)));
@@ -1053,8 +1055,10 @@ extern "C" int lu_step_trsm(lu_ctx c, lu_prec prec, int w, int N, const void* dL
   if (ldl != ldx) return -6;  // the kernel shares one row stride
   if (prec == LU_F64)
     CU_TRY(launch_trsm_lower<double>((const double*)dL, (double*)dX, ldx, w, N, c->stream));
-  else
+  else if (prec == LU_F32)
     CU_TRY(launch_trsm_lower<float>((const float*)dL, (float*)dX, ldx, w, N, c->stream));
+  else
+    CU_TRY(launch_trsm_inv((const float*)dL, (float*)dX, ldx, w, N, 0, nullptr, 0, nullptr, c->stream));
   return LU_OK;
 }
 

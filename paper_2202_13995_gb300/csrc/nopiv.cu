@@ -303,6 +303,230 @@ __global__ void __launch_bounds__(SL_THREADS) slab_lu_kernel(T* D, int64_t ld, i
   }
 }
 
+// ============================================================ slab LU in registers (FP32)
+// The factorization of slab_lu_kernel for FP32 slabs of up to 128 rows and
+// 32 * NG columns, with the slab held in registers instead of shared memory
+// (where each rank-1 update costs three loads and a store per product).
+// Lane l of warp w owns rows 4 l .. 4 l + 3 and, for g < NG, the column
+// block w + 8 g (columns 4 (w + 8 g) .. + 3).  Per column block J (its
+// columns j = 4 J .. 4 J + 3 are all owned by warp J % 8):
+//   A. the owning warp factors the block's four columns over all rows, in its
+//      registers: the pivot comes from lane J (which owns row j), each row
+//      below j is divided by it (as in the definition), and the block's
+//      remaining columns take the rank-1 update; the multipliers are
+//      published;
+//   B. after one barrier, every warp finishes its column blocks right of J:
+//      the block's four rows by forward substitution with the block's unit
+//      lower 4 x 4 (a lane per column, through shared memory), then the
+//      rows below the block by a rank-4 update in registers.
+// Blocks left of J are final and are skipped (a warp-uniform test).  The
+// loop over blocks stays rolled, so the body fits the instruction cache; the
+// place of a block's columns in the owner's registers is chosen with
+// selects once per block.  Spec and info semantics are those of
+// slab_lu_kernel.
+constexpr int SR_THREADS = 256;
+
+template <int NG>
+__global__ void __launch_bounds__(SR_THREADS, 1) slab_reg_kernel(float* D, int64_t ld, int hs, int wt, int kabs,
+                                                                 int* info, SpecDev<float> sp, int first, int tag,
+                                                                 int restore_rows) {
+  constexpr int NC = 4 * NG;      // columns per thread
+  constexpr int NGJ = NG < 4 ? NG : 4;  // groups that can hold a pivot column (j < 128)
+  __shared__ __align__(16) float lbs[2][4][128];  // multipliers of block J: [J & 1][jj][row]
+  __shared__ __align__(16) float ur[8][4][NC];    // per warp: the block's four rows of the warp's columns
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool spec = sp.flag != nullptr;
+  if (spec) {
+    const int f0 = __ldcg(sp.flag), f3 = __ldcg(sp.flag + 3);
+    if (f0 != 0 || f3 != 0) {
+      if (tid == 0 && f0 == 0) sp.flag[0] = 1;  // a failure of the rows below an earlier slab
+      return;
+    }
+  }
+  float a[4][NC];
+  const bool vec = ((reinterpret_cast<uintptr_t>(D) & 15) == 0) && (ld % 4) == 0;
+#pragma unroll
+  for (int ii = 0; ii < 4; ++ii) {
+    const int r = 4 * lane + ii;
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      const int c0 = 4 * (warp + 8 * g);
+      if (vec && r < hs && c0 + 4 <= wt) {
+        const float4 x = *reinterpret_cast<const float4*>(D + (int64_t)r * ld + c0);
+        a[ii][4 * g + 0] = x.x;
+        a[ii][4 * g + 1] = x.y;
+        a[ii][4 * g + 2] = x.z;
+        a[ii][4 * g + 3] = x.w;
+      } else {
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq)
+          a[ii][4 * g + qq] = (r < hs && c0 + qq < wt) ? D[(int64_t)r * ld + c0 + qq] : 0.0f;
+      }
+    }
+  }
+  if (spec && first) {
+#pragma unroll
+    for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+      for (int g = 0; g < NG; ++g)
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          const int r = 4 * lane + ii, c = 4 * (warp + 8 * g) + qq;
+          if (r < hs && c < wt) sp.backup[(int64_t)r * wt + c] = a[ii][4 * g + qq];
+        }
+    for (int j = tid; j < wt; j += SR_THREADS) sp.ipiv[kabs + j] = kabs + j + 1;
+    if (tid == 0) sp.perm[0] = 0;
+  }
+  bool bad = false;
+  for (int J = 0; 4 * J < hs; ++J) {
+    const int wj = J & 7, gj = J >> 3;
+    float(*lb)[128] = lbs[J & 1];
+    // A. the owning warp factors the block's columns
+    if (warp == wj) {
+      float blk[4][4];
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          blk[ii][qq] = a[ii][qq];
+#pragma unroll
+          for (int g = 1; g < NGJ; ++g)
+            if (g == gj) blk[ii][qq] = a[ii][4 * g + qq];
+        }
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const int j = 4 * J + jj;
+        float l[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (j < hs) {
+          const float piv = __shfl_sync(0xffffffffu, blk[jj][jj], J);
+          const bool pz = !(piv != 0.0f);
+          if (lane == 0) {
+            if (spec) {
+              if (!finite_nonzero(piv)) bad = true;
+            } else if (pz) {
+              atomicMin(info, kabs + j + 1);
+            }
+          }
+#pragma unroll
+          for (int ii = 0; ii < 4; ++ii) {
+            const int r = 4 * lane + ii;
+            if (r > j && r < hs) {
+              l[ii] = pz ? blk[ii][jj] : blk[ii][jj] / piv;
+              if (spec && !spec_ok_mult(l[ii])) bad = true;
+              blk[ii][jj] = l[ii];
+            }
+          }
+#pragma unroll
+          for (int qq = jj + 1; qq < 4; ++qq) {
+            const float u = __shfl_sync(0xffffffffu, blk[jj][qq], J);
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii) blk[ii][qq] = fmaf(-l[ii], u, blk[ii][qq]);
+          }
+        }
+        *reinterpret_cast<float4*>(&lb[jj][4 * lane]) = make_float4(l[0], l[1], l[2], l[3]);
+      }
+#pragma unroll
+      for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+          if (gj == 0) a[ii][qq] = blk[ii][qq];
+#pragma unroll
+          for (int g = 1; g < NGJ; ++g)
+            if (g == gj) a[ii][4 * g + qq] = blk[ii][qq];
+        }
+    }
+    __syncthreads();
+    // B. this warp's column blocks right of J
+    if (warp + 8 * (NG - 1) > J) {
+      float(*u)[NC] = ur[warp];
+      if (lane == J) {
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+          for (int g = 0; g < NG; ++g)
+            *reinterpret_cast<float4*>(&u[ii][4 * g]) =
+                make_float4(a[ii][4 * g + 0], a[ii][4 * g + 1], a[ii][4 * g + 2], a[ii][4 * g + 3]);
+      }
+      __syncwarp();
+      if (lane < NC && warp + 8 * (lane >> 2) > J) {  // lane = one of the warp's columns
+        const float* lj = &lb[0][0];
+        const float l10 = lj[0 * 128 + 4 * J + 1], l20 = lj[0 * 128 + 4 * J + 2], l30 = lj[0 * 128 + 4 * J + 3];
+        const float l21 = lj[1 * 128 + 4 * J + 2], l31 = lj[1 * 128 + 4 * J + 3], l32 = lj[2 * 128 + 4 * J + 3];
+        const float u0 = u[0][lane];
+        const float u1 = fmaf(-l10, u0, u[1][lane]);
+        const float u2 = fmaf(-l21, u1, fmaf(-l20, u0, u[2][lane]));
+        const float u3 = fmaf(-l32, u2, fmaf(-l31, u1, fmaf(-l30, u0, u[3][lane])));
+        u[1][lane] = u1;
+        u[2][lane] = u2;
+        u[3][lane] = u3;
+      }
+      __syncwarp();
+      float lv[4][4];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const float4 x = *reinterpret_cast<const float4*>(&lb[jj][4 * lane]);
+        lv[0][jj] = x.x;
+        lv[1][jj] = x.y;
+        lv[2][jj] = x.z;
+        lv[3][jj] = x.w;
+      }
+      const bool own_rows = lane == J;  // the block's rows: substituted above, not updated here
+#pragma unroll
+      for (int g = 0; g < NG; ++g) {
+        if (warp + 8 * g > J) {
+          float uv[4][4];
+#pragma unroll
+          for (int jj = 0; jj < 4; ++jj) {
+            const float4 x = *reinterpret_cast<const float4*>(&u[jj][4 * g]);
+            uv[jj][0] = x.x;
+            uv[jj][1] = x.y;
+            uv[jj][2] = x.z;
+            uv[jj][3] = x.w;
+          }
+          if (own_rows) {
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+              for (int qq = 0; qq < 4; ++qq) a[ii][4 * g + qq] = uv[ii][qq];
+          } else {
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+              for (int qq = 0; qq < 4; ++qq) {
+                float v = a[ii][4 * g + qq];
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) v = fmaf(-lv[ii][jj], uv[jj][qq], v);
+                a[ii][4 * g + qq] = v;
+              }
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int ii = 0; ii < 4; ++ii) {
+    const int r = 4 * lane + ii;
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      const int c0 = 4 * (warp + 8 * g);
+      if (vec && r < hs && c0 + 4 <= wt) {
+        *reinterpret_cast<float4*>(D + (int64_t)r * ld + c0) =
+            make_float4(a[ii][4 * g + 0], a[ii][4 * g + 1], a[ii][4 * g + 2], a[ii][4 * g + 3]);
+      } else {
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq)
+          if (r < hs && c0 + qq < wt) D[(int64_t)r * ld + c0 + qq] = a[ii][4 * g + qq];
+      }
+    }
+  }
+  if (spec && __syncthreads_or(bad) && tid == 0) {
+    sp.flag[1] = tag;
+    sp.flag[2] = restore_rows;
+    __threadfence();
+    sp.flag[0] = 1;
+  }
+}
+
 // ============================================================ inverses of U's diagonal blocks
 // The inverse of each 32 x 32 diagonal block of a factored slab's U (for the
 // rows below the slab): a CTA per block, a thread per column of the inverse,
@@ -313,9 +537,15 @@ __global__ void __launch_bounds__(32) uinv_kernel(const T* __restrict__ D, int64
   __shared__ T Us[32][33];
   __shared__ T Z[32][33];
   const int lane = threadIdx.x, c0 = blockIdx.x * 32, bw = min(32, hs - c0);
-  for (int t = 0; t < 32; ++t) {
-    Us[t][lane] = (t < bw && lane < bw) ? D[(int64_t)(c0 + t) * ld + c0 + lane] : T(0);
-    Z[t][lane] = (t == lane) ? T(1) : T(0);
+  {
+    T v[32];  // all 32 loads in flight together
+#pragma unroll
+    for (int t = 0; t < 32; ++t) v[t] = (t < bw && lane < bw) ? D[(int64_t)(c0 + t) * ld + c0 + lane] : T(0);
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      Us[t][lane] = v[t];
+      Z[t][lane] = (t == lane) ? T(1) : T(0);
+    }
   }
   __syncwarp();
   for (int t = bw - 1; t >= 0; --t) {
@@ -535,15 +765,49 @@ static cudaError_t launch_below(const T* U, const T* uinv, T* X, int64_t ld, int
   return cudaErrorInvalidValue;
 }
 
+// One slab: FP32 slabs of up to 128 x 256 in registers (unless
+// GB300LU_SLAB_SMEM is set), the rest in shared memory.
+template <typename T>
+static cudaError_t launch_slab(T* D, int64_t ld, int hs, int wt, int kabs, int* info, const SpecDev<T>& sp,
+                               int first, int tag, int restore, cudaStream_t st) {
+  auto kern = slab_lu_kernel<T>;
+  cudaError_t e = allow_max_smem((const void*)kern);
+  if (e != cudaSuccess) return e;
+  const size_t smem = ((size_t)hs * (wt | 1) + hs) * sizeof(T);
+  kern<<<1, SL_THREADS, smem, st>>>(D, ld, hs, wt, kabs, info, sp, first, tag, restore);
+  return cudaGetLastError();
+}
+
+static bool slab_in_registers() {
+  static const bool off = std::getenv("GB300LU_SLAB_SMEM") != nullptr;
+  return !off;
+}
+
+template <>
+cudaError_t launch_slab<float>(float* D, int64_t ld, int hs, int wt, int kabs, int* info, const SpecDev<float>& sp,
+                               int first, int tag, int restore, cudaStream_t st) {
+  if (hs <= 128 && wt <= 256 && slab_in_registers()) {
+    if (wt <= 128)
+      slab_reg_kernel<4><<<1, SR_THREADS, 0, st>>>(D, ld, hs, wt, kabs, info, sp, first, tag, restore);
+    else
+      slab_reg_kernel<8><<<1, SR_THREADS, 0, st>>>(D, ld, hs, wt, kabs, info, sp, first, tag, restore);
+    return cudaGetLastError();
+  }
+  auto kern = slab_lu_kernel<float>;
+  cudaError_t e = allow_max_smem((const void*)kern);
+  if (e != cudaSuccess) return e;
+  const size_t smem = ((size_t)hs * (wt | 1) + hs) * sizeof(float);
+  kern<<<1, SL_THREADS, smem, st>>>(D, ld, hs, wt, kabs, info, sp, first, tag, restore);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_block_column(T* P, int64_t ld, int m, int w, int kabs, int* info, T* uinv, cudaStream_t st,
                                 const SpecArgs& spec) {
   if (w <= 0) return cudaSuccess;
   if (m < w) return cudaErrorInvalidValue;
   const int h = slab_rows(w, sizeof(T));
-  auto kern = slab_lu_kernel<T>;
-  cudaError_t e = allow_max_smem((const void*)kern);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
   const int tag = kabs + 1;
   for (int s0 = 0; s0 < w; s0 += h) {
     const int hs = (w - s0) < h ? (w - s0) : h;
@@ -553,9 +817,9 @@ cudaError_t launch_block_column(T* P, int64_t ld, int m, int w, int kabs, int* i
     // a failed check of the first slab changed only its rows; any later
     // failure, every row of the block column
     const int restore = first ? hs : m;
-    const size_t smem = ((size_t)hs * (wt | 1) + hs) * sizeof(T);
-    kern<<<1, SL_THREADS, smem, st>>>(D, ld, hs, wt, kabs + s0, info, spec_dev<T>(spec, 0), first, tag, restore);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launch_slab<T>(D, ld, hs, wt, kabs + s0, info, spec_dev<T>(spec, 0), first, tag, restore, st)) !=
+        cudaSuccess)
+      return e;
     const int below = m - s0 - hs;
     T* ui = uinv + (size_t)(s0 / 32) * 1024;  // the slab's diagonal blocks' inverses
     if (below > 0) {

@@ -28,11 +28,6 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 
 // Shared memory of one triangular-solve CTA: a ring of STAGES matrix blocks
 // (64 x 64, rows contiguous) with the matching solution blocks, plus the
@@ -182,10 +177,10 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
 #pragma unroll 1
   for (int it = 0; it < count; ++it) {
     issue(it + STAGES - 1);
-    cp_async_wait<STAGES - 1>();
+    cp_async_wait_group<STAGES - 1>();
     __syncthreads();
     if (!sm.flag) {
-      cp_async_wait<0>();
+      cp_async_wait_group<0>();
       return;
     }
     const int st = it % STAGES;
@@ -204,7 +199,7 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
     }
     __syncthreads();
   }
-  cp_async_wait<0>();
+  cp_async_wait_group<0>();
   // row sums: a fixed butterfly over the lanes (deterministic)
 #pragma unroll
   for (int rr = 0; rr < 8; ++rr)

@@ -119,8 +119,9 @@ def test_panel_zero_pivot(ctx):
     assert np.allclose(Pd.cpu().numpy(), LUo, rtol=0, atol=1e-12)
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
-@pytest.mark.parametrize("w,N", [(1, 1), (32, 31), (64, 257), (100, 40), (256, 1000)])
+@pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("w,N", [(1, 1), (32, 31), (64, 257), (100, 40), (256, 1000), (384, 70), (512, 100),
+                                 (257, 33)])
 def test_trsm(ctx, prec, w, N):
     import torch
     rng = np.random.default_rng(w * 7 + N)
@@ -130,6 +131,7 @@ def test_trsm(ctx, prec, w, N):
     ldb = max(w, N)  # the kernel shares one row stride: embed both in w x ldb buffers
     Lbuf = np.zeros((w, ldb)); Lbuf[:, :w] = Lm
     Xbuf = np.zeros((w, ldb)); Xbuf[:, :N] = X
+    # bf16: the mixed factorizations' form (FP32 arithmetic, inverted diagonal blocks)
     dt = torch.float64 if prec == "f64" else torch.float32
     Ld, Xd = _rm(Lbuf, dt), _rm(Xbuf, dt)
     ctx.step_trsm(Ld[:, :w], Xd[:, :N], prec)
