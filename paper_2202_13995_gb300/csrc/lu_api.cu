@@ -102,7 +102,7 @@ struct lu_ctx_s {
   // diagonal-pivot check of FP32 panels, and the SMs its lookahead panels keep
   // (the trailing update gets the rest)
   bool spec = true;
-  int spec_sms = 24;
+  int spec_sms = 32;
   bool split_residual = true;  // the refinement's residual by the split product for >= 4 right-hand sides
 };
 

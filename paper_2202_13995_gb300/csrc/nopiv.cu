@@ -17,8 +17,6 @@
 // block column's remaining columns, a CTA per 64 rows.  The next slab starts
 // h rows and h columns further down.  The same two kernels serve the
 // diagonal-pivot check of a pivoted panel (SpecArgs in kernels.h).
-#include <cstdlib>
-
 #include "common.cuh"
 #include "kernels.h"
 
@@ -71,6 +69,17 @@ template <>
 __device__ __forceinline__ void v16_get<double>(const double2& v, double* o) {
   o[0] = v.x;
   o[1] = v.y;
+}
+
+template <typename T>
+__device__ __forceinline__ typename V16<T>::type v16_make(const T* e);
+template <>
+__device__ __forceinline__ float4 v16_make<float>(const float* e) {
+  return make_float4(e[0], e[1], e[2], e[3]);
+}
+template <>
+__device__ __forceinline__ double2 v16_make<double>(const double* e) {
+  return make_double2(e[0], e[1]);
 }
 
 // Rows [0, nrows) x columns [0, ncol) of G (row-major, ld) into S (row
@@ -132,26 +141,6 @@ __device__ __forceinline__ void load_rows(const T* G, int64_t ld, int nrows, int
   }
 }
 
-// y[k] += a * x[k] for k in [k0, k1), shared-memory vectors: eight loads of
-// each issued before their products and stores, so that the stores (which
-// might alias later loads, as far as the compiler knows) do not serialize
-// the loop on the load latency.
-template <typename T>
-__device__ __forceinline__ void axpy_batched(T* y, const T* x, T a, int k0, int k1) {
-  for (int k = k0; k < k1; k += 8) {
-    T yv[8], xv[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int kk = k + u < k1 ? k + u : k1 - 1;
-      yv[u] = y[kk];
-      xv[u] = x[kk];
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (k + u < k1) y[k + u] = fma(a, xv[u], yv[u]);
-  }
-}
-
 // ============================================================ slab LU
 // One CTA factors the slab D (hs rows x wt columns, row-major, ld) in shared
 // memory: the LU of its hs x hs diagonal block without pivoting, blocked by 32
@@ -159,9 +148,10 @@ __device__ __forceinline__ void axpy_batched(T* y, const T* x, T a, int k0, int 
 // 32 columns:
 //   (i)  the block's columns, one at a time: the multipliers of the column (a
 //        thread per row, dividing by the pivot as in the definition), then a
-//        rank-1 update of the block's rows across the whole slab width (which
-//        leaves U's rows right of the block final) and of the rows below the
-//        block within the block's columns; two barriers per column;
+//        rank-1 update of the rows below it within the block's columns (a
+//        thread per row); two barriers per column;
+//   (i') the block's rows right of the block (U's rows there) by forward
+//        substitution with the block's L, a thread per column;
 //   (ii) a rank-32 update of the rows below the block and the columns right
 //        of it (register tiles).
 // The loops stay rolled, with their shared-memory loads batched ahead of the
@@ -177,11 +167,27 @@ __device__ __forceinline__ void axpy_batched(T* y, const T* x, T a, int k0, int 
 // panel failed.
 constexpr int SL_THREADS = 256;
 
+// Row stride of the slab in shared memory, in elements: at least the width
+// and whole 32-column blocks, and VN (mod 2 VN) for VN elements per 16 bytes,
+// so that each thread's 16-byte piece of its own row falls in banks of its
+// own within a quarter-warp.
+__host__ __device__ inline int slab_wp(int hs, int wt, int tsize) {
+  const int vn = 16 / tsize;
+  const int w = wt > ((hs + 31) & ~31) ? wt : ((hs + 31) & ~31);
+  return (w + 2 * vn - 1) / (2 * vn) * (2 * vn) + vn;
+}
+// shared memory of one slab: rows, the pivot row's block columns, the multipliers
+inline size_t slab_smem_bytes(int hs, int wt, int tsize) {
+  return ((size_t)hs * slab_wp(hs, wt, tsize) + 32 + (size_t)hs) * tsize;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(SL_THREADS) slab_lu_kernel(T* D, int64_t ld, int hs, int wt, int kabs, int* info,
                                                              SpecDev<T> sp, int first, int tag, int restore_rows) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int wp = wt | 1;  // odd row stride: a row per thread is free of bank conflicts
+  constexpr int VN = V16<T>::n;
+  using VT = typename V16<T>::type;
+  const int wp = slab_wp(hs, wt, sizeof(T));
   T* A = reinterpret_cast<T*>(smem_raw);  // [hs][wp]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const bool spec = sp.flag != nullptr;
@@ -199,16 +205,17 @@ __global__ void __launch_bounds__(SL_THREADS) slab_lu_kernel(T* D, int64_t ld, i
     if (tid == 0) sp.perm[0] = 0;
   }
   __syncthreads();
-  T* lcol = A + (size_t)hs * wp;  // [hs]: the current column's multipliers
+  T* pr = A + (size_t)hs * wp;  // [32]: the pivot row's block columns right of the pivot, zero elsewhere
+  T* lcol = pr + 32;            // [hs]: the current column's multipliers
   for (int c0 = 0; c0 < hs; c0 += 32) {
     const int bw = min(32, hs - c0);
     const int r1 = c0 + bw;
     // (i) the block's columns, one at a time.  Column cj: (a) a thread per
-    //     row below the pivot divides by the pivot (as in the definition);
-    //     (b) all threads apply the rank-1 update to the block's rows right of
-    //     cj (so U's rows right of the block come out final: the forward
-    //     substitution with the block's L) and to the rows below the block
-    //     within the block's columns.
+    //     row below the pivot divides by the pivot (as in the definition),
+    //     and the last warp copies the pivot row's block columns right of cj;
+    //     (b) a thread per row below cj applies the rank-1 update to its
+    //     row's 32 block columns in 16-byte pieces (the copy's zeros leave
+    //     the columns at and left of cj as they are).
     for (int j = 0; j < bw; ++j) {
       const int cj = c0 + j;
       const T piv = A[cj * wp + cj];
@@ -227,38 +234,49 @@ __global__ void __launch_bounds__(SL_THREADS) slab_lu_kernel(T* D, int64_t ld, i
         A[r * wp + cj] = l;
         lcol[r] = l;
       }
+      if (warp == SL_THREADS / 32 - 1) {  // (never a row thread: a slab has at most 128 rows)
+        const int k = c0 + lane;
+        pr[lane] = (k > cj && k < r1) ? A[cj * wp + k] : T(0);
+      }
       __syncthreads();
-      const T* prow = A + cj * wp;
-      // the rank-1 update of an L-shaped region: (b1) the block's rows
-      // (cj, r1) x the columns right of cj, a thread per column, eight rows at
-      // a time with their loads ahead of the products; (b2) the rows below the
-      // block x the block's columns right of cj, a thread per row
-      // one list of items, spread evenly over the threads: the columns of
-      // (b1), then the rows of (b2) -- the same r1 - cj - 1 updates each
-      const int ncol1 = wt - cj - 1;
-      for (int it = tid; it < ncol1 + (hs - r1); it += SL_THREADS) {
-        if (it < ncol1) {
-          const int k = cj + 1 + it;
-          const T x = prow[k];
-          for (int r0 = cj + 1; r0 < r1; r0 += 8) {
-            T yv[8], lv[8];
+      for (int r = cj + 1 + tid; r < hs; r += SL_THREADS) {
+        const T nl = -lcol[r];
+        VT* y = reinterpret_cast<VT*>(A + r * wp + c0);
+        const VT* x = reinterpret_cast<const VT*>(pr);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              const int r = r0 + u < r1 ? r0 + u : r1 - 1;
-              yv[u] = A[r * wp + k];
-              lv[u] = lcol[r];
-            }
+        for (int v = 0; v < 32 / VN; ++v) {
+          T yv[VN], xv[VN];
+          v16_get<T>(y[v], yv);
+          v16_get<T>(x[v], xv);
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-              if (r0 + u < r1) A[(r0 + u) * wp + k] = fma(-lv[u], x, yv[u]);
-          }
-        } else {
-          const int r = r1 + it - ncol1;
-          axpy_batched<T>(A + r * wp, prow, -lcol[r], cj + 1, r1);
+          for (int e = 0; e < VN; ++e) yv[e] = fma(nl, xv[e], yv[e]);
+          y[v] = v16_make<T>(yv);
         }
       }
       __syncthreads();
     }
+    // (i') the block's rows right of the block: forward substitution with the
+    //      block's unit lower L, a thread per column -- the same products in
+    //      the same order as rank-1 updates column by column would apply them
+    for (int k = r1 + tid; k < wt; k += SL_THREADS) {
+      for (int t = c0 + 1; t < r1; ++t) {
+        T v = A[t * wp + k];
+        for (int s0 = c0; s0 < t; s0 += 8) {
+          T lv[8], xv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int ss = s0 + u < t ? s0 + u : t - 1;
+            lv[u] = A[t * wp + ss];
+            xv[u] = A[ss * wp + k];
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (s0 + u < t) v = fma(-lv[u], xv[u], v);
+        }
+        A[t * wp + k] = v;
+      }
+    }
+    __syncthreads();
     // (ii) rank-bw update of rows [r1, hs) x columns [r1, wt): a thread per
     //       4 rows x 4 columns 32 apart (the warp reads consecutive columns)
     const int nr = hs - r1, nc = wt - r1;
@@ -295,230 +313,6 @@ __global__ void __launch_bounds__(SL_THREADS) slab_lu_kernel(T* D, int64_t ld, i
   }
   for (int r = warp; r < hs; r += SL_THREADS / 32)
     for (int c = lane; c < wt; c += 32) D[(int64_t)r * ld + c] = A[r * wp + c];
-  if (spec && __syncthreads_or(bad) && tid == 0) {
-    sp.flag[1] = tag;
-    sp.flag[2] = restore_rows;
-    __threadfence();
-    sp.flag[0] = 1;
-  }
-}
-
-// ============================================================ slab LU in registers (FP32)
-// The factorization of slab_lu_kernel for FP32 slabs of up to 128 rows and
-// 32 * NG columns, with the slab held in registers instead of shared memory
-// (where each rank-1 update costs three loads and a store per product).
-// Lane l of warp w owns rows 4 l .. 4 l + 3 and, for g < NG, the column
-// block w + 8 g (columns 4 (w + 8 g) .. + 3).  Per column block J (its
-// columns j = 4 J .. 4 J + 3 are all owned by warp J % 8):
-//   A. the owning warp factors the block's four columns over all rows, in its
-//      registers: the pivot comes from lane J (which owns row j), each row
-//      below j is divided by it (as in the definition), and the block's
-//      remaining columns take the rank-1 update; the multipliers are
-//      published;
-//   B. after one barrier, every warp finishes its column blocks right of J:
-//      the block's four rows by forward substitution with the block's unit
-//      lower 4 x 4 (a lane per column, through shared memory), then the
-//      rows below the block by a rank-4 update in registers.
-// Blocks left of J are final and are skipped (a warp-uniform test).  The
-// loop over blocks stays rolled, so the body fits the instruction cache; the
-// place of a block's columns in the owner's registers is chosen with
-// selects once per block.  Spec and info semantics are those of
-// slab_lu_kernel.
-constexpr int SR_THREADS = 256;
-
-template <int NG>
-__global__ void __launch_bounds__(SR_THREADS, 1) slab_reg_kernel(float* D, int64_t ld, int hs, int wt, int kabs,
-                                                                 int* info, SpecDev<float> sp, int first, int tag,
-                                                                 int restore_rows) {
-  constexpr int NC = 4 * NG;      // columns per thread
-  constexpr int NGJ = NG < 4 ? NG : 4;  // groups that can hold a pivot column (j < 128)
-  __shared__ __align__(16) float lbs[2][4][128];  // multipliers of block J: [J & 1][jj][row]
-  __shared__ __align__(16) float ur[8][4][NC];    // per warp: the block's four rows of the warp's columns
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const bool spec = sp.flag != nullptr;
-  if (spec) {
-    const int f0 = __ldcg(sp.flag), f3 = __ldcg(sp.flag + 3);
-    if (f0 != 0 || f3 != 0) {
-      if (tid == 0 && f0 == 0) sp.flag[0] = 1;  // a failure of the rows below an earlier slab
-      return;
-    }
-  }
-  float a[4][NC];
-  const bool vec = ((reinterpret_cast<uintptr_t>(D) & 15) == 0) && (ld % 4) == 0;
-#pragma unroll
-  for (int ii = 0; ii < 4; ++ii) {
-    const int r = 4 * lane + ii;
-#pragma unroll
-    for (int g = 0; g < NG; ++g) {
-      const int c0 = 4 * (warp + 8 * g);
-      if (vec && r < hs && c0 + 4 <= wt) {
-        const float4 x = *reinterpret_cast<const float4*>(D + (int64_t)r * ld + c0);
-        a[ii][4 * g + 0] = x.x;
-        a[ii][4 * g + 1] = x.y;
-        a[ii][4 * g + 2] = x.z;
-        a[ii][4 * g + 3] = x.w;
-      } else {
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq)
-          a[ii][4 * g + qq] = (r < hs && c0 + qq < wt) ? D[(int64_t)r * ld + c0 + qq] : 0.0f;
-      }
-    }
-  }
-  if (spec && first) {
-#pragma unroll
-    for (int ii = 0; ii < 4; ++ii)
-#pragma unroll
-      for (int g = 0; g < NG; ++g)
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq) {
-          const int r = 4 * lane + ii, c = 4 * (warp + 8 * g) + qq;
-          if (r < hs && c < wt) sp.backup[(int64_t)r * wt + c] = a[ii][4 * g + qq];
-        }
-    for (int j = tid; j < wt; j += SR_THREADS) sp.ipiv[kabs + j] = kabs + j + 1;
-    if (tid == 0) sp.perm[0] = 0;
-  }
-  bool bad = false;
-  for (int J = 0; 4 * J < hs; ++J) {
-    const int wj = J & 7, gj = J >> 3;
-    float(*lb)[128] = lbs[J & 1];
-    // A. the owning warp factors the block's columns
-    if (warp == wj) {
-      float blk[4][4];
-#pragma unroll
-      for (int ii = 0; ii < 4; ++ii)
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq) {
-          blk[ii][qq] = a[ii][qq];
-#pragma unroll
-          for (int g = 1; g < NGJ; ++g)
-            if (g == gj) blk[ii][qq] = a[ii][4 * g + qq];
-        }
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        const int j = 4 * J + jj;
-        float l[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (j < hs) {
-          const float piv = __shfl_sync(0xffffffffu, blk[jj][jj], J);
-          const bool pz = !(piv != 0.0f);
-          if (lane == 0) {
-            if (spec) {
-              if (!finite_nonzero(piv)) bad = true;
-            } else if (pz) {
-              atomicMin(info, kabs + j + 1);
-            }
-          }
-#pragma unroll
-          for (int ii = 0; ii < 4; ++ii) {
-            const int r = 4 * lane + ii;
-            if (r > j && r < hs) {
-              l[ii] = pz ? blk[ii][jj] : blk[ii][jj] / piv;
-              if (spec && !spec_ok_mult(l[ii])) bad = true;
-              blk[ii][jj] = l[ii];
-            }
-          }
-#pragma unroll
-          for (int qq = jj + 1; qq < 4; ++qq) {
-            const float u = __shfl_sync(0xffffffffu, blk[jj][qq], J);
-#pragma unroll
-            for (int ii = 0; ii < 4; ++ii) blk[ii][qq] = fmaf(-l[ii], u, blk[ii][qq]);
-          }
-        }
-        *reinterpret_cast<float4*>(&lb[jj][4 * lane]) = make_float4(l[0], l[1], l[2], l[3]);
-      }
-#pragma unroll
-      for (int ii = 0; ii < 4; ++ii)
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq) {
-          if (gj == 0) a[ii][qq] = blk[ii][qq];
-#pragma unroll
-          for (int g = 1; g < NGJ; ++g)
-            if (g == gj) a[ii][4 * g + qq] = blk[ii][qq];
-        }
-    }
-    __syncthreads();
-    // B. this warp's column blocks right of J
-    if (warp + 8 * (NG - 1) > J) {
-      float(*u)[NC] = ur[warp];
-      if (lane == J) {
-#pragma unroll
-        for (int ii = 0; ii < 4; ++ii)
-#pragma unroll
-          for (int g = 0; g < NG; ++g)
-            *reinterpret_cast<float4*>(&u[ii][4 * g]) =
-                make_float4(a[ii][4 * g + 0], a[ii][4 * g + 1], a[ii][4 * g + 2], a[ii][4 * g + 3]);
-      }
-      __syncwarp();
-      if (lane < NC && warp + 8 * (lane >> 2) > J) {  // lane = one of the warp's columns
-        const float* lj = &lb[0][0];
-        const float l10 = lj[0 * 128 + 4 * J + 1], l20 = lj[0 * 128 + 4 * J + 2], l30 = lj[0 * 128 + 4 * J + 3];
-        const float l21 = lj[1 * 128 + 4 * J + 2], l31 = lj[1 * 128 + 4 * J + 3], l32 = lj[2 * 128 + 4 * J + 3];
-        const float u0 = u[0][lane];
-        const float u1 = fmaf(-l10, u0, u[1][lane]);
-        const float u2 = fmaf(-l21, u1, fmaf(-l20, u0, u[2][lane]));
-        const float u3 = fmaf(-l32, u2, fmaf(-l31, u1, fmaf(-l30, u0, u[3][lane])));
-        u[1][lane] = u1;
-        u[2][lane] = u2;
-        u[3][lane] = u3;
-      }
-      __syncwarp();
-      float lv[4][4];
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
-        const float4 x = *reinterpret_cast<const float4*>(&lb[jj][4 * lane]);
-        lv[0][jj] = x.x;
-        lv[1][jj] = x.y;
-        lv[2][jj] = x.z;
-        lv[3][jj] = x.w;
-      }
-      const bool own_rows = lane == J;  // the block's rows: substituted above, not updated here
-#pragma unroll
-      for (int g = 0; g < NG; ++g) {
-        if (warp + 8 * g > J) {
-          float uv[4][4];
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            const float4 x = *reinterpret_cast<const float4*>(&u[jj][4 * g]);
-            uv[jj][0] = x.x;
-            uv[jj][1] = x.y;
-            uv[jj][2] = x.z;
-            uv[jj][3] = x.w;
-          }
-          if (own_rows) {
-#pragma unroll
-            for (int ii = 0; ii < 4; ++ii)
-#pragma unroll
-              for (int qq = 0; qq < 4; ++qq) a[ii][4 * g + qq] = uv[ii][qq];
-          } else {
-#pragma unroll
-            for (int ii = 0; ii < 4; ++ii)
-#pragma unroll
-              for (int qq = 0; qq < 4; ++qq) {
-                float v = a[ii][4 * g + qq];
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) v = fmaf(-lv[ii][jj], uv[jj][qq], v);
-                a[ii][4 * g + qq] = v;
-              }
-          }
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int ii = 0; ii < 4; ++ii) {
-    const int r = 4 * lane + ii;
-#pragma unroll
-    for (int g = 0; g < NG; ++g) {
-      const int c0 = 4 * (warp + 8 * g);
-      if (vec && r < hs && c0 + 4 <= wt) {
-        *reinterpret_cast<float4*>(D + (int64_t)r * ld + c0) =
-            make_float4(a[ii][4 * g + 0], a[ii][4 * g + 1], a[ii][4 * g + 2], a[ii][4 * g + 3]);
-      } else {
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq)
-          if (r < hs && c0 + qq < wt) D[(int64_t)r * ld + c0 + qq] = a[ii][4 * g + qq];
-      }
-    }
-  }
   if (spec && __syncthreads_or(bad) && tid == 0) {
     sp.flag[1] = tag;
     sp.flag[2] = restore_rows;
@@ -727,12 +521,11 @@ static int device_smem_optin() {
   return optin;
 }
 
-// Slab height: the largest multiple of 32, at most 128, whose rows fit in
+// Slab height: the largest multiple of 32, at most 128, whose slab fits in
 // 136 KB of shared memory.
 static int slab_rows(int w, int tsize) {
-  const size_t row = (size_t)(w | 1) * tsize;
   int h = 128;
-  while (h > 32 && (size_t)h * row > 136 * 1024) h -= 32;
+  while (h > 32 && slab_smem_bytes(h, w, tsize) > 136 * 1024) h -= 32;
   return h;
 }
 
@@ -765,39 +558,14 @@ static cudaError_t launch_below(const T* U, const T* uinv, T* X, int64_t ld, int
   return cudaErrorInvalidValue;
 }
 
-// One slab: FP32 slabs of up to 128 x 256 in registers (unless
-// GB300LU_SLAB_SMEM is set), the rest in shared memory.
+// One slab: a CTA with the slab in shared memory.
 template <typename T>
 static cudaError_t launch_slab(T* D, int64_t ld, int hs, int wt, int kabs, int* info, const SpecDev<T>& sp,
                                int first, int tag, int restore, cudaStream_t st) {
   auto kern = slab_lu_kernel<T>;
   cudaError_t e = allow_max_smem((const void*)kern);
   if (e != cudaSuccess) return e;
-  const size_t smem = ((size_t)hs * (wt | 1) + hs) * sizeof(T);
-  kern<<<1, SL_THREADS, smem, st>>>(D, ld, hs, wt, kabs, info, sp, first, tag, restore);
-  return cudaGetLastError();
-}
-
-static bool slab_in_registers() {
-  static const bool off = std::getenv("GB300LU_SLAB_SMEM") != nullptr;
-  return !off;
-}
-
-template <>
-cudaError_t launch_slab<float>(float* D, int64_t ld, int hs, int wt, int kabs, int* info, const SpecDev<float>& sp,
-                               int first, int tag, int restore, cudaStream_t st) {
-  if (hs <= 128 && wt <= 256 && slab_in_registers()) {
-    if (wt <= 128)
-      slab_reg_kernel<4><<<1, SR_THREADS, 0, st>>>(D, ld, hs, wt, kabs, info, sp, first, tag, restore);
-    else
-      slab_reg_kernel<8><<<1, SR_THREADS, 0, st>>>(D, ld, hs, wt, kabs, info, sp, first, tag, restore);
-    return cudaGetLastError();
-  }
-  auto kern = slab_lu_kernel<float>;
-  cudaError_t e = allow_max_smem((const void*)kern);
-  if (e != cudaSuccess) return e;
-  const size_t smem = ((size_t)hs * (wt | 1) + hs) * sizeof(float);
-  kern<<<1, SL_THREADS, smem, st>>>(D, ld, hs, wt, kabs, info, sp, first, tag, restore);
+  kern<<<1, SL_THREADS, slab_smem_bytes(hs, wt, sizeof(T)), st>>>(D, ld, hs, wt, kabs, info, sp, first, tag, restore);
   return cudaGetLastError();
 }
 

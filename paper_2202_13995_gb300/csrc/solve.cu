@@ -18,7 +18,7 @@
 namespace gb {
 
 constexpr int TS_BS = 64;
-constexpr int TS_NRMAX = 8;  // right-hand sides per launch
+constexpr int TS_NRMAX = 16;  // right-hand sides per launch: 16 for FP32 factors, 8 for FP64
 
 // Leading dimension of the solution workspaces: a multiple of 16 elements, so
 // that every 16-byte chunk of a solution block starts 16-byte aligned.
@@ -107,10 +107,12 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
     }
   }
   // this block's right-hand side: thread (row tid & 63) holds columns
-  // q = (tid >> 6) + 4 u, u = 0, 1
-  T rhs[2] = {T(0), T(0)};
+  // q = (tid >> 6) + 4 u
+  constexpr int NU = (NR + 3) / 4;
+  T rhs[NU];
 #pragma unroll
-  for (int u = 0; u < 2; ++u) {
+  for (int u = 0; u < NU; ++u) {
+    rhs[u] = T(0);
     const int r = tid & 63, q = (tid >> 6) + 4 * u;
     if (q < NR && r < rows && q < nrhs) {
       if (LOWER)
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
   }
   __syncthreads();
 #pragma unroll
-  for (int u = 0; u < 2; ++u) {
+  for (int u = 0; u < NU; ++u) {
     const int r = tid & 63, q = (tid >> 6) + 4 * u;
     if (q < NR) sm.v[q][r] = (r < rows && q < nrhs) ? rhs[u] - sm.v[q][r] : T(0);
   }
@@ -385,7 +387,9 @@ cudaError_t launch_trinv(const T* W, int64_t ldw, int n, T* Dinv, cudaStream_t s
 template cudaError_t launch_trinv<float>(const float*, int64_t, int, float*, cudaStream_t);
 template cudaError_t launch_trinv<double>(const double*, int64_t, int, double*, cudaStream_t);
 
-// One launch pair per chunk of <= 8 right-hand sides (callers pass <= 32).
+// One launch pair per chunk of right-hand sides -- up to 16 with FP32
+// factors, 8 with FP64 (whose accumulators take twice the registers); the
+// chain of diagonal blocks is walked once per chunk (callers pass <= 32).
 template <typename T>
 cudaError_t launch_lu_solve(const T* W, int64_t ldw, const int* rowid, int n, int nrhs, const double* B,
                             int64_t ldb, double* X, int64_t ldx, const SolveScratch& s, int* status,
@@ -393,8 +397,10 @@ cudaError_t launch_lu_solve(const T* W, int64_t ldw, const int* rowid, int n, in
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
   if (nrhs > 32) return cudaErrorInvalidValue;
   if (((uintptr_t)W & 15u) || (ldw % (16 / sizeof(T))) != 0) return cudaErrorInvalidValue;
-  for (int q0 = 0; q0 < nrhs; q0 += TS_NRMAX) {
-    const int nr = (nrhs - q0) < TS_NRMAX ? (nrhs - q0) : TS_NRMAX;
+  constexpr int CHUNK = sizeof(T) == 4 ? 16 : 8;
+  static_assert(CHUNK <= TS_NRMAX, "solution workspace holds a chunk");
+  for (int q0 = 0; q0 < nrhs; q0 += CHUNK) {
+    const int nr = (nrhs - q0) < CHUNK ? (nrhs - q0) : CHUNK;
     const double* Bq = B + (int64_t)q0 * ldb;
     double* Xq = X + (int64_t)q0 * ldx;
     cudaError_t e;
@@ -406,8 +412,10 @@ cudaError_t launch_lu_solve(const T* W, int64_t ldw, const int* rowid, int n, in
         e = run_solve<T, 2, true>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
       else if (nr <= 4)
         e = run_solve<T, 4, true>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
-      else
+      else if (nr <= 8)
         e = run_solve<T, 8, true>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
+      else
+        e = run_solve<T, sizeof(T) == 4 ? 16 : 8, true>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
     } else {
       if (nr == 1)
         e = run_solve<T, 1, false>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
@@ -415,8 +423,10 @@ cudaError_t launch_lu_solve(const T* W, int64_t ldw, const int* rowid, int n, in
         e = run_solve<T, 2, false>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
       else if (nr <= 4)
         e = run_solve<T, 4, false>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
-      else
+      else if (nr <= 8)
         e = run_solve<T, 8, false>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
+      else
+        e = run_solve<T, sizeof(T) == 4 ? 16 : 8, false>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
     }
     if (e != cudaSuccess) return e;
   }
