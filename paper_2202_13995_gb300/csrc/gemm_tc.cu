@@ -398,10 +398,54 @@ cudaError_t launch_cast_operands(int kind, const float* L21, const float* U12, i
   return cudaGetLastError();
 }
 
+// The A operand alone, eight elements per thread: two 16-byte loads of L21
+// and one 16-byte store of the operand (L21's rows 16-byte aligned, k a
+// multiple of 8; launch_cast_a checks and otherwise uses cast_a_kernel).
+template <typename H>
+__global__ void cast_a8_kernel(const float* __restrict__ L21, int64_t ld, int m, int k, H* __restrict__ Aop, int kpad,
+                               int* status) {
+  const int per_row = kpad / 8;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool bad = false;
+  if (e < (int64_t)m * per_row) {
+    const int i = (int)(e / per_row), t = (int)(e % per_row) * 8;
+    float v[8];
+    if (t < k) {
+      const float4 x0 = *reinterpret_cast<const float4*>(L21 + (int64_t)i * ld + t);
+      const float4 x1 = *reinterpret_cast<const float4*>(L21 + (int64_t)i * ld + t + 4);
+      v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+      v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = 0.0f;
+    }
+    unsigned w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const H lo = to16<H>(v[2 * u]), hi = to16<H>(v[2 * u + 1]);
+      bad |= bad16<H>(lo) || bad16<H>(hi);
+      w[u] = (unsigned)bits16<H>(lo) | ((unsigned)bits16<H>(hi) << 16);
+    }
+    *reinterpret_cast<uint4*>(Aop + (int64_t)i * kpad + t) = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_RANGE);
+}
+
 cudaError_t launch_cast_a(int kind, const float* L21, int64_t ldw, int m, int k, void* Aop, int kpad, int* status,
                           cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
-  if (m > 65535 || (kpad % 64) != 0 || k > kpad) return cudaErrorInvalidValue;
+  if ((kpad % 64) != 0 || k > kpad) return cudaErrorInvalidValue;
+  const bool vec = (k % 8) == 0 && ((uintptr_t)L21 & 15u) == 0 && (ldw % 4) == 0 && ((uintptr_t)Aop & 15u) == 0;
+  if (vec) {
+    const int64_t items = (int64_t)m * (kpad / 8);
+    const unsigned grid = (unsigned)cdiv(items, 256);
+    if (kind == 1)
+      cast_a8_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(L21, ldw, m, k, (__nv_bfloat16*)Aop, kpad, status);
+    else
+      cast_a8_kernel<__half><<<grid, 256, 0, st>>>(L21, ldw, m, k, (__half*)Aop, kpad, status);
+    return cudaGetLastError();
+  }
+  if (m > 65535) return cudaErrorInvalidValue;
   dim3 ga((unsigned)cdiv(kpad, 256), (unsigned)m);
   if (kind == 1)
     cast_a_kernel<__nv_bfloat16><<<ga, 256, 0, st>>>(L21, ldw, m, k, (__nv_bfloat16*)Aop, kpad, status);

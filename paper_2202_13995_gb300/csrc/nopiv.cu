@@ -154,6 +154,8 @@ __device__ __forceinline__ void load_rows(const T* G, int64_t ld, int nrows, int
 //        substitution with the block's L, a thread per column;
 //   (ii) a rank-32 update of the rows below the block and the columns right
 //        of it (register tiles).
+// Then, for the rows below the slab, (iii) the inverses of U's 32 x 32
+// diagonal blocks (a warp per block), written to uinv.
 // The loops stay rolled, with their shared-memory loads batched ahead of the
 // products: the kernel runs once per launch on one SM, where a long
 // straight-line body would be fetched from L2 at every block.
@@ -176,14 +178,16 @@ __host__ __device__ inline int slab_wp(int hs, int wt, int tsize) {
   const int w = wt > ((hs + 31) & ~31) ? wt : ((hs + 31) & ~31);
   return (w + 2 * vn - 1) / (2 * vn) * (2 * vn) + vn;
 }
-// shared memory of one slab: rows, the pivot row's block columns, the multipliers
+// shared memory of one slab: rows, the pivot row's block columns, the
+// multipliers, and a 32 x 33 scratch per diagonal block for its U's inverse
 inline size_t slab_smem_bytes(int hs, int wt, int tsize) {
-  return ((size_t)hs * slab_wp(hs, wt, tsize) + 32 + (size_t)hs) * tsize;
+  return ((size_t)hs * slab_wp(hs, wt, tsize) + 32 + (size_t)hs + (size_t)((hs + 31) / 32) * 32 * 33) * tsize;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(SL_THREADS) slab_lu_kernel(T* D, int64_t ld, int hs, int wt, int kabs, int* info,
-                                                             SpecDev<T> sp, int first, int tag, int restore_rows) {
+                                                             SpecDev<T> sp, int first, int tag, int restore_rows,
+                                                             T* uinv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int VN = V16<T>::n;
   using VT = typename V16<T>::type;
@@ -313,54 +317,45 @@ __global__ void __launch_bounds__(SL_THREADS) slab_lu_kernel(T* D, int64_t ld, i
   }
   for (int r = warp; r < hs; r += SL_THREADS / 32)
     for (int c = lane; c < wt; c += 32) D[(int64_t)r * ld + c] = A[r * wp + c];
+  // (iii) for the rows below the slab: the inverse of each 32 x 32 diagonal
+  //       block of U, a warp per block, a lane per column of the inverse:
+  //       back substitution with the division by U's diagonal; uinv[b]
+  //       (32 x 32, row-major), the identity outside a ragged last block
+  if (uinv != nullptr) {
+    T* Zs = lcol + hs;
+    for (int b = warp; 32 * b < hs; b += SL_THREADS / 32) {
+      const int c0 = 32 * b, bw = min(32, hs - c0);
+      T* Z = Zs + (size_t)b * 32 * 33;  // [32][33]
+      const T* Ub = A + (size_t)c0 * wp + c0;
+      for (int t = 0; t < 32; ++t) Z[t * 33 + lane] = (t == lane) ? T(1) : T(0);
+      __syncwarp();
+      for (int t = bw - 1; t >= 0; --t) {
+        const T zt = Z[t * 33 + lane] / Ub[t * wp + t];
+        Z[t * 33 + lane] = zt;
+        for (int q0 = 0; q0 < t; q0 += 8) {
+          T uq[8], zq[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int q = q0 + u < t ? q0 + u : t - 1;
+            uq[u] = Ub[q * wp + t];
+            zq[u] = Z[q * 33 + lane];
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (q0 + u < t) Z[(q0 + u) * 33 + lane] = zq[u] - uq[u] * zt;
+        }
+        __syncwarp();
+      }
+      T* ub = uinv + (size_t)b * 1024;
+      for (int t = 0; t < 32; ++t) ub[t * 32 + lane] = Z[t * 33 + lane];
+    }
+  }
   if (spec && __syncthreads_or(bad) && tid == 0) {
     sp.flag[1] = tag;
     sp.flag[2] = restore_rows;
     __threadfence();
     sp.flag[0] = 1;
   }
-}
-
-// ============================================================ inverses of U's diagonal blocks
-// The inverse of each 32 x 32 diagonal block of a factored slab's U (for the
-// rows below the slab): a CTA per block, a thread per column of the inverse,
-// column-oriented back substitution with the division by U's diagonal;
-// uinv[b] (32 x 32, row-major) for the slab's block b.
-template <typename T>
-__global__ void __launch_bounds__(32) uinv_kernel(const T* __restrict__ D, int64_t ld, int hs, T* uinv) {
-  __shared__ T Us[32][33];
-  __shared__ T Z[32][33];
-  const int lane = threadIdx.x, c0 = blockIdx.x * 32, bw = min(32, hs - c0);
-  {
-    T v[32];  // all 32 loads in flight together
-#pragma unroll
-    for (int t = 0; t < 32; ++t) v[t] = (t < bw && lane < bw) ? D[(int64_t)(c0 + t) * ld + c0 + lane] : T(0);
-#pragma unroll
-    for (int t = 0; t < 32; ++t) {
-      Us[t][lane] = v[t];
-      Z[t][lane] = (t == lane) ? T(1) : T(0);
-    }
-  }
-  __syncwarp();
-  for (int t = bw - 1; t >= 0; --t) {
-    const T zt = Z[t][lane] / Us[t][t];
-    Z[t][lane] = zt;
-    for (int q0 = 0; q0 < t; q0 += 8) {
-      T uq[8], zq[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int q = q0 + u < t ? q0 + u : t - 1;
-        uq[u] = Us[q][t];
-        zq[u] = Z[q][lane];
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (q0 + u < t) Z[q0 + u][lane] = zq[u] - uq[u] * zt;
-    }
-    __syncwarp();
-  }
-  T* ub = uinv + (size_t)blockIdx.x * 1024;
-  for (int t = 0; t < 32; ++t) ub[t * 32 + lane] = Z[t][lane];
 }
 
 // ============================================================ rows below a slab
@@ -374,7 +369,8 @@ __global__ void __launch_bounds__(32) uinv_kernel(const T* __restrict__ D, int64
 //      inverse of U's 32 x 32 diagonal block, which the slab kernel wrote to
 //      uinv (32 x 32 per block, row-major);
 //   3. the columns to the right: a rank-32 update, each thread a register
-//      tile of RB/16 rows x 4 columns per 64-column chunk.
+//      tile of RB/16 rows x 4 columns per 64-column chunk, its rows' values
+//      of the block read from a transposed copy (one 16-byte load per k).
 // With sp.flag set it is a stage of the diagonal-pivot check: for the first
 // slab (first != 0) the rows are saved to sp.backup first and the stage runs
 // unless flag[0] is set; a later stage returns on flag[0] or flag[3].  A
@@ -395,6 +391,7 @@ __global__ void __launch_bounds__(LS_THREADS) below_solve_kernel(const T* __rest
   T* Us = reinterpret_cast<T*>(smem_raw);  // [32][wu]: rows c0 .. c0 + 31 of U, columns c0 .. wt
   T* Ui = Us + 32 * wu;                    // [32][32]: the inverse of U's current 32 x 32 diagonal block
   T* Xs = Ui + 32 * 32;                    // [RB][wx]
+  T* XT = Xs + RB * wx;                    // [32][RB]: the solved block, transposed (16-byte aligned)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int r0 = blockIdx.x * RB;
   const int rows = min(RB, m - r0);
@@ -466,6 +463,11 @@ __global__ void __launch_bounds__(LS_THREADS) below_solve_kernel(const T* __rest
       }
     }
     __syncthreads();
+    for (int e = tid; e < 32 * RB; e += LS_THREADS) {
+      const int k = e / RB, r = e % RB;
+      XT[k * RB + r] = k < bw ? Xs[r * wx + c0 + k] : T(0);
+    }
+    __syncthreads();
     const int c1 = c0 + bw;  // columns [c1, wt) remain
     const int rg = tid >> 4, cg = tid & 15;
     for (int cc = c1 + 4 * cg; cc < wt; cc += 64) {
@@ -483,8 +485,13 @@ __global__ void __launch_bounds__(LS_THREADS) below_solve_kernel(const T* __rest
         const T* up = &Us[k * wu + cc];
         v16_get<T>(*reinterpret_cast<const VT*>(up), ub);
         if (VN == 2) v16_get<T>(*reinterpret_cast<const VT*>(up + 2), ub + 2);
+        if constexpr (RT % VN == 0) {
 #pragma unroll
-        for (int i = 0; i < RT; ++i) xa[i] = Xs[(RT * rg + i) * wx + c0 + k];
+          for (int i = 0; i < RT; i += VN) v16_get<T>(*reinterpret_cast<const VT*>(&XT[k * RB + RT * rg + i]), xa + i);
+        } else {
+#pragma unroll
+          for (int i = 0; i < RT; ++i) xa[i] = XT[k * RB + RT * rg + i];
+        }
 #pragma unroll
         for (int i = 0; i < RT; ++i)
 #pragma unroll
@@ -522,16 +529,16 @@ static int device_smem_optin() {
 }
 
 // Slab height: the largest multiple of 32, at most 128, whose slab fits in
-// 136 KB of shared memory.
+// 168 KB of shared memory.
 static int slab_rows(int w, int tsize) {
   int h = 128;
-  while (h > 32 && slab_smem_bytes(h, w, tsize) > 136 * 1024) h -= 32;
+  while (h > 32 && slab_smem_bytes(h, w, tsize) > 168 * 1024) h -= 32;
   return h;
 }
 
 static size_t ls_smem(int rb, int wt, int tsize) {
   const size_t wu = (size_t)((wt + 3) & ~3);
-  return (32 * wu + 32 * 32 + (size_t)rb * (wt | 1)) * tsize;
+  return (32 * wu + 32 * 32 + (size_t)rb * (wt | 1) + 32 * (size_t)rb) * tsize;
 }
 
 template <typename T, int RB>
@@ -561,11 +568,12 @@ static cudaError_t launch_below(const T* U, const T* uinv, T* X, int64_t ld, int
 // One slab: a CTA with the slab in shared memory.
 template <typename T>
 static cudaError_t launch_slab(T* D, int64_t ld, int hs, int wt, int kabs, int* info, const SpecDev<T>& sp,
-                               int first, int tag, int restore, cudaStream_t st) {
+                               int first, int tag, int restore, T* uinv, cudaStream_t st) {
   auto kern = slab_lu_kernel<T>;
   cudaError_t e = allow_max_smem((const void*)kern);
   if (e != cudaSuccess) return e;
-  kern<<<1, SL_THREADS, slab_smem_bytes(hs, wt, sizeof(T)), st>>>(D, ld, hs, wt, kabs, info, sp, first, tag, restore);
+  kern<<<1, SL_THREADS, slab_smem_bytes(hs, wt, sizeof(T)), st>>>(D, ld, hs, wt, kabs, info, sp, first, tag, restore,
+                                                                   uinv);
   return cudaGetLastError();
 }
 
@@ -585,14 +593,12 @@ cudaError_t launch_block_column(T* P, int64_t ld, int m, int w, int kabs, int* i
     // a failed check of the first slab changed only its rows; any later
     // failure, every row of the block column
     const int restore = first ? hs : m;
-    if ((e = launch_slab<T>(D, ld, hs, wt, kabs + s0, info, spec_dev<T>(spec, 0), first, tag, restore, st)) !=
-        cudaSuccess)
-      return e;
     const int below = m - s0 - hs;
-    T* ui = uinv + (size_t)(s0 / 32) * 1024;  // the slab's diagonal blocks' inverses
+    T* ui = uinv + (size_t)(s0 / 32) * 1024;  // the slab's diagonal blocks' inverses (for the rows below)
+    if ((e = launch_slab<T>(D, ld, hs, wt, kabs + s0, info, spec_dev<T>(spec, 0), first, tag, restore,
+                            below > 0 ? ui : nullptr, st)) != cudaSuccess)
+      return e;
     if (below > 0) {
-      uinv_kernel<T><<<(hs + 31) / 32, 32, 0, st>>>(D, ld, hs, ui);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
       // the first slab's rows below it follow its rows in the backup (row stride w)
       e = launch_below<T>(D, ui, D + (int64_t)hs * ld, ld, below, hs, wt, spec_dev<T>(spec, (int64_t)hs * w), first,
                           tag, st);
@@ -608,7 +614,7 @@ int block_column_launches(int m, int w, int tsize) {
   int n = 0;
   for (int s0 = 0; s0 < w; s0 += h) {
     const int hs = (w - s0) < h ? (w - s0) : h;
-    n += (m - s0 - hs) > 0 ? 3 : 1;
+    n += (m - s0 - hs) > 0 ? 2 : 1;
   }
   return n;
 }

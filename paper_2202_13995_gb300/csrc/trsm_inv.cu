@@ -9,7 +9,8 @@
 //   X_b <- inv(L_bb) X_b,  then  X_r <- X_r - L_rb X_b for the rows r below,
 // with the rows of L below the block staged in shared memory one block ahead
 // (cp.async).  The CTA holds a strip of 32 columns of A12 in shared memory
-// throughout; each thread of the update keeps a 4 x 8 tile in registers.
+// throughout (8 for a short solve); each thread of the update keeps a 4 x 8
+// tile in registers (1 x 8 with 8 columns).
 //
 // Multiplying by the inverted diagonal block instead of substituting changes
 // only the rounding of U12; the mixed-precision factor is refined in FP64
@@ -24,7 +25,6 @@
 
 namespace gb {
 
-constexpr int TI_NS = 32;       // columns of A12 per CTA
 constexpr int TI_THREADS = 256;
 constexpr int TI_LDS = 33;      // row stride of staged rows of L: a column of them is conflict-free
 
@@ -37,17 +37,18 @@ struct TiLayout {
   size_t bytes;
 };
 
-__host__ __device__ inline TiLayout ti_layout(int w, int kpad, int nbuf) {
+// ns: columns of A12 per CTA (32, or 8 for short solves: four times the CTAs)
+__host__ __device__ inline TiLayout ti_layout(int w, int kpad, int nbuf, int ns) {
   TiLayout t;
   t.nblk = (w + 31) / 32;
   t.wr = t.nblk * 32;
   t.rb = t.wr - 32;
   t.nbuf = nbuf;
-  t.xs = (size_t)t.wr * TI_NS;
+  t.xs = (size_t)t.wr * ns;
   t.li = (size_t)t.nblk * 32 * TI_LDS;
   size_t ls = (size_t)nbuf * t.rb * TI_LDS;
   const size_t inv_stage = (size_t)(TI_THREADS / 32) * 32 * TI_LDS;  // each warp's copy of its diagonal block
-  const size_t op = ((size_t)TI_NS * (kpad + 2) + 1) / 2;            // the 16-bit transpose of the strip
+  const size_t op = ((size_t)ns * (kpad + 2) + 1) / 2;               // the 16-bit transpose of the strip
   if (ls < inv_stage) ls = inv_stage;
   if (ls < op) ls = op;
   t.ls = ls;
@@ -64,7 +65,7 @@ __device__ __forceinline__ void ti_stage(const float* L, int64_t ld, int w, int 
   }
 }
 
-template <typename H>
+template <int NS, typename H>
 __device__ __forceinline__ bool ti_write_operand(const float* Xs, int w, int nc, int c0, H* Bop, int kpad,
                                                  unsigned short* O) {
   // transpose through shared memory: O[c * (kpad + 2) + t] (an odd word
@@ -72,9 +73,9 @@ __device__ __forceinline__ bool ti_write_operand(const float* Xs, int w, int nc,
   // 4-byte stores of each column's kpad values
   const int so = kpad + 2;
   bool bad = false;
-  for (int e = threadIdx.x; e < TI_NS * kpad; e += TI_THREADS) {
-    const int c = e & 31, t = e >> 5;
-    const H h = to16<H>(t < w ? Xs[t * TI_NS + c] : 0.0f);
+  for (int e = threadIdx.x; e < NS * kpad; e += TI_THREADS) {
+    const int c = e % NS, t = e / NS;
+    const H h = to16<H>(t < w ? Xs[t * NS + c] : 0.0f);
     if (t < w && c < nc) bad |= bad16<H>(h);
     O[c * so + t] = bits16<H>(h);
   }
@@ -89,23 +90,28 @@ __device__ __forceinline__ bool ti_write_operand(const float* Xs, int w, int nc,
   return bad;
 }
 
+template <int NS>
 __global__ void __launch_bounds__(TI_THREADS) trsm_inv_kernel(const float* __restrict__ L, float* X, int64_t ld,
                                                               int w, int N, int nbuf, int kind, void* Bop, int kpad,
                                                               int* status) {
+  static_assert(NS == 32 || NS == 8, "strip widths");
+  constexpr int TQ = NS / 4;              // 16-byte pieces per strip row
+  constexpr int RT = NS == 32 ? 4 : 1;    // rows per update tile (tiles are RT x 8)
+  constexpr int CG = NS / 8;              // 8-column groups per strip
   extern __shared__ __align__(16) float smf[];
-  const TiLayout lay = ti_layout(w, kind ? kpad : 0, nbuf);
-  float* Xs = smf;            // [wr][32]: the strip of A12, solved in place
+  const TiLayout lay = ti_layout(w, kind ? kpad : 0, nbuf, NS);
+  float* Xs = smf;            // [wr][NS]: the strip of A12, solved in place
   float* Li = Xs + lay.xs;    // [nblk][32][33]: inverses of the diagonal blocks
   float* Ls = Li + lay.li;    // staged rows of L (also the inversion's copies and the operand transpose)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int c0 = blockIdx.x * TI_NS;
-  const int nc = min(TI_NS, N - c0);
+  const int c0 = blockIdx.x * NS;
+  const int nc = min(NS, N - c0);
 
   // 1. the strip -> Xs (rows past w and columns past N zero)
-  const bool vec = nc == TI_NS && ((reinterpret_cast<uintptr_t>(X + c0) & 15) == 0) && (ld % 4) == 0;
-  for (int e = tid; e < lay.wr * 8; e += TI_THREADS) {
-    const int r = e >> 3, q = (e & 7) * 4;
-    float* dst = &Xs[r * TI_NS + q];
+  const bool vec = nc == NS && ((reinterpret_cast<uintptr_t>(X + c0) & 15) == 0) && (ld % 4) == 0;
+  for (int e = tid; e < lay.wr * TQ; e += TI_THREADS) {
+    const int r = e / TQ, q = (e % TQ) * 4;
+    float* dst = &Xs[r * NS + q];
     if (r < w && vec) {
       cp_async<16>(dst, X + (int64_t)r * ld + c0 + q);
     } else {
@@ -167,19 +173,20 @@ __global__ void __launch_bounds__(TI_THREADS) trsm_inv_kernel(const float* __res
     }
     // (i) X_b <- Z_b X_b: thread = one row t, four columns
     {
-      const int t = tid >> 3, cq = (tid & 7) * 4;
+      const int t = tid / TQ, cq = (tid % TQ) * 4;
+      const bool act = t < 32;
       const float* Z = Li + b * 32 * TI_LDS;
       float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-      for (int s = 0; s < bw; ++s) {  // Z[t][s] = 0 for s > t
+      for (int s = 0; act && s < bw; ++s) {  // Z[t][s] = 0 for s > t
         const float z = Z[t * TI_LDS + s];
-        const float4 x = *reinterpret_cast<const float4*>(&Xs[(b0 + s) * TI_NS + cq]);
+        const float4 x = *reinterpret_cast<const float4*>(&Xs[(b0 + s) * NS + cq]);
         a0 = fmaf(z, x.x, a0);
         a1 = fmaf(z, x.y, a1);
         a2 = fmaf(z, x.z, a2);
         a3 = fmaf(z, x.w, a3);
       }
       __syncthreads();  // every thread has read X_b
-      if (t < bw) *reinterpret_cast<float4*>(&Xs[(b0 + t) * TI_NS + cq]) = make_float4(a0, a1, a2, a3);
+      if (act && t < bw) *reinterpret_cast<float4*>(&Xs[(b0 + t) * NS + cq]) = make_float4(a0, a1, a2, a3);
     }
     if (nbuf == 2) {
       // the next block's rows go to the other buffer, last read in the
@@ -191,36 +198,36 @@ __global__ void __launch_bounds__(TI_THREADS) trsm_inv_kernel(const float* __res
       cp_async_wait_group<0>();
     }
     __syncthreads();
-    // (ii) rows below: X_r -= L_rb X_b; item = 4 rows x 8 columns
+    // (ii) rows below: X_r -= L_rb X_b; item = RT rows x 8 columns
     const int R = w - b0 - 32;
     if (R > 0) {
-      const int R4 = (R + 3) & ~3;
-      const float* xb = Xs + b0 * TI_NS;
-      for (int it = tid; it < R4; it += TI_THREADS) {
-        const int rg = it >> 2, cg = it & 3;
-        const float* lr = cur + 4 * rg * TI_LDS;
-        float acc[4][8];
+      const int Rp = (R + RT - 1) / RT * RT;
+      const float* xb = Xs + b0 * NS;
+      for (int it = tid; it < Rp / RT * CG; it += TI_THREADS) {
+        const int rg = it / CG, cg = it % CG;
+        const float* lr = cur + RT * rg * TI_LDS;
+        float acc[RT][8];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < RT; ++i)
 #pragma unroll
           for (int q = 0; q < 8; ++q) acc[i][q] = 0.0f;
 #pragma unroll 8
         for (int k = 0; k < 32; ++k) {
-          const float4 x0 = *reinterpret_cast<const float4*>(&xb[k * TI_NS + 8 * cg]);
-          const float4 x1 = *reinterpret_cast<const float4*>(&xb[k * TI_NS + 8 * cg + 4]);
+          const float4 x0 = *reinterpret_cast<const float4*>(&xb[k * NS + 8 * cg]);
+          const float4 x1 = *reinterpret_cast<const float4*>(&xb[k * NS + 8 * cg + 4]);
           const float xv[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
+          for (int i = 0; i < RT; ++i) {
             const float l = lr[i * TI_LDS + k];
 #pragma unroll
             for (int q = 0; q < 8; ++q) acc[i][q] = fmaf(l, xv[q], acc[i][q]);
           }
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const int r = b0 + 32 + 4 * rg + i;
+        for (int i = 0; i < RT; ++i) {
+          const int r = b0 + 32 + RT * rg + i;
           if (r < w) {
-            float4* p = reinterpret_cast<float4*>(&Xs[r * TI_NS + 8 * cg]);
+            float4* p = reinterpret_cast<float4*>(&Xs[r * NS + 8 * cg]);
             float4 u = p[0], v = p[1];
             u.x -= acc[i][0]; u.y -= acc[i][1]; u.z -= acc[i][2]; u.w -= acc[i][3];
             v.x -= acc[i][4]; v.y -= acc[i][5]; v.z -= acc[i][6]; v.w -= acc[i][7];
@@ -234,20 +241,20 @@ __global__ void __launch_bounds__(TI_THREADS) trsm_inv_kernel(const float* __res
   }
 
   // 3. the solved strip back to A12, and the B operand
-  for (int e = tid; e < w * 8; e += TI_THREADS) {
-    const int r = e >> 3, q = (e & 7) * 4;
+  for (int e = tid; e < w * TQ; e += TI_THREADS) {
+    const int r = e / TQ, q = (e % TQ) * 4;
     if (vec) {
-      *reinterpret_cast<float4*>(X + (int64_t)r * ld + c0 + q) = *reinterpret_cast<const float4*>(&Xs[r * TI_NS + q]);
+      *reinterpret_cast<float4*>(X + (int64_t)r * ld + c0 + q) = *reinterpret_cast<const float4*>(&Xs[r * NS + q]);
     } else {
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        if (q + i < nc) X[(int64_t)r * ld + c0 + q + i] = Xs[r * TI_NS + q + i];
+        if (q + i < nc) X[(int64_t)r * ld + c0 + q + i] = Xs[r * NS + q + i];
     }
   }
   if (kind != 0) {
     unsigned short* O = reinterpret_cast<unsigned short*>(Ls);
-    const bool bad = kind == 1 ? ti_write_operand<__nv_bfloat16>(Xs, w, nc, c0, (__nv_bfloat16*)Bop, kpad, O)
-                               : ti_write_operand<__half>(Xs, w, nc, c0, (__half*)Bop, kpad, O);
+    const bool bad = kind == 1 ? ti_write_operand<NS, __nv_bfloat16>(Xs, w, nc, c0, (__nv_bfloat16*)Bop, kpad, O)
+                               : ti_write_operand<NS, __half>(Xs, w, nc, c0, (__half*)Bop, kpad, O);
     if (__syncthreads_or(bad) && tid == 0) atomicOr(status, ST_RANGE);
   }
 }
@@ -262,19 +269,27 @@ cudaError_t launch_trsm_inv(const float* L11, float* A12, int64_t ldw, int w, in
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  // A grid of one wave loads the next block's rows during this block (two
-  // buffers); a larger grid keeps one buffer, so that two CTAs fit an SM and
-  // each hides the other's waits.
+  // A short solve (fewer 32-column strips than half the SMs: the next
+  // panel's columns) takes strips of 8 columns, four times the CTAs for the
+  // same chain of blocks.  A grid of one wave loads the next block's rows
+  // during this block (two buffers); a larger grid keeps one buffer, so that
+  // two CTAs fit an SM and each hides the other's waits.
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const bool one_wave = cdiv(N, TI_NS) <= sms;
-  TiLayout lay = ti_layout(w, kind ? kpad : 0, one_wave ? 2 : 1);
-  if (lay.bytes > (size_t)optin) lay = ti_layout(w, kind ? kpad : 0, 1);
+  const int ns = cdiv(N, 32) < sms / 2 ? 8 : 32;
+  const bool one_wave = cdiv(N, ns) <= sms;
+  TiLayout lay = ti_layout(w, kind ? kpad : 0, one_wave ? 2 : 1, ns);
+  if (lay.bytes > (size_t)optin) lay = ti_layout(w, kind ? kpad : 0, 1, ns);
   if (lay.bytes > (size_t)optin) return cudaErrorInvalidValue;
-  cudaError_t e = allow_max_smem((const void*)trsm_inv_kernel);
+  const void* kern = ns == 8 ? (const void*)trsm_inv_kernel<8> : (const void*)trsm_inv_kernel<32>;
+  cudaError_t e = allow_max_smem(kern);
   if (e != cudaSuccess) return e;
-  trsm_inv_kernel<<<(unsigned)cdiv(N, TI_NS), TI_THREADS, lay.bytes, st>>>(L11, A12, ldw, w, N, lay.nbuf, kind, Bop,
-                                                                           kpad, status);
+  if (ns == 8)
+    trsm_inv_kernel<8><<<(unsigned)cdiv(N, 8), TI_THREADS, lay.bytes, st>>>(L11, A12, ldw, w, N, lay.nbuf, kind, Bop,
+                                                                            kpad, status);
+  else
+    trsm_inv_kernel<32><<<(unsigned)cdiv(N, 32), TI_THREADS, lay.bytes, st>>>(L11, A12, ldw, w, N, lay.nbuf, kind,
+                                                                              Bop, kpad, status);
   return cudaGetLastError();
 }
 

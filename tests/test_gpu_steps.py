@@ -121,7 +121,7 @@ def test_panel_zero_pivot(ctx):
 
 @pytest.mark.parametrize("prec", ["f64", "f32", "bf16"])
 @pytest.mark.parametrize("w,N", [(1, 1), (32, 31), (64, 257), (100, 40), (256, 1000), (384, 70), (512, 100),
-                                 (257, 33)])
+                                 (257, 33), (256, 3000), (200, 5001)])
 def test_trsm(ctx, prec, w, N):
     import torch
     rng = np.random.default_rng(w * 7 + N)
@@ -131,7 +131,8 @@ def test_trsm(ctx, prec, w, N):
     ldb = max(w, N)  # the kernel shares one row stride: embed both in w x ldb buffers
     Lbuf = np.zeros((w, ldb)); Lbuf[:, :w] = Lm
     Xbuf = np.zeros((w, ldb)); Xbuf[:, :N] = X
-    # bf16: the mixed factorizations' form (FP32 arithmetic, inverted diagonal blocks)
+    # bf16: the mixed factorizations' form (FP32 arithmetic, inverted diagonal
+    # blocks; strips of 8 columns below about 2400 columns, 32 above)
     dt = torch.float64 if prec == "f64" else torch.float32
     Ld, Xd = _rm(Lbuf, dt), _rm(Xbuf, dt)
     ctx.step_trsm(Ld[:, :w], Xd[:, :N], prec)
