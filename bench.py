@@ -21,6 +21,11 @@ import argparse
 import json
 import math
 import os
+
+# The served companion runs many requests' streams at once: with CUDA's
+# default of 8 hardware work queues they share queues and wait behind one
+# another.  Set before any CUDA context exists in this process.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 import statistics
 import subprocess
 import sys
@@ -62,7 +67,7 @@ WORKLOADS = {
     # right-hand sides, 30% repeat-RHS on resident factors, FP16 factor + FP64
     # refinement, admission by a 120 GB HBM budget
     "served_2000": dict(rate=2000.0, seconds=60.0, nmin=64, nmax=8192, kmax=16, repeat=0.3, seed=6, prec="fp16",
-                        budget_gb=120, slots=8, pool=48),
+                        budget_gb=120, slots=24, pool=48),
 }
 DEFAULT = "hpl_f64_n16384_nb256"
 METRIC = "LU solve TFLOP/s (HPL count 2/3 n^3 + 2 n^2 nrhs) at scaled residual < 16"

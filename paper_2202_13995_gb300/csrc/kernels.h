@@ -189,6 +189,7 @@ struct SolveScratch {
   int nblk_max;
   void* dinv = nullptr;     // optional inverses of the 64 x 64 diagonal blocks
   bool dinv_ready = false;
+  int max_ctas = 0;         // CTAs per triangle launch (0: one per 64-row block)
 };
 size_t solve_dinv_bytes(int n, int tsize);
 template <typename T>

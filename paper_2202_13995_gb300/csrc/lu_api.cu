@@ -98,12 +98,15 @@ struct lu_ctx_s {
   // lookahead: a side stream for the next panel, joined back by events
   cudaStream_t side = nullptr;
   cudaEvent_t ev_next = nullptr, ev_panel = nullptr;
+  cudaEvent_t ev_block = nullptr;  // shared contexts: host waits sleep on this event instead of spinning
   bool lookahead = true;
+  int solve_ctas = 0;  // CTAs per triangular-solve launch (0: one per 64-row block)
+  int gemm_ctas = 0;   // persistent CTAs of a trailing update without the lookahead (0: every SM)
   // diagonal-pivot check of FP32 panels, and the SMs its lookahead panels keep
   // (the trailing update gets the rest)
   bool spec = true;
   int spec_sms = 32;
-  bool split_residual = true;  // the refinement's residual by the split product for >= 4 right-hand sides
+  bool split_residual = true;  // the refinement's residual by the split product for > 16 right-hand sides
 };
 
 enum { PH_PANEL = 0, PH_LASWP, PH_TRSM, PH_CAST, PH_GEMM, PH_SOLVE, PH_RESID, PH_OTHER, PH_N };
@@ -167,7 +170,7 @@ struct lu_fact_s {
   void* solve_mem = nullptr;
   SolveScratch ss{};
   double* vec_ws = nullptr;  // refinement: R, D, partial sums
-  void* res_ws = nullptr;    // refinement with >= 4 right-hand sides: split operands of the residual product
+  void* res_ws = nullptr;    // refinement with > 16 right-hand sides: split operands of the residual product
   size_t res_ws_bytes = 0;
   size_t vec_ws_bytes = 0;
   int info = -1;             // cached host info (-1 = unknown)
@@ -285,6 +288,7 @@ extern "C" void lu_destroy(lu_ctx c) {
     cudaStreamSynchronize(c->side);
     cudaStreamDestroy(c->side);
   }
+  if (c->ev_block) cudaEventDestroy(c->ev_block);
   if (c->ev_next) cudaEventDestroy(c->ev_next);
   if (c->ev_panel) cudaEventDestroy(c->ev_panel);
   if (c->mem) {
@@ -336,9 +340,18 @@ extern "C" int lu_profile_read(lu_ctx c, double* ms, long long* launches) {
   return LU_OK;
 }
 
+// The host waits for the context's stream: spinning (the lowest latency),
+// or for a shared context, asleep on a blocking event, so that many contexts
+// waiting at once do not hold a host core each.
+static cudaError_t ctx_wait(lu_ctx c, cudaStream_t st) {
+  if (c->ev_block == nullptr) return cudaStreamSynchronize(st);
+  cudaError_t e = cudaEventRecord(c->ev_block, st);
+  return e != cudaSuccess ? e : cudaEventSynchronize(c->ev_block);
+}
+
 static int read_status(lu_ctx c) {
   CU_TRY(cudaMemcpyAsync(c->h_pinned, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  CU_TRY(cudaStreamSynchronize(c->stream));
+  CU_TRY(ctx_wait(c, c->stream));
   const int s = c->h_pinned[0];
   if (s) {
     CU_TRY(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
@@ -410,6 +423,10 @@ static cudaError_t panel_step(lu_fact f, int mode, T* Wkk, int m, int w, int kab
                                                     c->dev, s, f->spec_flag, (const T*)f->spec_backup));
 }
 
+// Persistent CTAs of a trailing update that has the device to itself: all
+// SMs; a shared context's (server slots) keep to gemm_ctas.
+static int gemm_cap(lu_ctx c) { return c->gemm_ctas > 0 ? c->gemm_ctas : c->dev.sm_count; }
+
 template <typename T>
 static int factor_loop(lu_fact f) {
   lu_ctx c = f->ctx;
@@ -439,10 +456,14 @@ static int factor_loop(lu_fact f) {
       CU_TRY(cudaStreamWaitEvent(st, c->ev_panel, 0));
       panel_ready = false;
     } else {
-      CU_TRY(panel_step<T>(f, mode, Wkk, n - k, w, k, st, 0));
+      // a checked panel's pivoted kernel (a cooperative launch, whose CTAs
+      // must all be resident at once) keeps to spec_sms CTAs: it returns at
+      // once when the check passed, and a launch across the whole device
+      // would wait for the device to drain whenever other work shares it
+      CU_TRY(panel_step<T>(f, mode, Wkk, n - k, w, k, st, mode != SPEC_OFF ? spec_sms : 0));
       if (mode == SPEC_TRY) {
         CU_TRY(cudaMemcpyAsync(hflag, f->spec_flag, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-        CU_TRY(cudaStreamSynchronize(st));
+        CU_TRY(ctx_wait(c, st));
         mode = (hflag[0] == 0 && hflag[3] == 0) ? SPEC_ON : SPEC_OFF;
         hflag[4] = hflag[7] = 0;
       }
@@ -481,7 +502,7 @@ static int factor_loop(lu_fact f) {
     CU_TRY(PHASE(c, PH_CAST, 1, launch_cast_a(kind, (const float*)L21, ld, rest, w, f->aop, f->kpad, c->d_status, st)));
     if (!split_top) {
       CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)A22, ld, f->aop, f->bop, rest, rest, f->kpad,
-                                               c->d_status, c->dev, st)));
+                                               c->d_status, c->dev, st, gemm_cap(c))));
       continue;
     }
     // columns of the next panel first
@@ -576,7 +597,7 @@ static int factor_loop_nopiv(lu_fact f) {
                                                 st)));
       if (!split_top) {
         CU_TRY(PHASE(c, PH_GEMM, 1, tc_gemm_run(kind, (float*)A22, ld, f->aop, f->bop, rest, rest, f->kpad,
-                                                 c->d_status, c->dev, st)));
+                                                 c->d_status, c->dev, st, gemm_cap(c))));
         continue;
       }
       // the next block column, then its diagonal block and left blocks beside the rest
@@ -773,15 +794,17 @@ static int ensure_info(lu_fact f) {
 
 static int solve_chunks(lu_fact f, int nrhs, const double* dB, int64_t ldb, double* dX, int64_t ldx) {
   lu_ctx c = f->ctx;
+  SolveScratch ss = f->ss;
+  ss.max_ctas = c->solve_ctas;
   for (int q0 = 0; q0 < nrhs; q0 += 32) {
     const int nr = (nrhs - q0) < 32 ? (nrhs - q0) : 32;
     if (f->prec == LU_F64) {
       CU_TRY(PHASE(c, PH_SOLVE, 2, launch_lu_solve<double>((const double*)f->W, f->ldw, f->rowid, f->n, nr,
-                                                            dB + q0 * ldb, ldb, dX + q0 * ldx, ldx, f->ss,
+                                                            dB + q0 * ldb, ldb, dX + q0 * ldx, ldx, ss,
                                                             c->d_status, c->stream)));
     } else {
       CU_TRY(PHASE(c, PH_SOLVE, 2, launch_lu_solve<float>((const float*)f->W, f->ldw, f->rowid, f->n, nr,
-                                                           dB + q0 * ldb, ldb, dX + q0 * ldx, ldx, f->ss,
+                                                           dB + q0 * ldb, ldb, dX + q0 * ldx, ldx, ss,
                                                            c->d_status, c->stream)));
     }
   }
@@ -829,14 +852,18 @@ static int residual_chunk(lu_ctx c, int n, int nr, const double* dA, int64_t lda
   return LU_OK;
 }
 
-// The refinement's residual R = B - A X for a chunk of nr >= 4 right-hand
-// sides on the tensor cores: the product A X in FP64 accuracy by error-free
+// The refinement's residual R = B - A X for a chunk of more than 16
+// right-hand sides on the tensor cores: the product A X in FP64 accuracy by error-free
 // splitting (the split update's kernels, k = 256 columns of A at a time,
 // each chunk's product exact before its one FP64 subtraction), in the
 // transposed form R^T -= X^T A^T, so that both operands are read along their
 // contiguous columns.  The FP64 CUDA-core residual does 2 n^2 nr FMAs on
 // GB300's slow FP64 pipes; here that work goes to the BF16 tensor cores.
-static bool split_residual_applies(lu_fact f, int n, int nr) { return f->ctx->split_residual && nr >= 4 && n >= 1024; }
+// The tensor-core product pads the chunk's right-hand sides to 128 rows, so
+// its cost does not shrink with nr while the CUDA-core residual's does: they
+// cost the same at about 16 (n = 32768: 33 and 32 ms), and with fewer the
+// CUDA-core residual also keeps the device freer for other work (served).
+static bool split_residual_applies(lu_fact f, int n, int nr) { return f->ctx->split_residual && nr > 16 && n >= 1024; }
 
 static int residual_chunk_split(lu_fact f, int n, int nr, const double* dA, int64_t lda, const double* dX,
                                 int64_t ldx, const double* dB, int64_t ldb, double* dR, int64_t ldr) {
@@ -930,7 +957,7 @@ extern "C" int lu_refine(lu_fact f, const double* dA, int lda, const double* dB,
           rc = solve_chunks(f, nr, R + (size_t)q0 * n, n, D, n);
           if (rc) return rc;
           CU_TRY(PHASE(c, PH_OTHER, 1, launch_add_update(dX + (int64_t)q0 * ldx, ldx, D, n, n, nr, c->d_active, st)));
-          CU_TRY(cudaStreamSynchronize(st));  // h_pinned is reused by the next chunk
+          CU_TRY(ctx_wait(c, st));  // h_pinned is reused by the next chunk
         }
       }
     }
@@ -1154,7 +1181,7 @@ size_t gb_fact_bytes(int n, int nrhs, lu_prec prec, int nb, int sm_count) {
   if (prec == LU_BF16 || prec == LU_FP16) b += (size_t)2 * nn * round_up(nb, 64) * 2 + 1024;
   const int nr = nrhs > 32 ? 32 : (nrhs < 1 ? 1 : nrhs);
   b += 2 * (size_t)nn * nrhs * 8 + residual_partial_bytes(nn, nr) + 4096;
-  if (nrhs >= 4 && nn >= 1024) b += ozaki_ws_bytes(32, nn, 256, sm_count);  // the split residual
+  if (nrhs > 16 && nn >= 1024) b += ozaki_ws_bytes(32, nn, 256, sm_count);  // the split residual
   return b;
 }
 
@@ -1162,6 +1189,22 @@ size_t gb_fact_bytes(int n, int nrhs, lu_prec prec, int nb, int sm_count) {
 // pinned buffers).  The caller guarantees that no work on the old context
 // still uses it.
 void gb_fact_rebind(lu_fact f, lu_ctx c) { f->ctx = c; }
+// The server's contexts factor without the lookahead: with several requests
+// on the device at once the other requests fill the SMs that the lookahead
+// would give the next panel, and its extra launches and stream waits only
+// lengthen each request (the results are the same bit for bit either way).
+// Likewise their triangular solves run on a few persistent CTAs (a solve's
+// CTAs wait on the blocks before theirs, and one CTA per block would hold
+// most SMs idle-waiting for the length of the solve), and their trailing
+// updates' persistent CTAs, each holding most of an SM's shared memory, on
+// part of the device, so that the other requests' panels find SMs.
+void gb_ctx_set_shared(lu_ctx c, int solve_ctas, int gemm_ctas) {
+  c->lookahead = false;
+  c->solve_ctas = solve_ctas;
+  c->gemm_ctas = gemm_ctas;
+  if (c->ev_block == nullptr) cudaEventCreateWithFlags(&c->ev_block, cudaEventBlockingSync | cudaEventDisableTiming);
+}
+void gb_ctx_wait(lu_ctx c) { ctx_wait(c, c->stream); }
 
 extern "C" int lu_default_nb(int n, lu_prec prec, int flags) {
   if (n < 0) return -1;

@@ -26,6 +26,8 @@
 
 size_t gb_fact_bytes(int n, int nrhs, lu_prec prec, int nb, int sm_count);
 void gb_fact_rebind(lu_fact f, lu_ctx c);
+void gb_ctx_set_shared(lu_ctx c, int solve_ctas, int gemm_ctas);
+void gb_ctx_wait(lu_ctx c);
 size_t gb_batch_bytes(int count, int nmax, int sm_count);
 
 namespace {
@@ -90,6 +92,12 @@ struct lu_server_s {
   // overlap too, and a panel launch that finds no room retries.
   std::mutex factor_mu;
   bool serialize_factor = false;
+  // CTAs per triangular-solve launch in the slots' contexts
+  // (GB300LU_SERVER_SOLVE_CTAS, default 8)
+  int solve_ctas = 8;
+  // persistent CTAs of the slots' trailing updates (GB300LU_SERVER_GEMM_CTAS,
+  // default 0: every SM)
+  int gemm_ctas = 0;
 };
 
 static size_t request_bytes(lu_server s, const lu_request& r) {
@@ -125,6 +133,7 @@ static void slot_main(lu_server s, int slot) {
     if (st) cudaStreamDestroy(st);
     return;
   }
+  gb_ctx_set_shared(ctx, s->solve_ctas, s->gemm_ctas);
   std::unique_lock<std::mutex> lk(s->mu);
   s->ctxs[slot] = ctx;
   s->streams[slot] = st;
@@ -199,7 +208,7 @@ static void slot_main(lu_server s, int slot) {
     if (rc == LU_OK)
       rc = lu_refine(f, job.req.dA, job.req.lda, job.req.dB, job.req.ldb, job.req.dX, job.req.ldx, job.req.nrhs,
                      16.0, 50, &iters, &sr);
-    cudaStreamSynchronize(st);
+    gb_ctx_wait(ctx);
     res.t_done_ns = now_ns();
     res.status = rc;
     res.iters = iters;
@@ -378,6 +387,8 @@ extern "C" int lu_server_create(lu_server* out, size_t hbm_budget_bytes, lu_prec
   s->prec = prec;
   s->budget = hbm_budget_bytes;
   s->serialize_factor = getenv("GB300LU_SERVER_SERIAL_FACTOR") != nullptr;
+  if (const char* e = getenv("GB300LU_SERVER_SOLVE_CTAS")) s->solve_ctas = atoi(e);
+  if (const char* e = getenv("GB300LU_SERVER_GEMM_CTAS")) s->gemm_ctas = atoi(e);
   s->max_slots = max_slots;
   s->ctxs.assign(max_slots, nullptr);
   s->streams.assign(max_slots, nullptr);

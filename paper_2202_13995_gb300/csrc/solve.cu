@@ -69,229 +69,235 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nblk = (n + TS_BS - 1) / TS_BS;
   const int64_t ldy = trsv_ldy(n);
-  if (tid == 0) {
-    sm.blk = atomicAdd(ticket, 1);
-    sm.flag = 1;
-  }
-  __syncthreads();
-  const int t_ = sm.blk;
-  if (!GB_IN_BOUNDS(status, t_ >= 0 && t_ < nblk)) return;  // uniform: sm.blk is the CTA's
-  const int ib = LOWER ? t_ : nblk - 1 - t_;
-  const int i0 = ib * TS_BS;
-  const int rows = min(TS_BS, n - i0);
-  const int count = LOWER ? ib : nblk - 1 - ib;
-  auto jb_of = [&](int it) { return LOWER ? it : nblk - 1 - it; };
+  // Persistent: a CTA takes blocks in ticket order until none is left (a
+  // block waits only on lower tickets, all held by running CTAs or done, so
+  // any grid size works; a capped grid leaves the other SMs to other work).
+  for (;;) {
+    if (tid == 0) {
+      sm.blk = atomicAdd(ticket, 1);
+      sm.flag = 1;
+    }
+    __syncthreads();
+    const int t_ = sm.blk;
+    if (t_ >= nblk) return;  // uniform: sm.blk is the CTA's
+    if (!GB_IN_BOUNDS(status, t_ >= 0)) return;
+    const int ib = LOWER ? t_ : nblk - 1 - t_;
+    const int i0 = ib * TS_BS;
+    const int rows = min(TS_BS, n - i0);
+    const int count = LOWER ? ib : nblk - 1 - ib;
+    auto jb_of = [&](int it) { return LOWER ? it : nblk - 1 - it; };
 
-  // Off the dependency chain: the diagonal block (or its inverse) and this
-  // block's right-hand side are loaded first; all loads issue before any use.
-  {
-    constexpr int PER = TS_BS * TS_BS / 256;
-    T dv[PER];
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int e = tid + q * 256;
-      const int rr = e >> 6, cc = e & 63;
-      if (DINV)
-        dv[q] = Dinv[((int64_t)ib * 2 + (LOWER ? 0 : 1)) * TS_BS * TS_BS + e];
-      else
-        dv[q] = (rr < rows && cc < rows) ? W[(int64_t)(i0 + rr) * ldw + i0 + cc] : T(0);
-    }
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int e = tid + q * 256;
-      sm.Ld[e >> 6][e & 63] = dv[q];
-    }
-    if (!DINV && !LOWER) {
-      __syncthreads();
-      if (tid < TS_BS) sm.rinv[tid] = tid < rows ? T(1) / sm.Ld[tid][tid] : T(0);
-    }
-  }
-  // this block's right-hand side: thread (row tid & 63) holds columns
-  // q = (tid >> 6) + 4 u
-  constexpr int NU = (NR + 3) / 4;
-  T rhs[NU];
-#pragma unroll
-  for (int u = 0; u < NU; ++u) {
-    rhs[u] = T(0);
-    const int r = tid & 63, q = (tid >> 6) + 4 * u;
-    if (q < NR && r < rows && q < nrhs) {
-      if (LOWER)
-        rhs[u] = (T)B[(int64_t)q * ldb + rowid[i0 + r]];
-      else
-        rhs[u] = Yin[(int64_t)q * trsv_ldy(n) + i0 + r];
-    }
-  }
-
-  // issue the loads of iteration `it` into its stage (all threads), after the
-  // solution block it needs has been published (warp 0 waits for the flag)
-  auto issue = [&](int it) {
-    if (it < count) {
-      const int jb = jb_of(it);
-      const int j0 = jb * TS_BS;
-      const int cols = min(TS_BS, n - j0);
-      const int st = it % STAGES;
-      for (int e = tid; e < TS_BS * TS_BS / CH; e += 256) {
-        const int rr = e / (TS_BS / CH), cc = (e % (TS_BS / CH)) * CH;
-        T* dst = &sm.Lb[st][rr][cc];
-        if (rr < rows && cc + CH <= cols) {
-          cp_async16(dst, W + (int64_t)(i0 + rr) * ldw + j0 + cc);
-        } else {
-#pragma unroll
-          for (int u = 0; u < CH; ++u)
-            dst[u] = (rr < rows && cc + u < cols) ? W[(int64_t)(i0 + rr) * ldw + j0 + cc + u] : T(0);
-        }
+    // Off the dependency chain: the diagonal block (or its inverse) and this
+    // block's right-hand side are loaded first; all loads issue before any use.
+    {
+      constexpr int PER = TS_BS * TS_BS / 256;
+      T dv[PER];
+  #pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int e = tid + q * 256;
+        const int rr = e >> 6, cc = e & 63;
+        if (DINV)
+          dv[q] = Dinv[((int64_t)ib * 2 + (LOWER ? 0 : 1)) * TS_BS * TS_BS + e];
+        else
+          dv[q] = (rr < rows && cc < rows) ? W[(int64_t)(i0 + rr) * ldw + i0 + cc] : T(0);
       }
-      if (warp == 0) {
-        int ok = 1;
-        if (lane == 0) ok = wait_flag_eq(flags + jb, 1, status) ? 1 : 0;
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        __syncwarp();  // orders lane 0's acquire before every lane's reads
-        if (!ok) {
-          if (lane == 0) sm.flag = 0;
-        } else {
-          // the published solution block (written before the flag's release)
-          for (int e = lane; e < NR * TS_BS / CH; e += 32) {
-            const int q = e / (TS_BS / CH), cc = (e % (TS_BS / CH)) * CH;
-            T* dst = &sm.yb[st][q][cc];
-            if (q < nrhs && cc + CH <= cols) {
-              cp_async16(dst, Yout + (int64_t)q * ldy + j0 + cc);
-            } else {
-#pragma unroll
-              for (int u = 0; u < CH; ++u)
-                dst[u] = (q < nrhs && cc + u < cols) ? __ldcg(Yout + (int64_t)q * ldy + j0 + cc + u) : T(0);
+  #pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int e = tid + q * 256;
+        sm.Ld[e >> 6][e & 63] = dv[q];
+      }
+      if (!DINV && !LOWER) {
+        __syncthreads();
+        if (tid < TS_BS) sm.rinv[tid] = tid < rows ? T(1) / sm.Ld[tid][tid] : T(0);
+      }
+    }
+    // this block's right-hand side: thread (row tid & 63) holds columns
+    // q = (tid >> 6) + 4 u
+    constexpr int NU = (NR + 3) / 4;
+    T rhs[NU];
+  #pragma unroll
+    for (int u = 0; u < NU; ++u) {
+      rhs[u] = T(0);
+      const int r = tid & 63, q = (tid >> 6) + 4 * u;
+      if (q < NR && r < rows && q < nrhs) {
+        if (LOWER)
+          rhs[u] = (T)B[(int64_t)q * ldb + rowid[i0 + r]];
+        else
+          rhs[u] = Yin[(int64_t)q * trsv_ldy(n) + i0 + r];
+      }
+    }
+
+    // issue the loads of iteration `it` into its stage (all threads), after the
+    // solution block it needs has been published (warp 0 waits for the flag)
+    auto issue = [&](int it) {
+      if (it < count) {
+        const int jb = jb_of(it);
+        const int j0 = jb * TS_BS;
+        const int cols = min(TS_BS, n - j0);
+        const int st = it % STAGES;
+        for (int e = tid; e < TS_BS * TS_BS / CH; e += 256) {
+          const int rr = e / (TS_BS / CH), cc = (e % (TS_BS / CH)) * CH;
+          T* dst = &sm.Lb[st][rr][cc];
+          if (rr < rows && cc + CH <= cols) {
+            cp_async16(dst, W + (int64_t)(i0 + rr) * ldw + j0 + cc);
+          } else {
+  #pragma unroll
+            for (int u = 0; u < CH; ++u)
+              dst[u] = (rr < rows && cc + u < cols) ? W[(int64_t)(i0 + rr) * ldw + j0 + cc + u] : T(0);
+          }
+        }
+        if (warp == 0) {
+          int ok = 1;
+          if (lane == 0) ok = wait_flag_eq(flags + jb, 1, status) ? 1 : 0;
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          __syncwarp();  // orders lane 0's acquire before every lane's reads
+          if (!ok) {
+            if (lane == 0) sm.flag = 0;
+          } else {
+            // the published solution block (written before the flag's release)
+            for (int e = lane; e < NR * TS_BS / CH; e += 32) {
+              const int q = e / (TS_BS / CH), cc = (e % (TS_BS / CH)) * CH;
+              T* dst = &sm.yb[st][q][cc];
+              if (q < nrhs && cc + CH <= cols) {
+                cp_async16(dst, Yout + (int64_t)q * ldy + j0 + cc);
+              } else {
+  #pragma unroll
+                for (int u = 0; u < CH; ++u)
+                  dst[u] = (q < nrhs && cc + u < cols) ? __ldcg(Yout + (int64_t)q * ldy + j0 + cc + u) : T(0);
+              }
             }
           }
         }
       }
-    }
-    cp_async_commit();
-  };
+      cp_async_commit();
+    };
 
-  // acc[rr][q]: partial sums of rows 8*warp + rr over this lane's columns
-  T acc[8][NR];
-#pragma unroll
-  for (int rr = 0; rr < 8; ++rr)
-#pragma unroll
-    for (int q = 0; q < NR; ++q) acc[rr][q] = T(0);
+    // acc[rr][q]: partial sums of rows 8*warp + rr over this lane's columns
+    T acc[8][NR];
+  #pragma unroll
+    for (int rr = 0; rr < 8; ++rr)
+  #pragma unroll
+      for (int q = 0; q < NR; ++q) acc[rr][q] = T(0);
 
-#pragma unroll 1
-  for (int s0 = 0; s0 < STAGES - 1; ++s0) issue(s0);
-#pragma unroll 1
-  for (int it = 0; it < count; ++it) {
-    issue(it + STAGES - 1);
-    cp_async_wait_group<STAGES - 1>();
-    __syncthreads();
-    if (!sm.flag) {
-      cp_async_wait_group<0>();
-      return;
-    }
-    const int st = it % STAGES;
-    T y0[NR], y1[NR];
-#pragma unroll
-    for (int q = 0; q < NR; ++q) {
-      y0[q] = sm.yb[st][q][lane];
-      y1[q] = sm.yb[st][q][lane + 32];
-    }
-#pragma unroll
-    for (int rr = 0; rr < 8; ++rr) {
-      const T l0 = sm.Lb[st][warp * 8 + rr][lane];
-      const T l1 = sm.Lb[st][warp * 8 + rr][lane + 32];
-#pragma unroll
-      for (int q = 0; q < NR; ++q) acc[rr][q] = fma(l0, y0[q], fma(l1, y1[q], acc[rr][q]));
-    }
-    __syncthreads();
-  }
-  cp_async_wait_group<0>();
-  // row sums: a fixed butterfly over the lanes (deterministic)
-#pragma unroll
-  for (int rr = 0; rr < 8; ++rr)
-#pragma unroll
-    for (int q = 0; q < NR; ++q) {
-      T v = acc[rr][q];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-      acc[rr][q] = v;
-    }
-  if (lane < NR) {
-#pragma unroll
-    for (int rr = 0; rr < 8; ++rr) {
-      T tot = T(0);
-#pragma unroll
-      for (int q = 0; q < NR; ++q)
-        if (q == lane) tot = acc[rr][q];
-      sm.v[lane][warp * 8 + rr] = tot;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int u = 0; u < NU; ++u) {
-    const int r = tid & 63, q = (tid >> 6) + 4 * u;
-    if (q < NR) sm.v[q][r] = (r < rows && q < nrhs) ? rhs[u] - sm.v[q][r] : T(0);
-  }
-  __syncthreads();
-  if (DINV) {
-    // x = inverse(diagonal block) * v: warp w computes rows 8w .. 8w+7
-    T xr[8][NR];
-#pragma unroll
-    for (int rr = 0; rr < 8; ++rr) {
-      const T d0 = sm.Ld[warp * 8 + rr][lane], d1 = sm.Ld[warp * 8 + rr][lane + 32];
-#pragma unroll
+  #pragma unroll 1
+    for (int s0 = 0; s0 < STAGES - 1; ++s0) issue(s0);
+  #pragma unroll 1
+    for (int it = 0; it < count; ++it) {
+      issue(it + STAGES - 1);
+      cp_async_wait_group<STAGES - 1>();
+      __syncthreads();
+      if (!sm.flag) {
+        cp_async_wait_group<0>();
+        return;
+      }
+      const int st = it % STAGES;
+      T y0[NR], y1[NR];
+  #pragma unroll
       for (int q = 0; q < NR; ++q) {
-        T v = d0 * sm.v[q][lane] + d1 * sm.v[q][lane + 32];
-#pragma unroll
+        y0[q] = sm.yb[st][q][lane];
+        y1[q] = sm.yb[st][q][lane + 32];
+      }
+  #pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        const T l0 = sm.Lb[st][warp * 8 + rr][lane];
+        const T l1 = sm.Lb[st][warp * 8 + rr][lane + 32];
+  #pragma unroll
+        for (int q = 0; q < NR; ++q) acc[rr][q] = fma(l0, y0[q], fma(l1, y1[q], acc[rr][q]));
+      }
+      __syncthreads();
+    }
+    cp_async_wait_group<0>();
+    // row sums: a fixed butterfly over the lanes (deterministic)
+  #pragma unroll
+    for (int rr = 0; rr < 8; ++rr)
+  #pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        T v = acc[rr][q];
+  #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        xr[rr][q] = v;
+        acc[rr][q] = v;
+      }
+    if (lane < NR) {
+  #pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        T tot = T(0);
+  #pragma unroll
+        for (int q = 0; q < NR; ++q)
+          if (q == lane) tot = acc[rr][q];
+        sm.v[lane][warp * 8 + rr] = tot;
       }
     }
     __syncthreads();
-    if (lane < NR) {
-#pragma unroll
+  #pragma unroll
+    for (int u = 0; u < NU; ++u) {
+      const int r = tid & 63, q = (tid >> 6) + 4 * u;
+      if (q < NR) sm.v[q][r] = (r < rows && q < nrhs) ? rhs[u] - sm.v[q][r] : T(0);
+    }
+    __syncthreads();
+    if (DINV) {
+      // x = inverse(diagonal block) * v: warp w computes rows 8w .. 8w+7
+      T xr[8][NR];
+  #pragma unroll
       for (int rr = 0; rr < 8; ++rr) {
-        T x = T(0);
-#pragma unroll
-        for (int q = 0; q < NR; ++q)
-          if (q == lane) x = xr[rr][q];
-        sm.v[lane][warp * 8 + rr] = x;
-      }
-    }
-  } else
-  for (int q = warp; q < nrhs; q += 8) {
-    T x0 = sm.v[q][lane], x1 = sm.v[q][lane + 32];
-    if (LOWER) {
-      for (int t = 0; t < rows; ++t) {
-        const T xt = __shfl_sync(0xffffffffu, t < 32 ? x0 : x1, t & 31);
-        if (lane > t) x0 -= sm.Ld[lane][t] * xt;
-        if (lane + 32 > t) x1 -= sm.Ld[lane + 32][t] * xt;
-      }
-    } else {
-      for (int t = rows - 1; t >= 0; --t) {
-        T xt;
-        if (t >= 32) {
-          if (lane == t - 32) x1 = x1 * sm.rinv[t];
-          xt = __shfl_sync(0xffffffffu, x1, t - 32);
-        } else {
-          if (lane == t) x0 = x0 * sm.rinv[t];
-          xt = __shfl_sync(0xffffffffu, x0, t);
+        const T d0 = sm.Ld[warp * 8 + rr][lane], d1 = sm.Ld[warp * 8 + rr][lane + 32];
+  #pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          T v = d0 * sm.v[q][lane] + d1 * sm.v[q][lane + 32];
+  #pragma unroll
+          for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+          xr[rr][q] = v;
         }
-        if (lane < t) x0 -= sm.Ld[lane][t] * xt;
-        if (lane + 32 < t) x1 -= sm.Ld[lane + 32][t] * xt;
+      }
+      __syncthreads();
+      if (lane < NR) {
+  #pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+          T x = T(0);
+  #pragma unroll
+          for (int q = 0; q < NR; ++q)
+            if (q == lane) x = xr[rr][q];
+          sm.v[lane][warp * 8 + rr] = x;
+        }
+      }
+    } else
+    for (int q = warp; q < nrhs; q += 8) {
+      T x0 = sm.v[q][lane], x1 = sm.v[q][lane + 32];
+      if (LOWER) {
+        for (int t = 0; t < rows; ++t) {
+          const T xt = __shfl_sync(0xffffffffu, t < 32 ? x0 : x1, t & 31);
+          if (lane > t) x0 -= sm.Ld[lane][t] * xt;
+          if (lane + 32 > t) x1 -= sm.Ld[lane + 32][t] * xt;
+        }
+      } else {
+        for (int t = rows - 1; t >= 0; --t) {
+          T xt;
+          if (t >= 32) {
+            if (lane == t - 32) x1 = x1 * sm.rinv[t];
+            xt = __shfl_sync(0xffffffffu, x1, t - 32);
+          } else {
+            if (lane == t) x0 = x0 * sm.rinv[t];
+            xt = __shfl_sync(0xffffffffu, x0, t);
+          }
+          if (lane < t) x0 -= sm.Ld[lane][t] * xt;
+          if (lane + 32 < t) x1 -= sm.Ld[lane + 32][t] * xt;
+        }
+      }
+      sm.v[q][lane] = x0;
+      sm.v[q][lane + 32] = x1;
+    }
+    __syncthreads();
+    for (int e = tid; e < TS_BS * NR; e += 256) {
+      const int rr = e & 63, q = e >> 6;
+      if (rr < rows && q < nrhs) {
+        const T v = sm.v[q][rr];
+        Yout[(int64_t)q * ldy + i0 + rr] = v;
+        if (!LOWER) X[(int64_t)q * ldx + i0 + rr] = (double)v;
       }
     }
-    sm.v[q][lane] = x0;
-    sm.v[q][lane + 32] = x1;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) st_release_s32(flags + ib, 1);
   }
-  __syncthreads();
-  for (int e = tid; e < TS_BS * NR; e += 256) {
-    const int rr = e & 63, q = e >> 6;
-    if (rr < rows && q < nrhs) {
-      const T v = sm.v[q][rr];
-      Yout[(int64_t)q * ldy + i0 + rr] = v;
-      if (!LOWER) X[(int64_t)q * ldx + i0 + rr] = (double)v;
-    }
-  }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) st_release_s32(flags + ib, 1);
 }
 
 size_t solve_scratch_bytes(int n, int tsize) {
@@ -328,14 +334,15 @@ static cudaError_t run_solve(const T* W, int64_t ldw, const int* rowid, int n, i
   int* ticket = s.sync + nblk;
   T* y = (T*)s.y;
   T* z = (T*)s.z;
+  const int grid = (s.max_ctas > 0 && s.max_ctas < nblk) ? s.max_ctas : nblk;
   e = cudaMemsetAsync(s.sync, 0, (size_t)(nblk + 1) * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  kl<<<nblk, 256, smem, st>>>(W, ldw, n, nrhs, B, ldb, rowid, nullptr, y, nullptr, 0, flags, ticket, status, Dinv);
+  kl<<<grid, 256, smem, st>>>(W, ldw, n, nrhs, B, ldb, rowid, nullptr, y, nullptr, 0, flags, ticket, status, Dinv);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(s.sync, 0, (size_t)(nblk + 1) * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  ku<<<nblk, 256, smem, st>>>(W, ldw, n, nrhs, nullptr, 0, nullptr, y, z, X, ldx, flags, ticket, status, Dinv);
+  ku<<<grid, 256, smem, st>>>(W, ldw, n, nrhs, nullptr, 0, nullptr, y, z, X, ldx, flags, ticket, status, Dinv);
   return cudaGetLastError();
 }
 
