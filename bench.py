@@ -772,7 +772,7 @@ def main():
     ap.add_argument("--slots", type=int, default=None, help="served: worker slots of the server")
     ap.add_argument("--no-served", action="store_true", help="skip the served companion of the default run")
     ap.add_argument("--served-seconds", type=float, default=60.0, help="served companion: seconds of arrivals")
-    ap.add_argument("--served-low-rate", type=float, default=500.0,
+    ap.add_argument("--served-low-rate", type=float, default=1500.0,
                     help="served companion: the lower offered rate reported beside 2000/s")
     args = ap.parse_args()
     cfg = WORKLOADS[args.workload]
