@@ -1189,15 +1189,16 @@ size_t gb_fact_bytes(int n, int nrhs, lu_prec prec, int nb, int sm_count) {
 // pinned buffers).  The caller guarantees that no work on the old context
 // still uses it.
 void gb_fact_rebind(lu_fact f, lu_ctx c) { f->ctx = c; }
-// The server's contexts factor without the lookahead: with several requests
-// on the device at once the other requests fill the SMs that the lookahead
-// would give the next panel, and its extra launches and stream waits only
-// lengthen each request (the results are the same bit for bit either way).
-// Likewise their triangular solves run on a few persistent CTAs (a solve's
-// CTAs wait on the blocks before theirs, and one CTA per block would hold
-// most SMs idle-waiting for the length of the solve), and their trailing
-// updates' persistent CTAs, each holding most of an SM's shared memory, on
-// part of the device, so that the other requests' panels find SMs.
+
+// A context that shares the device with others (the server's slots):
+//  - no lookahead: the other requests fill the SMs that the lookahead would
+//    give the next panel, and its extra launches and stream waits only
+//    lengthen each request (the results are the same bit for bit either way);
+//  - triangular solves on solve_ctas persistent CTAs: a solve's CTAs wait on
+//    the blocks before theirs, and one CTA per block would hold most SMs
+//    waiting for the length of the solve;
+//  - trailing updates on gemm_ctas persistent CTAs (0: every SM);
+//  - host waits asleep on a blocking event instead of spinning.
 void gb_ctx_set_shared(lu_ctx c, int solve_ctas, int gemm_ctas) {
   c->lookahead = false;
   c->solve_ctas = solve_ctas;

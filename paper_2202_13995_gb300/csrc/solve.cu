@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
     {
       constexpr int PER = TS_BS * TS_BS / 256;
       T dv[PER];
-  #pragma unroll
+#pragma unroll
       for (int q = 0; q < PER; ++q) {
         const int e = tid + q * 256;
         const int rr = e >> 6, cc = e & 63;
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
         else
           dv[q] = (rr < rows && cc < rows) ? W[(int64_t)(i0 + rr) * ldw + i0 + cc] : T(0);
       }
-  #pragma unroll
+#pragma unroll
       for (int q = 0; q < PER; ++q) {
         const int e = tid + q * 256;
         sm.Ld[e >> 6][e & 63] = dv[q];
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
     // q = (tid >> 6) + 4 u
     constexpr int NU = (NR + 3) / 4;
     T rhs[NU];
-  #pragma unroll
+#pragma unroll
     for (int u = 0; u < NU; ++u) {
       rhs[u] = T(0);
       const int r = tid & 63, q = (tid >> 6) + 4 * u;
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
           if (rr < rows && cc + CH <= cols) {
             cp_async16(dst, W + (int64_t)(i0 + rr) * ldw + j0 + cc);
           } else {
-  #pragma unroll
+#pragma unroll
             for (int u = 0; u < CH; ++u)
               dst[u] = (rr < rows && cc + u < cols) ? W[(int64_t)(i0 + rr) * ldw + j0 + cc + u] : T(0);
           }
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
               if (q < nrhs && cc + CH <= cols) {
                 cp_async16(dst, Yout + (int64_t)q * ldy + j0 + cc);
               } else {
-  #pragma unroll
+#pragma unroll
                 for (int u = 0; u < CH; ++u)
                   dst[u] = (q < nrhs && cc + u < cols) ? __ldcg(Yout + (int64_t)q * ldy + j0 + cc + u) : T(0);
               }
@@ -174,14 +174,14 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
 
     // acc[rr][q]: partial sums of rows 8*warp + rr over this lane's columns
     T acc[8][NR];
-  #pragma unroll
+#pragma unroll
     for (int rr = 0; rr < 8; ++rr)
-  #pragma unroll
+#pragma unroll
       for (int q = 0; q < NR; ++q) acc[rr][q] = T(0);
 
-  #pragma unroll 1
+#pragma unroll 1
     for (int s0 = 0; s0 < STAGES - 1; ++s0) issue(s0);
-  #pragma unroll 1
+#pragma unroll 1
     for (int it = 0; it < count; ++it) {
       issue(it + STAGES - 1);
       cp_async_wait_group<STAGES - 1>();
@@ -192,43 +192,43 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
       }
       const int st = it % STAGES;
       T y0[NR], y1[NR];
-  #pragma unroll
+#pragma unroll
       for (int q = 0; q < NR; ++q) {
         y0[q] = sm.yb[st][q][lane];
         y1[q] = sm.yb[st][q][lane + 32];
       }
-  #pragma unroll
+#pragma unroll
       for (int rr = 0; rr < 8; ++rr) {
         const T l0 = sm.Lb[st][warp * 8 + rr][lane];
         const T l1 = sm.Lb[st][warp * 8 + rr][lane + 32];
-  #pragma unroll
+#pragma unroll
         for (int q = 0; q < NR; ++q) acc[rr][q] = fma(l0, y0[q], fma(l1, y1[q], acc[rr][q]));
       }
       __syncthreads();
     }
     cp_async_wait_group<0>();
     // row sums: a fixed butterfly over the lanes (deterministic)
-  #pragma unroll
+#pragma unroll
     for (int rr = 0; rr < 8; ++rr)
-  #pragma unroll
+#pragma unroll
       for (int q = 0; q < NR; ++q) {
         T v = acc[rr][q];
-  #pragma unroll
+#pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
         acc[rr][q] = v;
       }
     if (lane < NR) {
-  #pragma unroll
+#pragma unroll
       for (int rr = 0; rr < 8; ++rr) {
         T tot = T(0);
-  #pragma unroll
+#pragma unroll
         for (int q = 0; q < NR; ++q)
           if (q == lane) tot = acc[rr][q];
         sm.v[lane][warp * 8 + rr] = tot;
       }
     }
     __syncthreads();
-  #pragma unroll
+#pragma unroll
     for (int u = 0; u < NU; ++u) {
       const int r = tid & 63, q = (tid >> 6) + 4 * u;
       if (q < NR) sm.v[q][r] = (r < rows && q < nrhs) ? rhs[u] - sm.v[q][r] : T(0);
@@ -237,23 +237,23 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
     if (DINV) {
       // x = inverse(diagonal block) * v: warp w computes rows 8w .. 8w+7
       T xr[8][NR];
-  #pragma unroll
+#pragma unroll
       for (int rr = 0; rr < 8; ++rr) {
         const T d0 = sm.Ld[warp * 8 + rr][lane], d1 = sm.Ld[warp * 8 + rr][lane + 32];
-  #pragma unroll
+#pragma unroll
         for (int q = 0; q < NR; ++q) {
           T v = d0 * sm.v[q][lane] + d1 * sm.v[q][lane + 32];
-  #pragma unroll
+#pragma unroll
           for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
           xr[rr][q] = v;
         }
       }
       __syncthreads();
       if (lane < NR) {
-  #pragma unroll
+#pragma unroll
         for (int rr = 0; rr < 8; ++rr) {
           T x = T(0);
-  #pragma unroll
+#pragma unroll
           for (int q = 0; q < NR; ++q)
             if (q == lane) x = xr[rr][q];
           sm.v[lane][warp * 8 + rr] = x;
