@@ -19,6 +19,10 @@
  * CTAs leave room for a panel CTA on every SM, and a cooperative panel launch
  * that finds no room retries (bounded).  The environment variable
  * GB300LU_SERVER_SERIAL_FACTOR runs factorizations one at a time instead.
+ * Requests with n >= 2048 in BF16 or FP16 are factored with block width 256
+ * (lu_factor's default is 128 up to n = 12288): with many requests on the
+ * device their trailing updates share HBM, and the wider block halves their
+ * traffic per FLOP.
  * The slots' contexts factor without the lookahead (other requests fill the
  * SMs it would use), run their triangular solves on 8 persistent CTAs
  * (GB300LU_SERVER_SOLVE_CTAS) and wait for the device asleep rather than

@@ -100,8 +100,18 @@ struct lu_server_s {
   int gemm_ctas = 0;
 };
 
+// Block width of a request's factorization: for the tensor-core precisions
+// 256 from n = 2048 up (the single-request table's choice is 128 up to n =
+// 12288): with many requests on the device at once their trailing updates
+// share HBM, whose traffic per FLOP nb = 256 halves (served mix at 2000/s
+// offered, 24 slots: 1776 -> 1865 solves/s).  It depends on the request
+// alone, so a result is the same alone and in a mix.
+static int request_nb(lu_server s, int n) {
+  return (s->prec == LU_BF16 || s->prec == LU_FP16) && n >= 2048 ? 256 : 0;
+}
+
 static size_t request_bytes(lu_server s, const lu_request& r) {
-  return gb_fact_bytes(r.n, r.nrhs, s->prec, 0, s->sm_count);
+  return gb_fact_bytes(r.n, r.nrhs, s->prec, request_nb(s, r.n), s->sm_count);
 }
 
 // Evict least-recently-used resident factors not in use until `need` fits.
@@ -200,7 +210,7 @@ static void slot_main(lu_server s, int slot) {
       std::unique_lock<std::mutex> flk(s->factor_mu, std::defer_lock);
       if (s->serialize_factor) flk.lock();
       int info = 0;
-      rc = lu_factor(ctx, job.req.n, job.req.dA, job.req.lda, s->prec, 0, &f, &info);  // synchronizes
+      rc = lu_factor(ctx, job.req.n, job.req.dA, job.req.lda, s->prec, request_nb(s, job.req.n), &f, &info);
       if (rc == LU_OK && info > 0) rc = LU_ESINGULAR;
     }
     int iters = 0;

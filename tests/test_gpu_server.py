@@ -37,7 +37,8 @@ def test_alone_equals_in_mix_and_oracle():
     import torch
     from paper_2202_13995_gb300 import lu
     rng = np.random.default_rng(11)
-    sizes = [(int(n), int(k)) for n, k in zip(np.exp(rng.uniform(np.log(64), np.log(2048), 24)).astype(int),
+    # (sizes past 2048 take the server's block width of 256)
+    sizes = [(int(n), int(k)) for n, k in zip(np.exp(rng.uniform(np.log(64), np.log(3000), 24)).astype(int),
                                                  rng.integers(1, 17, 24))]
     reqs = [_req(n, k, 500 + i) for i, (n, k) in enumerate(sizes)]
     alone = lu.Server(8 * GB, "fp16", max_slots=1)
