@@ -11,14 +11,20 @@
 // accumulates the products of its block row with every finished solution
 // block as soon as that block's flag is published, then solves its own
 // 64 x 64 diagonal block and publishes its solution block.  Every matrix entry
-// is read once, and the only serial chain is the diagonal solves.
+// is read once per chunk of right-hand sides, and the only serial chain is
+// the diagonal solves.  More right-hand sides than one CTA holds are cut in
+// chunks whose blocks interleave on the one ticket counter (block b of chunk
+// c is ticket b * chunks + c), so the chunks' chains run side by side in one
+// launch instead of one after the other.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace gb {
 
 constexpr int TS_BS = 64;
-constexpr int TS_NRMAX = 16;  // right-hand sides per launch: 16 for FP32 factors, 8 for FP64
+constexpr int TS_NRMAX = 16;  // right-hand sides per CTA: 16 for FP32 factors, 8 for FP64
+constexpr int TS_RHS_MAX = 32;  // right-hand sides per launch (chunks of the above)
+constexpr int TS_CHUNKS_MAX = TS_RHS_MAX / 8;
 
 // Leading dimension of the solution workspaces: a multiple of 16 elements, so
 // that every 16-byte chunk of a solution block starts 16-byte aligned.
@@ -54,14 +60,16 @@ struct TrsvSmem {
 //        from B through rowid: (P b)[i] = b[rowid[i]].
 // UPPER: X = U^-1 Y with non-unit upper U; the result goes to Yout (T) for
 //        the later blocks and to X (FP64).
-// Y layouts: Yin/Yout[q * ldy + i] (column q of the n x nr block), ldy = trsv_ldy(n).
+// Y layouts: Yin/Yout[q * ldy + i] (column q of the n x nrhs block), ldy = trsv_ldy(n).
+// nch chunks of NR right-hand sides (the last one possibly narrower); chunk c
+// takes columns [c NR, c NR + NR) of B, Y and X and the flags [c nblk, (c+1) nblk).
 // Requires ldw % (16 / sizeof(T)) == 0 and a 16-byte aligned W (the working
 // matrix is allocated that way).
 template <typename T, int NR, int STAGES, bool LOWER, bool DINV>
-__global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int64_t ldw, int n, int nrhs,
-                                                   const double* __restrict__ B, int64_t ldb,
-                                                   const int* __restrict__ rowid, const T* __restrict__ Yin,
-                                                   T* Yout, double* X, int64_t ldx, int* flags, int* ticket,
+__global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int64_t ldw, int n, int nrhs_all, int nch,
+                                                   const double* __restrict__ B0, int64_t ldb,
+                                                   const int* __restrict__ rowid, const T* __restrict__ Yin0,
+                                                   T* Yout0, double* X0, int64_t ldx, int* flags0, int* ticket,
                                                    int* status, const T* __restrict__ Dinv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TrsvSmem<T, NR, STAGES>& sm = *reinterpret_cast<TrsvSmem<T, NR, STAGES>*>(smem_raw);
@@ -78,9 +86,16 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
       sm.flag = 1;
     }
     __syncthreads();
-    const int t_ = sm.blk;
-    if (t_ >= nblk) return;  // uniform: sm.blk is the CTA's
-    if (!GB_IN_BOUNDS(status, t_ >= 0)) return;
+    const int tk = sm.blk;
+    if (tk >= nblk * nch) return;  // uniform: sm.blk is the CTA's
+    if (!GB_IN_BOUNDS(status, tk >= 0)) return;
+    const int chunk = tk % nch, t_ = tk / nch;
+    const int nrhs = min(NR, nrhs_all - chunk * NR);
+    const double* B = B0 ? B0 + (int64_t)chunk * NR * ldb : nullptr;
+    const T* Yin = Yin0 ? Yin0 + (int64_t)chunk * NR * ldy : nullptr;
+    T* Yout = Yout0 + (int64_t)chunk * NR * ldy;
+    double* X = X0 ? X0 + (int64_t)chunk * NR * ldx : nullptr;
+    int* flags = flags0 + (int64_t)chunk * nblk;
     const int ib = LOWER ? t_ : nblk - 1 - t_;
     const int i0 = ib * TS_BS;
     const int rows = min(TS_BS, n - i0);
@@ -123,12 +138,42 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
         if (LOWER)
           rhs[u] = (T)B[(int64_t)q * ldb + rowid[i0 + r]];
         else
-          rhs[u] = Yin[(int64_t)q * trsv_ldy(n) + i0 + r];
+          rhs[u] = Yin[(int64_t)q * ldy + i0 + r];
       }
     }
 
-    // issue the loads of iteration `it` into its stage (all threads), after the
-    // solution block it needs has been published (warp 0 waits for the flag)
+    // warp 0: wait for the flag of iteration it's solution block, then copy
+    // that block (written before the flag's release) into its stage
+    auto load_y = [&](int it) {
+      const int jb = jb_of(it);
+      const int j0 = jb * TS_BS;
+      const int cols = min(TS_BS, n - j0);
+      const int st = it % STAGES;
+      int ok = 1;
+      if (lane == 0) ok = wait_flag_eq(flags + jb, 1, status) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      __syncwarp();  // orders lane 0's acquire before every lane's reads
+      if (!ok) {
+        if (lane == 0) sm.flag = 0;
+        return;
+      }
+      for (int e = lane; e < NR * TS_BS / CH; e += 32) {
+        const int q = e / (TS_BS / CH), cc = (e % (TS_BS / CH)) * CH;
+        T* dst = &sm.yb[st][q][cc];
+        if (q < nrhs && cc + CH <= cols) {
+          cp_async16(dst, Yout + (int64_t)q * ldy + j0 + cc);
+        } else {
+#pragma unroll
+          for (int u = 0; u < CH; ++u)
+            dst[u] = (q < nrhs && cc + u < cols) ? __ldcg(Yout + (int64_t)q * ldy + j0 + cc + u) : T(0);
+        }
+      }
+    };
+    // issue the loads of iteration `it` into its stage (all threads): the
+    // matrix block, and (warp 0, after its flag) the solution block -- except
+    // for the last iteration, the block just before this one on the chain:
+    // its solution block is fetched only when that iteration runs, so that
+    // one product, not STAGES of them, follows the predecessor's flag
     auto issue = [&](int it) {
       if (it < count) {
         const int jb = jb_of(it);
@@ -146,28 +191,7 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
               dst[u] = (rr < rows && cc + u < cols) ? W[(int64_t)(i0 + rr) * ldw + j0 + cc + u] : T(0);
           }
         }
-        if (warp == 0) {
-          int ok = 1;
-          if (lane == 0) ok = wait_flag_eq(flags + jb, 1, status) ? 1 : 0;
-          ok = __shfl_sync(0xffffffffu, ok, 0);
-          __syncwarp();  // orders lane 0's acquire before every lane's reads
-          if (!ok) {
-            if (lane == 0) sm.flag = 0;
-          } else {
-            // the published solution block (written before the flag's release)
-            for (int e = lane; e < NR * TS_BS / CH; e += 32) {
-              const int q = e / (TS_BS / CH), cc = (e % (TS_BS / CH)) * CH;
-              T* dst = &sm.yb[st][q][cc];
-              if (q < nrhs && cc + CH <= cols) {
-                cp_async16(dst, Yout + (int64_t)q * ldy + j0 + cc);
-              } else {
-#pragma unroll
-                for (int u = 0; u < CH; ++u)
-                  dst[u] = (q < nrhs && cc + u < cols) ? __ldcg(Yout + (int64_t)q * ldy + j0 + cc + u) : T(0);
-              }
-            }
-          }
-        }
+        if (warp == 0 && it < count - 1) load_y(it);
       }
       cp_async_commit();
     };
@@ -185,6 +209,10 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
     for (int it = 0; it < count; ++it) {
       issue(it + STAGES - 1);
       cp_async_wait_group<STAGES - 1>();
+      if (it == count - 1 && warp == 0) {
+        load_y(it);
+        cp_async_wait_all();
+      }
       __syncthreads();
       if (!sm.flag) {
         cp_async_wait_group<0>();
@@ -300,22 +328,25 @@ __global__ void __launch_bounds__(256) trsv_kernel(const T* __restrict__ W, int6
   }
 }
 
+// flags of every (block, chunk) and the ticket, then the two solution workspaces
 size_t solve_scratch_bytes(int n, int tsize) {
   const int nblk = (int)cdiv(n, TS_BS);
-  return 256 + (size_t)(nblk + 2) * sizeof(int) + 2 * (size_t)trsv_ldy(n) * TS_NRMAX * tsize + 512;
+  return 256 + (size_t)(nblk * TS_CHUNKS_MAX + 2) * sizeof(int) + 2 * (size_t)trsv_ldy(n) * TS_RHS_MAX * tsize +
+         512;
 }
 
 void solve_scratch_carve(SolveScratch* s, void* base, int n, int tsize) {
   const int nblk = (int)cdiv(n, TS_BS);
   char* p = (char*)base;
   s->sync = (int*)p;
-  p += ((size_t)(nblk + 2) * sizeof(int) + 255) / 256 * 256;
+  p += ((size_t)(nblk * TS_CHUNKS_MAX + 2) * sizeof(int) + 255) / 256 * 256;
   s->y = p;
-  p += ((size_t)trsv_ldy(n) * TS_NRMAX * tsize + 255) / 256 * 256;
+  p += ((size_t)trsv_ldy(n) * TS_RHS_MAX * tsize + 255) / 256 * 256;
   s->z = p;
   s->nblk_max = nblk;
 }
 
+// nrhs right-hand sides in nch = ceil(nrhs / NR) chunks of NR
 template <typename T, int NR, bool DINV>
 static cudaError_t run_solve(const T* W, int64_t ldw, const int* rowid, int n, int nrhs, const double* B,
                              int64_t ldb, double* X, int64_t ldx, const SolveScratch& s, int* status,
@@ -330,19 +361,23 @@ static cudaError_t run_solve(const T* W, int64_t ldw, const int* rowid, int n, i
   if (e != cudaSuccess) return e;
   e = allow_max_smem((const void*)ku);
   if (e != cudaSuccess) return e;
+  const int nch = (nrhs + NR - 1) / NR;
+  if (nch > TS_CHUNKS_MAX || nrhs > TS_RHS_MAX) return cudaErrorInvalidValue;
+  const int tickets = nblk * nch;
   int* flags = s.sync;
-  int* ticket = s.sync + nblk;
+  int* ticket = s.sync + tickets;
   T* y = (T*)s.y;
   T* z = (T*)s.z;
-  const int grid = (s.max_ctas > 0 && s.max_ctas < nblk) ? s.max_ctas : nblk;
-  e = cudaMemsetAsync(s.sync, 0, (size_t)(nblk + 1) * sizeof(int), st);
+  const int grid = (s.max_ctas > 0 && s.max_ctas < tickets) ? s.max_ctas : tickets;
+  e = cudaMemsetAsync(s.sync, 0, (size_t)(tickets + 1) * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  kl<<<grid, 256, smem, st>>>(W, ldw, n, nrhs, B, ldb, rowid, nullptr, y, nullptr, 0, flags, ticket, status, Dinv);
+  kl<<<grid, 256, smem, st>>>(W, ldw, n, nrhs, nch, B, ldb, rowid, nullptr, y, nullptr, 0, flags, ticket, status,
+                              Dinv);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(s.sync, 0, (size_t)(nblk + 1) * sizeof(int), st);
+  e = cudaMemsetAsync(s.sync, 0, (size_t)(tickets + 1) * sizeof(int), st);
   if (e != cudaSuccess) return e;
-  ku<<<grid, 256, smem, st>>>(W, ldw, n, nrhs, nullptr, 0, nullptr, y, z, X, ldx, flags, ticket, status, Dinv);
+  ku<<<grid, 256, smem, st>>>(W, ldw, n, nrhs, nch, nullptr, 0, nullptr, y, z, X, ldx, flags, ticket, status, Dinv);
   return cudaGetLastError();
 }
 
@@ -394,50 +429,34 @@ cudaError_t launch_trinv(const T* W, int64_t ldw, int n, T* Dinv, cudaStream_t s
 template cudaError_t launch_trinv<float>(const float*, int64_t, int, float*, cudaStream_t);
 template cudaError_t launch_trinv<double>(const double*, int64_t, int, double*, cudaStream_t);
 
-// One launch pair per chunk of right-hand sides -- up to 16 with FP32
-// factors, 8 with FP64 (whose accumulators take twice the registers); the
-// chain of diagonal blocks is walked once per chunk (callers pass <= 32).
+// One launch pair for up to 32 right-hand sides: a CTA holds up to 16 with
+// FP32 factors, 8 with FP64 (whose accumulators take twice the registers);
+// more are cut in chunks of that width whose chains of diagonal blocks run
+// side by side in the same launches.
 template <typename T>
 cudaError_t launch_lu_solve(const T* W, int64_t ldw, const int* rowid, int n, int nrhs, const double* B,
                             int64_t ldb, double* X, int64_t ldx, const SolveScratch& s, int* status,
                             cudaStream_t st) {
   if (n <= 0 || nrhs <= 0) return cudaSuccess;
-  if (nrhs > 32) return cudaErrorInvalidValue;
+  if (nrhs > TS_RHS_MAX) return cudaErrorInvalidValue;
   if (((uintptr_t)W & 15u) || (ldw % (16 / sizeof(T))) != 0) return cudaErrorInvalidValue;
   constexpr int CHUNK = sizeof(T) == 4 ? 16 : 8;
-  static_assert(CHUNK <= TS_NRMAX, "solution workspace holds a chunk");
-  for (int q0 = 0; q0 < nrhs; q0 += CHUNK) {
-    const int nr = (nrhs - q0) < CHUNK ? (nrhs - q0) : CHUNK;
-    const double* Bq = B + (int64_t)q0 * ldb;
-    double* Xq = X + (int64_t)q0 * ldx;
-    cudaError_t e;
-    const bool dinv = s.dinv != nullptr && s.dinv_ready;
-    if (dinv) {
-      if (nr == 1)
-        e = run_solve<T, 1, true>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
-      else if (nr == 2)
-        e = run_solve<T, 2, true>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
-      else if (nr <= 4)
-        e = run_solve<T, 4, true>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
-      else if (nr <= 8)
-        e = run_solve<T, 8, true>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
-      else
-        e = run_solve<T, sizeof(T) == 4 ? 16 : 8, true>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
-    } else {
-      if (nr == 1)
-        e = run_solve<T, 1, false>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
-      else if (nr == 2)
-        e = run_solve<T, 2, false>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
-      else if (nr <= 4)
-        e = run_solve<T, 4, false>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
-      else if (nr <= 8)
-        e = run_solve<T, 8, false>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
-      else
-        e = run_solve<T, sizeof(T) == 4 ? 16 : 8, false>(W, ldw, rowid, n, nr, Bq, ldb, Xq, ldx, s, status, st);
-    }
-    if (e != cudaSuccess) return e;
+  static_assert(CHUNK <= TS_NRMAX && TS_RHS_MAX / CHUNK <= TS_CHUNKS_MAX, "solve workspace holds the chunks");
+  // a CTA's width: the right-hand sides rounded up to 1, 2, 4, 8 or the
+  // chunk (a column's arithmetic is the same at every width)
+  const bool dinv = s.dinv != nullptr && s.dinv_ready;
+  if (dinv) {
+    if (nrhs == 1) return run_solve<T, 1, true>(W, ldw, rowid, n, nrhs, B, ldb, X, ldx, s, status, st);
+    if (nrhs == 2) return run_solve<T, 2, true>(W, ldw, rowid, n, nrhs, B, ldb, X, ldx, s, status, st);
+    if (nrhs <= 4) return run_solve<T, 4, true>(W, ldw, rowid, n, nrhs, B, ldb, X, ldx, s, status, st);
+    if (nrhs <= 8) return run_solve<T, 8, true>(W, ldw, rowid, n, nrhs, B, ldb, X, ldx, s, status, st);
+    return run_solve<T, CHUNK, true>(W, ldw, rowid, n, nrhs, B, ldb, X, ldx, s, status, st);
   }
-  return cudaSuccess;
+  if (nrhs == 1) return run_solve<T, 1, false>(W, ldw, rowid, n, nrhs, B, ldb, X, ldx, s, status, st);
+  if (nrhs == 2) return run_solve<T, 2, false>(W, ldw, rowid, n, nrhs, B, ldb, X, ldx, s, status, st);
+  if (nrhs <= 4) return run_solve<T, 4, false>(W, ldw, rowid, n, nrhs, B, ldb, X, ldx, s, status, st);
+  if (nrhs <= 8) return run_solve<T, 8, false>(W, ldw, rowid, n, nrhs, B, ldb, X, ldx, s, status, st);
+  return run_solve<T, CHUNK, false>(W, ldw, rowid, n, nrhs, B, ldb, X, ldx, s, status, st);
 }
 
 template cudaError_t launch_lu_solve<double>(const double*, int64_t, const int*, int, int, const double*, int64_t,
