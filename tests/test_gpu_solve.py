@@ -100,6 +100,38 @@ def test_multi_rhs_f64(ctx, nrhs):
     assert np.all(O.scaled_residual(A, Xg, B) < 16.0)
 
 
+@pytest.mark.parametrize("prec,n", [("f64", 1000), ("f32", 1537), ("bf16", 2049)])
+def test_solve_columns_independent_of_batch(ctx, prec, n):
+    """A right-hand side's solution does not depend on the others solved with
+    it: 32 columns in one call (chunks of 8 or 16 per CTA, the chunks' chains
+    interleaved in one launch), 20 columns (a narrower last chunk), each half
+    of 16 and a single column give the same bits; and x against the oracle."""
+    A = I.hpl_matrix(n, 90 + n, diag_shift=0.25 * n)
+    B = I.hpl_rhs(n, 32, 91 + n)
+    f = ctx.factor(_dev(A), prec, 0)
+    assert f.info == 0
+
+    def solve(Bc):
+        X = _dev(Bc)
+        f.solve_(X)
+        return X.cpu().numpy()
+
+    X32 = solve(B)
+    assert np.array_equal(solve(B[:, :20]), X32[:, :20])
+    assert np.array_equal(solve(B[:, :16]), X32[:, :16])
+    assert np.array_equal(solve(B[:, 16:]), X32[:, 16:])
+    assert np.array_equal(solve(B[:, 21:22]), X32[:, 21:22])
+    if prec == "f64":
+        Xo, LUo, ipo, _ = O.solve(A, B)
+        tol, _ = _fwd_tol(LUo, ipo, A)
+        assert np.abs(X32 - Xo).max() / np.abs(Xo).max() <= tol
+    else:
+        # the low-precision factor's solve is an approximation: its error
+        # stays within what the factor's precision allows
+        Xo, _, _, _ = O.solve(A, B)
+        assert np.abs(X32 - Xo).max() / np.abs(Xo).max() <= (1e-4 if prec == "f32" else 1e-1)
+
+
 def test_residual_norms_against_oracle(ctx):
     """lu_residual_norms: the four infinity norms per column against the
     oracle's, and both checks (HPL's and the paper's shape) built from them."""
