@@ -236,6 +236,7 @@ struct OzParams {
   const int* ea;   // row exponents e_i
   const int* fb;   // column exponents f_j of this update's columns
   int vec_ok;      // C rows 16-byte aligned (vector loads and stores)
+  int stacked;     // m == 32: an A box holds four consecutive slices (see the kernel)
   long long* scratch;  // per CTA: the previous tile's sums (OZ_BM x OZ_BN)
   uint32_t idesc;
   int* status;
@@ -331,13 +332,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
   const uint32_t bar_tfull = bar_bempty + 8 * OZ_BSTAGES;
   const uint32_t bar_tempty = bar_tfull + 8 * OZ_NACC;
   const uint32_t bar_drain = bar_tempty + 8 * OZ_NACC;
-  constexpr int NBAR = 4 + 2 * OZ_BSTAGES + 2 * OZ_NACC + 1;
+  const uint32_t bar_consumed = bar_drain + 8;  // stacked: every epilogue warp has read the parked sums
+  const uint32_t bar_parked = bar_consumed + 8;  // stacked: every epilogue warp has parked its sums
+  constexpr int NBAR = 4 + 2 * OZ_BSTAGES + 2 * OZ_NACC + 3;
   static_assert(8 * NBAR + 16 <= 256, "control block");
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ctl + 8 * NBAR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(ctl + 8 * NBAR + 8);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = P.tiles_m * P.tiles_n;
+  // With m == 32 the 128-row box of A slice p holds slices p .. p + 3 in its
+  // four 32-row quarters, so one product with B slice q serves the pairs
+  // (p + g, q), g = 0..3: the tile walks p = 0, 4 (12 products instead of 36)
+  // and each epilogue warp weights its quarter by that quarter's slice order.
+  const int pstep = P.stacked ? 4 : 1;
 
   if (threadIdx.x == 0) {
     for (int a = 0; a < 2; ++a) {
@@ -353,6 +361,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       mbar_init(bar_tempty + 8 * a, OZ_EPI_WARPS);
     }
     mbar_init(bar_drain, 1);
+    mbar_init(bar_consumed, OZ_EPI_WARPS);
+    mbar_init(bar_parked, OZ_EPI_WARPS);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -381,7 +391,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       uint32_t ph = 0, abph = 0;
       bool ok = true;
       // A slices load one slice ahead, into the buffer the MMA released last:
-      // slice (tile, p + 1) is issued once the B chunks of (p, q = 0) are.
+      // slice (tile, p + pstep) is issued once the B chunks of (p, q = 0) are.
       auto load_a = [&](int tile, int p) -> bool {
         if (!mbar_wait(bar_aempty + 8 * ab, abph ^ 1u, P.status, abort_flag)) return false;
         int tm, tn_unused;
@@ -401,7 +411,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         int tm_unused, tn;
         oz_tile(t, P.tiles_m, P.tiles_n, tm_unused, tn);
-        for (int p = 0; p < OZ_S && ok; ++p) {
+        for (int p = 0; p < OZ_S && ok; p += pstep) {
           for (int q = 0; q < OZ_S - p && ok; ++q) {
             for (int kc = 0; kc < P.kchunks; ++kc) {
               if (!mbar_wait(bar_bempty + 8 * s, ph ^ 1u, P.status, abort_flag)) {
@@ -418,8 +428,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
               }
             }
             if (ok && q == 0) {
-              if (p + 1 < OZ_S)
-                ok = load_a(t, p + 1);
+              if (p + pstep < OZ_S)
+                ok = load_a(t, p + pstep);
               else if (t + (int)gridDim.x < ntiles)
                 ok = load_a(t + gridDim.x, 0);
             }
@@ -449,7 +459,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       uint32_t ph = 0, abph = 0, tph = 0;
       bool ok = true, issued = false;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-        for (int p = 0; p < OZ_S && ok; ++p) {
+        for (int p = 0; p < OZ_S && ok; p += pstep) {
           if (!mbar_wait(bar_afull + 8 * ab, abph, P.status, abort_flag)) {
             ok = false;
             break;
@@ -513,6 +523,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     const int half = (warp - 4) >> 2;      // which 64 columns of the tile
     const int et = threadIdx.x - 128;      // 0 .. 255
     const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+    // stacked: this warp's TMEM rows are slice p + gq of the box of slice p;
+    // every quarter then updates C row `lane`, the column pairs 4 i + gq, from
+    // the four quarters' parked sums
+    const int gq = P.stacked ? quarter : 0;
+    const int kstep = P.stacked ? 4 : 1;
+    const int kn = 32 / kstep;  // column pairs of the deferred update per thread
+    uint32_t sph = 0;  // stacked: phase parity of bar_consumed and bar_parked
     // This thread's 64 sums of the previous tile, parked in the CTA's scratch
     // ([pair of columns][thread][2]: a warp's accesses are contiguous) and
     // applied to C two columns per slice pair of the next tile, so that the
@@ -530,6 +547,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       const longlong2 iv = *reinterpret_cast<const longlong2*>(scr + (size_t)k * (2 * 256));
       qI[0] = iv.x;
       qI[1] = iv.y;
+      if (P.stacked) {
+        // the same row's partial sums of the other quarters (threads
+        // et + 32 (g - gq)): exact integers, so their sum is the whole product's
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          if (g == gq) continue;
+          const longlong2 w =
+              __ldcg(reinterpret_cast<const longlong2*>(scr + (size_t)k * (2 * 256) + 64 * (g - gq)));
+          qI[0] = (long long)((unsigned long long)qI[0] + (unsigned long long)w.x);
+          qI[1] = (long long)((unsigned long long)qI[1] + (unsigned long long)w.y);
+        }
+      }
       const int gc = dcol0 + 2 * k;
       if (P.vec_ok && gc + 2 <= P.n) {
         const double2 cv = *reinterpret_cast<const double2*>(dcrow + 2 * k);
@@ -561,7 +590,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int tm, tn;
       oz_tile(t, P.tiles_m, P.tiles_n, tm, tn);
-      const int row = tm * OZ_BM + quarter * 32 + lane;
+      const int row = P.stacked ? lane : tm * OZ_BM + quarter * 32 + lane;
       const bool rok = row < P.m;
       const int col0 = tn * OZ_BN + half * 64;
       double* crow = P.C + (int64_t)row * P.ldc + col0;
@@ -570,8 +599,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
       for (int j = 0; j < 64; ++j) lo[j] = hi[j] = 0u;
       unsigned long long corr = 0ull;
       int pi = 0;  // slice pair index within the tile
-      for (int p = 0; p < OZ_S && ok; ++p) {
-        if (p == 6 && rok) {
+      for (int p = 0; p < OZ_S && ok; p += pstep) {
+        if (p == (P.stacked ? 4 : 6) && rok) {
           // bring this tile's C segment into L2 for its deferred update
 #pragma unroll
           for (int c = 0; c < 64; c += 16)
@@ -586,38 +615,80 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
             break;
           }
           tc_fence_after();
-          const int tt = p + q;
-          const uint32_t taddr = tmem_base + lane_addr + (uint32_t)(acc * OZ_BN + half * 64);
-          uint32_t v[32];
-          TMEM_LD_X16(taddr, v);
-          TMEM_LD_X16(taddr + 16, (v + 16));
-          tmem_wait_ld();
-          oz_acc32(lo, hi, v, tt);
-          TMEM_LD_X16(taddr + 32, v);
-          TMEM_LD_X16(taddr + 48, (v + 16));
-          tmem_wait_ld();
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(bar_tempty + 8 * acc);
-          oz_acc32(lo + 32, hi + 32, v, tt);
-          corr += oz_corr(tt);
+          const int tt = p + gq + q;
+          if (tt < OZ_S) {
+            const uint32_t taddr = tmem_base + lane_addr + (uint32_t)(acc * OZ_BN + half * 64);
+            uint32_t v[32];
+            TMEM_LD_X16(taddr, v);
+            TMEM_LD_X16(taddr + 16, (v + 16));
+            tmem_wait_ld();
+            oz_acc32(lo, hi, v, tt);
+            TMEM_LD_X16(taddr + 32, v);
+            TMEM_LD_X16(taddr + 48, (v + 16));
+            tmem_wait_ld();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_tempty + 8 * acc);
+            oz_acc32(lo + 32, hi + 32, v, tt);
+            corr += oz_corr(tt);
+          } else {
+            // a stacked quarter whose pair order is past the last kept one
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_tempty + 8 * acc);
+          }
           if (++acc == OZ_NACC) {
             acc = 0;
             tph ^= 1u;
           }
           // the previous tile's update, two columns per pair, loads one pair ahead
           defer_complete();
-          if (pi < 32) defer_issue(pi);
+          if (pi < kn) defer_issue(pi * kstep + gq);
         }
       }
       if (!ok) break;
       defer_complete();
+      // (every pair of a tile has passed: nothing of the previous update is left)
+      for (; pi < kn; ++pi) {
+        defer_issue(pi * kstep + gq);
+        defer_complete();
+      }
+      if (P.stacked) {
+        // every quarter has read the previous sums that this warp overwrites now
+        __syncwarp();
+        int okw = 1;
+        if (lane == 0) {
+          mbar_arrive(bar_consumed);
+          okw = mbar_wait(bar_consumed, sph, P.status, abort_flag) ? 1 : 0;
+        }
+        okw = __shfl_sync(0xffffffffu, okw, 0);
+        if (!okw) {
+          ok = false;
+          break;
+        }
+      }
       // park this tile's sums; their update runs during the next tile
 #pragma unroll
       for (int k = 0; k < 32; ++k) {
         const unsigned long long i0 = (((unsigned long long)hi[2 * k] << 32) | lo[2 * k]) - corr;
         const unsigned long long i1 = (((unsigned long long)hi[2 * k + 1] << 32) | lo[2 * k + 1]) - corr;
         *reinterpret_cast<longlong2*>(scr + (size_t)k * (2 * 256)) = make_longlong2((long long)i0, (long long)i1);
+      }
+      if (P.stacked) {
+        // the quarters read each other's parked sums only after all are written
+        __threadfence_block();
+        __syncwarp();
+        int okw = 1;
+        if (lane == 0) {
+          mbar_arrive(bar_parked);
+          okw = mbar_wait(bar_parked, sph, P.status, abort_flag) ? 1 : 0;
+        }
+        okw = __shfl_sync(0xffffffffu, okw, 0);
+        if (!okw) {
+          ok = false;
+          break;
+        }
+        sph ^= 1u;
       }
       dcrow = rok ? crow : nullptr;
       dcol0 = col0;
@@ -626,8 +697,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     if (ok && dcrow != nullptr) {
       // the last tile's update
 #pragma unroll 1
-      for (int k = 0; k < 32; ++k) {
-        defer_issue(k);
+      for (int i = 0; i < kn; ++i) {
+        defer_issue(i * kstep + gq);
         defer_complete();
       }
     }
@@ -747,6 +818,7 @@ cudaError_t ozaki_gemm(double* C, int64_t ldc, const void* ws, int m, int n, int
   P.scratch = L.scratch;
   P.idesc = tc_idesc_mn(1u, OZ_BM, OZ_BN);
   P.vec_ok = (((uintptr_t)C & 15u) == 0 && (ldc % 2) == 0) ? 1 : 0;
+  P.stacked = m == 32 ? 1 : 0;  // the slices of a 32-row A are 32 rows apart: four per 128-row box
   P.status = status;
   const int ntiles = P.tiles_m * P.tiles_n;
   int grid = ntiles < dev.sm_count ? ntiles : dev.sm_count;

@@ -69,7 +69,9 @@ def _run(ctx, Cm, Am, Bm):
     return c.cpu().numpy()
 
 
-@pytest.mark.parametrize("m,n,k", [(300, 300, 256), (128, 128, 64), (1, 1, 1), (257, 130, 200), (129, 385, 33)])
+# m = 32 takes the kernel's stacked form (four slices of A per 128-row box)
+@pytest.mark.parametrize("m,n,k", [(300, 300, 256), (128, 128, 64), (1, 1, 1), (257, 130, 200), (129, 385, 33),
+                                   (32, 300, 256), (32, 129, 200), (32, 1300, 64)])
 def test_exact_on_sliceable_operands(ctx, m, n, k):
     rng = np.random.default_rng(m * 7 + n + k)
     Am = rng.integers(-127, 128, (m, k)) / 128.0 * 2.0 ** rng.integers(-3, 4, (m, 1))
@@ -81,7 +83,8 @@ def test_exact_on_sliceable_operands(ctx, m, n, k):
     assert ctx.status() == 0
 
 
-@pytest.mark.parametrize("m,n,k", [(333, 333, 256), (200, 520, 37), (130, 140, 1), (640, 384, 256)])
+@pytest.mark.parametrize("m,n,k", [(333, 333, 256), (200, 520, 37), (130, 140, 1), (640, 384, 256), (32, 520, 256),
+                                   (32, 1000, 37)])
 def test_error_bound_against_dot2(ctx, m, n, k):
     rng = np.random.default_rng(m + n + k)
     Am = I.uniform_np(30 + k, 0, np.arange(m * k, dtype=np.uint64)).reshape(m, k)
