@@ -45,8 +45,15 @@
 // tile's sums are parked in a per-CTA scratch (L2-resident) and applied to C
 // two columns per slice pair of the next tile, so the FP64 conversion and
 // subtraction (GB300 runs about two FP64 operations per clock per SM) overlap
-// the next tile's products instead of stalling them.  Every mbarrier wait is bounded; on timeout the kernel
-// raises ST_TIMEOUT, lets issued copies and MMAs land, frees TMEM and returns.
+// the next tile's products instead of stalling them.  With m = 32 (the
+// refinement's residual for 32 right-hand sides) A's slices lie 32 rows apart,
+// so the box of slice p holds slices p .. p + 3 in its four TMEM lane quarters:
+// a tile then takes the products of slices 0 and 4 only (12 instead of 36),
+// each epilogue warp weights its quarter by that quarter's slice order, and
+// the four quarters' exact partial sums are added before the FP64 update,
+// which every quarter applies to a quarter of the columns.  Every mbarrier
+// wait is bounded; on timeout the kernel raises ST_TIMEOUT, lets issued copies
+// and MMAs land, frees TMEM and returns.
 #include <cuda_bf16.h>
 
 #include <mutex>
